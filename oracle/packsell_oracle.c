@@ -1,0 +1,419 @@
+/*
+ * PackSELL oracle: a plain, slow, obviously correct CPU implementation of what
+ * the PackSELL format and its SpMV compute (arXiv 2604.13433).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library's compute path may link,
+ * load or call this file; only the tests, the smoke check and the bench's CPU
+ * baseline do. It shares no code, header, table or helper with the CUDA
+ * library: every routine here is written from the paper's text.
+ *
+ * Precision: integer and bit work is exact. Values are handled in double
+ * precision except the FP32 "twin" SpMV, which fixes FP32 fused multiply-add
+ * in stored order on purpose. Build with -ffp-contract=off (no implicit FMA).
+ *
+ * Readings of the paper taken here where it is silent (each is listed with its
+ * reason in the design notes):
+ *  - E8MY below FP32's normal range: the rounding grid stays at the spacing
+ *    of the smallest normal binade (the paper's ldexpf would underflow).
+ *  - Padding and dummy words contribute nothing (no x load, no multiply).
+ *  - Stable sort inside sigma blocks: equal word counts keep original order.
+ *  - Columns must be strictly increasing inside a row.
+ */
+#include <math.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_UNSORTED = 2, ORC_ERR_NONFINITE = 3,
+       ORC_ERR_RANGE = 4 };
+enum { ORC_FMT_FP16 = 1, ORC_FMT_E8MY = 2 };
+
+/* ------------------------------------------------------------------------ */
+/* Value formats (§4.2.2)                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* IEEE 754 binary16 from a real value, round to nearest, ties to even.
+ * Written from the binary16 definition: 1 sign, 5 exponent bits (bias 15),
+ * 10 fraction bits; subnormals have spacing 2^-24; largest finite 65504.
+ * Returns ORC_OK, ORC_ERR_NONFINITE (input inf/nan) or ORC_ERR_RANGE
+ * (rounds past 65504). */
+int orc_f16_bits(double v, uint16_t *out)
+{
+    if (isnan(v) || isinf(v)) return ORC_ERR_NONFINITE;
+    uint16_t sign = signbit(v) ? 0x8000u : 0u;
+    double a = fabs(v);
+    if (a == 0.0) { *out = sign; return ORC_OK; }
+    int ex;
+    (void)frexp(a, &ex); /* a = f * 2^ex, f in [0.5, 1): binade [2^(ex-1), 2^ex) */
+    int e = ex - 1;      /* a in [2^e, 2^(e+1)) */
+    double q = (e < -14) ? ldexp(1.0, -24) : ldexp(1.0, e - 10); /* spacing */
+    double r = a / q;    /* exact: division by a power of two */
+    double fl = floor(r);
+    double rem = r - fl;
+    if (rem > 0.5 || (rem == 0.5 && fmod(fl, 2.0) != 0.0)) fl += 1.0;
+    double res = fl * q;
+    if (res > 65504.0) return ORC_ERR_RANGE;
+    uint16_t bits;
+    if (res < ldexp(1.0, -14)) {
+        bits = (uint16_t)fl; /* subnormal: count of 2^-24 (0 .. 1023) */
+    } else {
+        int rex;
+        (void)frexp(res, &rex);
+        int E = rex - 1;                        /* res in [2^E, 2^(E+1)) */
+        double frac = res / ldexp(1.0, E) - 1.0; /* in [0, 1) */
+        bits = (uint16_t)(((E + 15) << 10) | (uint16_t)(frac * 1024.0));
+    }
+    *out = (uint16_t)(sign | bits);
+    return ORC_OK;
+}
+
+/* Real value of a binary16 bit pattern. */
+double orc_f16_value(uint16_t h)
+{
+    int s = (h >> 15) & 1, E = (h >> 10) & 0x1f, F = h & 0x3ff;
+    double mag;
+    if (E == 0) mag = ldexp((double)F, -24);
+    else if (E == 31) mag = F ? NAN : INFINITY;
+    else mag = ldexp(1.0 + F / 1024.0, E - 15);
+    return s ? -mag : mag;
+}
+
+static uint32_t f32_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+static float f32_from_bits(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+
+/* E8MY bits (1 sign, 8 exponent, Y = 22 - D mantissa bits, FP32 layout with
+ * the low D + 1 bits clear), following the paper's steps (§4.2.2): take the
+ * binary exponent of v, set the rounding unit to 2^(exp - 24 + D + 1), round
+ * v / unit to the nearest integer with halves away from zero, scale back,
+ * reinterpret as FP32 bits and clear the low D + 1 bits.
+ * Reading where the paper is silent: below FP32's normal range the exponent is
+ * held at that of the smallest normal binade, so the unit stays 2^(D + 1)
+ * FP32 subnormal steps. Returns ORC_OK, ORC_ERR_NONFINITE or ORC_ERR_RANGE. */
+int orc_e8my_bits(double v, int D, uint32_t *out)
+{
+    if (D < 1 || D > 22) return ORC_ERR_ARG;
+    if (isnan(v) || isinf(v)) return ORC_ERR_NONFINITE;
+    if (v == 0.0) { *out = signbit(v) ? 0x80000000u : 0u; return ORC_OK; }
+    int ex;
+    (void)frexp(v, &ex);
+    if (ex < -125) ex = -125;
+    double unit = ldexp(1.0, ex - 24 + D + 1);
+    double r = round(v / unit) * unit; /* round(): halves away from zero */
+    if (fabs(r) >= ldexp(1.0, 128)) return ORC_ERR_RANGE;
+    float rf = (float)r;
+    if ((double)rf != r) return ORC_ERR_RANGE; /* cannot happen on the grid */
+    uint32_t b = f32_bits(rf);
+    b = (b >> (D + 1)) << (D + 1);
+    *out = b;
+    return ORC_OK;
+}
+
+/* Upper-V-bit value field for format fmt (FP16 needs D = 15). */
+int orc_value_field(double v, int fmt, int D, uint32_t *field)
+{
+    if (fmt == ORC_FMT_FP16) {
+        if (D != 15) return ORC_ERR_ARG;
+        uint16_t h;
+        int st = orc_f16_bits(v, &h);
+        if (st) return st;
+        *field = (uint32_t)h << 16;
+        return ORC_OK;
+    }
+    if (fmt == ORC_FMT_E8MY) return orc_e8my_bits(v, D, field);
+    return ORC_ERR_ARG;
+}
+
+/* The working-precision value a field stands for. */
+double orc_field_value(uint32_t field, int fmt)
+{
+    if (fmt == ORC_FMT_FP16) return orc_f16_value((uint16_t)(field >> 16));
+    return (double)f32_from_bits(field);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Words (§4.2.1): bit 0 is the flag.                                         */
+/*   flag 1: bits 1..D hold the delta, bits D+1..31 the value.                */
+/*   flag 0: bits 1..31 hold the delta; there is no value.                    */
+/* ------------------------------------------------------------------------ */
+uint32_t orc_word_value(uint32_t field, uint32_t delta) { return field | (delta << 1) | 1u; }
+uint32_t orc_word_dummy(uint32_t delta) { return delta << 1; }
+
+/* Split a word into (flag, delta, value field). */
+void orc_unpack(uint32_t w, int D, uint32_t *flag, uint32_t *delta, uint32_t *field)
+{
+    if (w & 1u) {
+        *flag = 1;
+        *delta = (w >> 1) & ((1u << D) - 1u);
+        *field = w & ~((1u << (D + 1)) - 1u);
+    } else {
+        *flag = 0;
+        *delta = w >> 1;
+        *field = 0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Encoding (§4.1 delta encoding, §4.3 alignment, dummies, permutation)       */
+/* ------------------------------------------------------------------------ */
+
+/* Lower bandwidth k_left = max(0, max over nonzeros a_ij of i - j). */
+int64_t orc_lower_bandwidth(int64_t n, const int64_t *rowptr, const int32_t *col)
+{
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (i - col[p] > k) k = i - col[p];
+    return k;
+}
+
+/* Left offset of Eq. 4: uniform inside each block of sigma rows. */
+int64_t orc_left_offset(int64_t i, int64_t sigma, int64_t k_left)
+{
+    int64_t b = (i / sigma) * sigma;
+    return (k_left < b) ? b - k_left : 0;
+}
+
+/* Check the CSR: columns in [0, m), strictly increasing inside each row. */
+int orc_check_csr(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col)
+{
+    if (rowptr[0] != 0) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return ORC_ERR_ARG;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            if (col[p] < 0 || col[p] >= m) return ORC_ERR_RANGE;
+            if (p > rowptr[i] && col[p] <= col[p - 1]) return ORC_ERR_UNSORTED;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Stored words of original row i: its nonzeros plus one dummy before every
+ * nonzero whose delta (Eq. 2, first delta taken from the left offset) does not
+ * fit in D bits. Returns -1 if a delta would be negative. */
+int64_t orc_row_words(int64_t i, const int64_t *rowptr, const int32_t *col, int64_t sigma,
+                      int64_t k_left, int D, int64_t *dummies)
+{
+    int64_t prev = orc_left_offset(i, sigma, k_left), words = 0;
+    *dummies = 0;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int64_t d = (int64_t)col[p] - prev;
+        if (d < 0) return -1;
+        if (d >= ((int64_t)1 << D)) { ++words; ++*dummies; }
+        ++words;
+        prev = col[p];
+    }
+    return words;
+}
+
+typedef struct { int64_t key; int64_t idx; } orc_kv;
+
+static int orc_kv_cmp(const void *a, const void *b)
+{
+    const orc_kv *x = (const orc_kv *)a, *y = (const orc_kv *)b;
+    if (x->key != y->key) return (x->key > y->key) ? -1 : 1; /* descending words */
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);        /* stable */
+}
+
+/* Plan: word counts, sigma permutation, slice offsets.
+ *   words[n]         stored words per ORIGINAL row
+ *   perm[n]          for STORAGE row i, original row = floor(i/sigma)*sigma + perm[i]
+ *   offset[S+1]      S = ceil(n / C) slices, offset[k+1] - offset[k] = C * w_k
+ *   stats[4]         k_left used, total words, dummies, padding words
+ * k_left_in < 0 computes the lower bandwidth. */
+int orc_encode_plan(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col,
+                    int32_t C, int32_t sigma, int32_t D, int64_t k_left_in,
+                    int64_t *words, int32_t *perm, int64_t *offset, int64_t *stats)
+{
+    if (n < 0 || m < 0 || m >= ((int64_t)1 << 31) || C < 1 || sigma < 1 || D < 1 || D > 22)
+        return ORC_ERR_ARG;
+    int st = orc_check_csr(n, m, rowptr, col);
+    if (st) return st;
+    int64_t k_left = k_left_in < 0 ? orc_lower_bandwidth(n, rowptr, col) : k_left_in;
+    int64_t dummies = 0, nnz = rowptr[n];
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t dm;
+        words[i] = orc_row_words(i, rowptr, col, sigma, k_left, D, &dm);
+        if (words[i] < 0) return ORC_ERR_ARG; /* k_left smaller than the bandwidth */
+        dummies += dm;
+    }
+    orc_kv *kv = (orc_kv *)malloc(sizeof(orc_kv) * (size_t)(sigma > 0 ? sigma : 1));
+    if (!kv) return ORC_ERR_ARG;
+    for (int64_t b0 = 0; b0 < n; b0 += sigma) {
+        int64_t len = (n - b0 < sigma) ? n - b0 : sigma;
+        for (int64_t t = 0; t < len; ++t) { kv[t].key = words[b0 + t]; kv[t].idx = t; }
+        qsort(kv, (size_t)len, sizeof(orc_kv), orc_kv_cmp);
+        for (int64_t t = 0; t < len; ++t) perm[b0 + t] = (int32_t)kv[t].idx;
+    }
+    free(kv);
+    int64_t S = (n + C - 1) / C;
+    offset[0] = 0;
+    for (int64_t k = 0; k < S; ++k) {
+        int64_t w = 0;
+        for (int64_t i = k * C; i < (k + 1) * C && i < n; ++i) {
+            int64_t orig = (i / sigma) * sigma + perm[i];
+            if (words[orig] > w) w = words[orig];
+        }
+        offset[k + 1] = offset[k] + (int64_t)C * w;
+    }
+    stats[0] = k_left;
+    stats[1] = offset[S];
+    stats[2] = dummies;
+    stats[3] = offset[S] - nnz - dummies; /* padding, phantom rows included */
+    return ORC_OK;
+}
+
+/* Fill pack[offset[S]] given the plan. field[nnz] holds each nonzero's value
+ * field (from orc_value_field) in CSR order. */
+int orc_encode_fill(int64_t n, const int64_t *rowptr, const int32_t *col, const uint32_t *field,
+                    int32_t C, int32_t sigma, int32_t D, int64_t k_left, const int32_t *perm,
+                    const int64_t *offset, uint32_t *pack)
+{
+    int64_t S = (n + C - 1) / C;
+    memset(pack, 0, sizeof(uint32_t) * (size_t)offset[S]); /* padding words are 0 */
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t prev = orc_left_offset(i, sigma, k_left), j = 0;
+        for (int64_t p = rowptr[orig]; p < rowptr[orig + 1]; ++p) {
+            int64_t d = (int64_t)col[p] - prev;
+            if (d < 0) return ORC_ERR_ARG;
+            if (d >= ((int64_t)1 << D)) {
+                pack[offset[k] + j * C + l] = orc_word_dummy((uint32_t)d);
+                ++j;
+                d = 0;
+            }
+            pack[offset[k] + j * C + l] = orc_word_value(field[p], (uint32_t)d);
+            ++j;
+            prev = col[p];
+        }
+        if (offset[k] + j * C > offset[k + 1]) return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
+
+/* Decode back to CSR in ORIGINAL row order: counts[n] real words per row,
+ * then col_out/field_out at out_rowptr positions (caller passes the rowptr it
+ * expects; the function reports a mismatch in counts through the return). */
+int orc_decode(int64_t n, int32_t C, int32_t sigma, int32_t D, int64_t k_left,
+               const int32_t *perm, const int64_t *offset, const uint32_t *pack,
+               const int64_t *rowptr, int32_t *col_out, uint32_t *field_out, int64_t *counts)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t w = (offset[k + 1] - offset[k]) / C;
+        int64_t c = orc_left_offset(i, sigma, k_left), q = rowptr[orig], cnt = 0;
+        for (int64_t j = 0; j < w; ++j) {
+            uint32_t flag, delta, fld;
+            orc_unpack(pack[offset[k] + j * C + l], D, &flag, &delta, &fld);
+            c += delta;
+            if (flag) {
+                if (q < rowptr[orig + 1]) { col_out[q] = (int32_t)c; field_out[q] = fld; }
+                ++q;
+                ++cnt;
+            }
+        }
+        counts[orig] = cnt;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SpMV                                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* y = A x in double over CSR (y_i = sum_j a_ij x_j, CSR order). */
+void orc_csr_spmv_f64(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                      const double *x, double *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) t += val[p] * x[col[p]];
+        y[i] = t;
+    }
+}
+
+/* y = A x in single precision with one fused multiply-add per nonzero in CSR
+ * (= stored) order, starting from +0. This is exactly what a thread that owns
+ * one row and walks its packed words in order computes. */
+void orc_csr_spmv_fma_f32(int64_t n, const int64_t *rowptr, const int32_t *col,
+                          const float *val, const float *x, float *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        float t = 0.0f;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) t = fmaf(val[p], x[col[p]], t);
+        y[i] = t;
+    }
+}
+
+/* dx = A^T dy in double. */
+void orc_csr_spmv_t_f64(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col,
+                        const double *val, const double *dy, double *dx)
+{
+    for (int64_t j = 0; j < m; ++j) dx[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) dx[col[p]] += val[p] * dy[i];
+}
+
+/* Y = A X in double, X row-major [m x k] (leading dimension ldx), Y [n x k]. */
+void orc_csr_spmm_f64(int64_t n, int64_t k, const int64_t *rowptr, const int32_t *col,
+                      const double *val, const double *X, int64_t ldx, double *Y, int64_t ldy)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t r = 0; r < k; ++r) Y[i * ldy + r] = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            for (int64_t r = 0; r < k; ++r) Y[i * ldy + r] += val[p] * X[(int64_t)col[p] * ldx + r];
+    }
+}
+
+/* The paper's PackSELL SpMV algorithm (§4.4) run over packed words, in double:
+ * for each storage row i, c starts at the left offset, every word adds its
+ * delta to c, and every word that carries a value adds value * x_c.
+ * explicit_order != 0 writes y in storage order, else in original order. */
+void orc_packsell_spmv_f64(int64_t n, int32_t C, int32_t sigma, int32_t D, int32_t fmt,
+                           int64_t k_left, const int32_t *perm, const int64_t *offset,
+                           const uint32_t *pack, const double *x, double *y, int explicit_order)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C;
+        int64_t iout = explicit_order ? i : (i / sigma) * sigma + perm[i];
+        int64_t s = offset[k], w = (offset[k + 1] - s) / C;
+        int64_t c = orc_left_offset(i, sigma, k_left);
+        double t = 0.0;
+        for (int64_t j = 0; j < w; ++j) {
+            uint32_t flag, delta, fld;
+            orc_unpack(pack[s + j * C + l], D, &flag, &delta, &fld);
+            c += delta;
+            if (flag) t += orc_field_value(fld, fmt) * x[c];
+        }
+        y[iout] = t;
+    }
+}
+
+/* Quantize nnz values into value fields and their working-precision values.
+ * Returns the first error, with its index in *bad (or -1). */
+int orc_quantize(int64_t nnz, const double *val, int32_t fmt, int32_t D, uint32_t *field,
+                 double *deq, int64_t *bad)
+{
+    *bad = -1;
+    for (int64_t p = 0; p < nnz; ++p) {
+        int st = orc_value_field(val[p], fmt, D, &field[p]);
+        if (st) { *bad = p; return st; }
+        deq[p] = orc_field_value(field[p], fmt);
+    }
+    return ORC_OK;
+}
+
+/* Number of threads the OpenMP loops above use (1 without OpenMP). */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,179 @@
+"""Oracle solvers: Jacobi PCG, inner-outer CG and adjoints, in numpy.
+
+TEST INFRASTRUCTURE ONLY (see :mod:`oracle`).
+
+* :func:`pcg` - preconditioned CG in double precision with a Jacobi
+  (diagonal) preconditioner; the FP64 PCG baseline of §5.2.2.
+* :func:`iocg` - the inner-outer CG of §5.2.2: flexible CG in double
+  precision whose preconditioner is ``m_in`` iterations of PCG run in single
+  precision (simulated: every inner vector is stored as float32 and every inner
+  dot product is accumulated in double) with the quantised matrix.
+* :func:`adjoint_grads` - gradients of a loss of the solution of A x = b with
+  respect to b and to the matrix entries on the sparsity pattern, from one
+  adjoint solve A^T lam = dL/dx.
+
+Readings where the paper is silent (§5.2.2 gives the scheme, not the details):
+the outer method is flexible CG with truncation 1 (one previous direction,
+Notay's FCG(1)); the inner solve starts from zero, takes exactly ``m_in``
+iterations, and works on the outer residual divided by its 2-norm (scaled
+back afterwards); convergence is declared on the true residual
+||b - A x||_2 / ||b||_2 recomputed in double precision.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import csr_spmv_f64
+
+
+def _dot(a, b) -> float:
+    return float(np.dot(np.asarray(a, np.float64), np.asarray(b, np.float64)))
+
+
+def pcg(A, b, x0=None, tol=1e-10, maxit=10000, inv_diag=None, val=None):
+    """Jacobi-preconditioned CG in double precision.
+
+    ``A`` is a CSR (values ``val`` or ``A.val``). Returns (x, iters, hist) with
+    hist[k] = ||r_k||_2 / ||b||_2 of the recurrence residual; on reaching tol
+    the true residual is recomputed, and the iteration continues from it if
+    it is not yet below tol.
+    """
+    val = A.val if val is None else val
+    b = np.asarray(b, np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+    M = np.ones_like(b) if inv_diag is None else np.asarray(inv_diag, np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - csr_spmv_f64(A, val, x)
+    z = M * r
+    p = z.copy()
+    rz = _dot(r, z)
+    hist = [np.linalg.norm(r) / nb]
+    it = 0
+    while it < maxit:
+        if hist[-1] < tol:
+            rt = b - csr_spmv_f64(A, val, x)
+            if np.linalg.norm(rt) / nb < tol:
+                break
+            r = rt
+            z = M * r
+            p = z.copy()
+            rz = _dot(r, z)
+        q = csr_spmv_f64(A, val, p)
+        pq = _dot(p, q)
+        if pq <= 0.0:
+            raise FloatingPointError("pcg: p^T A p <= 0 (matrix not SPD)")
+        alpha = rz / pq
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        hist.append(np.linalg.norm(r) / nb)
+        z = M * r
+        rz_new = _dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, hist
+
+
+def inner_pcg_f32(A, deq, r, m_in, inv_diag=None):
+    """m_in PCG iterations on A z = r from z = 0 in simulated single precision.
+
+    The right-hand side is r / ||r||_2 (rounded to float32); the result is
+    scaled back by ||r||_2 in double. Vectors are float32, dot products are
+    accumulated in double, scalars alpha and beta are rounded to float32 before
+    they scale a vector, and A v is the quantised matrix applied in double and
+    rounded to float32.
+    """
+    s = float(np.linalg.norm(r))
+    if s == 0.0:
+        return np.zeros_like(r, dtype=np.float64)
+    rr = (np.asarray(r, np.float64) / s).astype(np.float32)
+    M = None if inv_diag is None else np.asarray(inv_diag, np.float32)
+    xx = np.zeros_like(rr)
+    z = rr if M is None else (M * rr).astype(np.float32)
+    p = z.copy()
+    rz = _dot(rr, z)
+    for _ in range(m_in):
+        if rz == 0.0:
+            break
+        q = csr_spmv_f64(A, deq, p).astype(np.float32)
+        pq = _dot(p, q)
+        if pq <= 0.0:
+            break
+        a = np.float32(rz / pq)
+        xx = (xx + a * p).astype(np.float32)
+        rr = (rr - a * q).astype(np.float32)
+        z = rr if M is None else (M * rr).astype(np.float32)
+        rz_new = _dot(rr, z)
+        bta = np.float32(rz_new / rz)
+        p = (z + bta * p).astype(np.float32)
+        rz = rz_new
+    return xx.astype(np.float64) * s
+
+
+def iocg(A, b, deq, m_in=20, tol=1e-10, max_outer=1000, x0=None, inv_diag=None,
+         val64=None, inner=None):
+    """Inner-outer CG (§5.2.2): FCG(1) in double, preconditioned by m_in
+    single-precision PCG iterations on the quantised matrix ``deq``.
+
+    ``inner`` may replace the inner solve (a callable r -> z) for tests.
+    Returns (x, outer_iters, hist) with hist[k] the outer recurrence relative
+    residual after outer iteration k.
+    """
+    val64 = A.val if val64 is None else val64
+    b = np.asarray(b, np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - csr_spmv_f64(A, val64, x)
+    hist = [np.linalg.norm(r) / nb]
+    p_prev = q_prev = None
+    pq_prev = 0.0
+    k = 0
+    solve = inner if inner is not None else (lambda v: inner_pcg_f32(A, deq, v, m_in, inv_diag))
+    while k < max_outer:
+        if hist[-1] < tol:
+            rt = b - csr_spmv_f64(A, val64, x)
+            if np.linalg.norm(rt) / nb < tol:
+                break
+            r = rt
+            p_prev = None
+        z = solve(r)
+        if p_prev is None:
+            p = z
+        else:
+            p = z - (_dot(z, q_prev) / pq_prev) * p_prev
+        q = csr_spmv_f64(A, val64, p)
+        pq = _dot(p, q)
+        if pq <= 0.0:
+            raise FloatingPointError("iocg: p^T A p <= 0")
+        alpha = _dot(p, r) / pq
+        x += alpha * p
+        r -= alpha * q
+        k += 1
+        hist.append(np.linalg.norm(r) / nb)
+        p_prev, q_prev, pq_prev = p, q, pq
+    return x, k, hist
+
+
+def adjoint_grads(A, x, g, val=None, tol=1e-13, inv_diag=None):
+    """For x = A^-1 b and a loss with dL/dx = g: lam = A^-T g (A symmetric
+    here, so one PCG solve), dL/db = lam and dL/da_ij = -lam_i x_j on the
+    pattern of A (CSR order)."""
+    val = A.val if val is None else val
+    lam, _, _ = pcg(A, g, tol=tol, maxit=100000, inv_diag=inv_diag, val=val)
+    row = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dval = -lam[row] * np.asarray(x, np.float64)[A.col]
+    return lam, dval
+
+
+def face_grads(faces, dval):
+    """Chain dL/dA on the pattern to the face coefficients of
+    A = sum_f theta_f (e_u - e_v)(e_u - e_v)^T + sum_b theta_b e_b e_b^T:
+    dL/dtheta_f = dA_uu + dA_vv - dA_uv - dA_vu, dL/dtheta_b = dA_bb."""
+    gf = (dval[faces["pos_uu"]] + dval[faces["pos_vv"]] - dval[faces["pos_uv"]]
+          - dval[faces["pos_vu"]])
+    gb = dval[faces["pos_b"]]
+    return np.concatenate([gf, gb])
