@@ -1,0 +1,196 @@
+/*
+ * packsell.h - C ABI of the PackSELL library for GB300 (sm_103a).
+ *
+ * PackSELL (arXiv 2604.13433) is sliced ELLPACK in which every 32-bit word
+ * packs a delta-encoded column index and a matrix value:
+ *   bit 0 (flag) = 1: bits 1..D hold the delta, bits D+1..31 hold the value
+ *                     (V = 31 - D bits; W = V + D + 1 = 32, §4.2.1);
+ *   bit 0 (flag) = 0: bits 1..31 hold the delta and there is no value
+ *                     (a dummy, inserted before any nonzero whose delta does
+ *                     not fit in D bits, or padding when the word is 0, §4.3).
+ * Column indices are deltas from the previous nonzero of the row; the first
+ * one is taken from the left offset of Eq. 4, which depends only on the block
+ * of sigma rows the row belongs to (§4.1, §4.3). Rows are grouped into slices
+ * of C rows stored column-major and padded to the slice's widest row; rows
+ * are sorted by stored-word count inside blocks of sigma rows (SELL-C-sigma,
+ * §3), the in-block permutation kept in `perm`.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers unless the name starts with h_ (host).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous on it unless the comment says the call synchronises.
+ *  - The caller owns every vector it passes; the library owns the device
+ *    buffers inside a packsell_matrix until packsell_destroy.
+ *  - Every call returns a packsell_status. On failure nothing is written to
+ *    outputs except where stated, and packsell_last_error() describes it.
+ *    No C++ exception crosses this boundary.
+ *  - Index types: row and column counts below 2^31, nonzero and word counts
+ *    in int64.
+ */
+#ifndef PACKSELL_H
+#define PACKSELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PACKSELL_VERSION_MAJOR 0
+#define PACKSELL_VERSION_MINOR 1
+
+typedef enum packsell_status {
+    PACKSELL_OK = 0,
+    PACKSELL_ERR_INVALID_ARG = 1,   /* bad size, parameter or pointer */
+    PACKSELL_ERR_UNSORTED = 2,      /* CSR columns not strictly increasing in a row */
+    PACKSELL_ERR_NONFINITE = 3,     /* a matrix value is Inf or NaN */
+    PACKSELL_ERR_RANGE = 4,         /* value overflows the format, or column out of range */
+    PACKSELL_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    PACKSELL_ERR_NOT_CONVERGED = 6, /* solver hit its iteration limit */
+    PACKSELL_ERR_BREAKDOWN = 7,     /* solver: p^T A p <= 0 or a non-finite residual */
+    PACKSELL_ERR_NO_MEMORY = 8,     /* device allocation failed */
+    PACKSELL_ERR_CORRUPT = 9        /* imported data fails validation */
+} packsell_status;
+
+/* Value formats.
+ * FP16  : IEEE binary16 in bits 16..31, round to nearest even; needs D = 15
+ *         (§4.2.2, the paper's FP16 configuration).
+ * E8MY  : 1 sign, 8 exponent, Y = 22 - D mantissa bits: an FP32 bit pattern
+ *         with the low D+1 bits clear, rounded half away from zero on its
+ *         grid (§4.2.2); D in [1, 22].
+ * SELL_F32 / SELL_F64 : plain SELL-C-sigma (§3) with separate FP32 / FP64
+ *         value and int32 column arrays: the baseline format and the FP64
+ *         outer operator of the mixed-precision solver. D is ignored. */
+typedef enum packsell_format {
+    PACKSELL_FMT_FP16 = 1,
+    PACKSELL_FMT_E8MY = 2,
+    PACKSELL_FMT_SELL_F32 = 3,
+    PACKSELL_FMT_SELL_F64 = 4
+} packsell_format;
+
+typedef struct packsell_params {
+    int32_t C;             /* slice height in rows, 1..1024 (32 = one warp) */
+    int32_t sigma;         /* sort block in rows, 1..65536 (1 = no sorting) */
+    int32_t D;             /* delta bits (see packsell_format) */
+    int32_t format;        /* a packsell_format */
+    int32_t explicit_perm; /* 1: y is written in storage (sorted) row order,
+                              0: y is written in the original row order */
+    int32_t keep_rowptr;   /* 1: keep a copy of the CSR row pointer, needed to
+                              write matrix gradients in CSR order */
+    int64_t k_left;        /* lower bandwidth used in Eq. 4; -1 computes it */
+} packsell_params;
+
+/* Defaults: C = 32, sigma = 256, D = 15, FP16, implicit permutation,
+ * keep_rowptr = 0, k_left = -1. */
+void packsell_params_default(packsell_params *p);
+
+typedef struct packsell_matrix packsell_matrix; /* opaque */
+
+typedef struct packsell_info {
+    int64_t n, m, nnz;
+    packsell_params params; /* k_left filled in with the value used */
+    int64_t n_slices;       /* ceil(n / C) */
+    int64_t n_words;        /* stored words (PackSELL) or elements (SELL) */
+    int64_t n_dummies;      /* dummy words (0 for SELL) */
+    int64_t n_pad;          /* padding words, phantom rows of the last slice included */
+    int32_t max_width;      /* widest slice, in words per row */
+    int32_t perm_bytes;     /* bytes per perm entry: 0 (sigma = 1), 1 or 2 */
+    int64_t bytes;          /* device bytes the matrix holds (all arrays) */
+    /* device arrays (read-only views for tests and tools) */
+    const uint32_t *pack;   /* PackSELL words, NULL for SELL formats */
+    const void *val;        /* SELL values (float or double), NULL for PackSELL */
+    const int32_t *col;     /* SELL columns, NULL for PackSELL */
+    const int64_t *offset;  /* n_slices + 1 word offsets of the slices */
+    const void *perm;       /* n entries of perm_bytes, NULL when sigma = 1 */
+} packsell_info;
+
+const char *packsell_version(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *packsell_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Encoding (§4.1 Eq. 2, §4.2, §4.3 Eq. 4, §3 sigma sort)                   */
+/* ---------------------------------------------------------------------- */
+
+/* Encode an n x m CSR matrix into PackSELL (or SELL) on the device.
+ *   rowptr : int64 [n + 1], rowptr[0] = 0, rowptr[n] = nnz
+ *   col    : int32 [nnz], strictly increasing within each row, in [0, m)
+ *   val    : [nnz] float (val_is_f64 = 0) or double (val_is_f64 = 1)
+ * Every step runs in CUDA kernels on `stream`: validation, lower bandwidth,
+ * quantisation, word counts with dummies, the stable sigma sort (descending
+ * stored words), slice widths, offsets, scatter. The call SYNCHRONISES the
+ * stream once (to size the word array). Temporaries are stream-ordered
+ * allocations freed before return. On success *out owns new device buffers.
+ * Errors: INVALID_ARG (parameters, k_left below the bandwidth), UNSORTED,
+ * RANGE (column out of range, value overflows the format), NONFINITE,
+ * NO_MEMORY, CUDA. The encoded words are bit-identical to the paper's
+ * definition for the same parameters. */
+packsell_status packsell_encode(const packsell_params *params, int64_t n, int64_t m,
+                                int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                                const void *val, int32_t val_is_f64, void *stream,
+                                packsell_matrix **out);
+
+/* Free the matrix (synchronises the device first). NULL is accepted. */
+packsell_status packsell_destroy(packsell_matrix *A);
+
+packsell_status packsell_get_info(const packsell_matrix *A, packsell_info *info);
+
+/* Serialise to a host blob: header, offset, perm, then pack (or val, col).
+ * With h_blob == NULL only *bytes is set. Synchronises `stream`. */
+packsell_status packsell_export(const packsell_matrix *A, void *h_blob, size_t *bytes,
+                                void *stream);
+
+/* Rebuild a matrix from packsell_export's blob. The blob is validated on the
+ * device (every row decoded, columns checked against m, value words counted
+ * against nnz) before the call returns; a bad blob gives CORRUPT and no
+ * matrix. Synchronises `stream`. */
+packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
+                                packsell_matrix **out);
+
+/* ---------------------------------------------------------------------- */
+/* Products (§4.4 PackSELL SpMV; §3 SELL SpMV)                              */
+/* ---------------------------------------------------------------------- */
+
+/* y = A x. x: float [m], y: float [n] (original order, or storage order with
+ * explicit_perm). FP32 accumulation; each row is summed by one thread in
+ * stored order with fused multiply-adds, so the result is bitwise
+ * reproducible. Words with flag 0 (dummies, padding) read no x and add
+ * nothing. Works for PackSELL and SELL_F32 matrices. No allocation. */
+packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
+                              void *stream);
+
+/* y = A x in double for a SELL_F64 matrix (the FP64 outer operator). */
+packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
+                                  void *stream);
+
+/* Y = A X for k right-hand sides. X: float, row-major [m x k] with leading
+ * dimension ldx >= k; Y: float, row-major [n x k] with ldy >= k. One decode
+ * of each word feeds k multiply-adds. PackSELL and SELL_F32 matrices. */
+packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X,
+                              int64_t ldx, float *Y, int64_t ldy, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Backward (adjoint) products                                              */
+/* ---------------------------------------------------------------------- */
+
+/* dx = A^T dy (float [m]), written from the packed layout with atomic adds:
+ * the result is overwritten (not accumulated) and its rounding depends on
+ * the order of the adds. */
+packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *dy,
+                                        float *dx, void *stream);
+
+/* out[q] = alpha * u_i * v_j for every stored nonzero a_ij, with q its CSR
+ * position. u: float [n] (original row order), v: float [m], out: float
+ * [nnz]. This is dL/dA on the pattern for y = A x (u = dL/dy, v = x,
+ * alpha = 1) and for x = A^-1 b (u = adjoint solution, v = x, alpha = -1).
+ * Needs a matrix encoded with keep_rowptr = 1. */
+packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, const float *u,
+                                       const float *v, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACKSELL_H */

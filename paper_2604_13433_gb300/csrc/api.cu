@@ -1,0 +1,280 @@
+// C ABI entry points: argument checks, error text, matrix lifetime, export.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace packsell {
+
+static thread_local std::string g_last_error;
+
+packsell_status fail(packsell_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+packsell_status cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PACKSELL_ERR_NO_MEMORY : PACKSELL_ERR_CUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int64_t matrix_bytes(const Matrix &A) {
+    int64_t b = 8 * (A.n_slices + 1) + (int64_t)A.perm_bytes * A.n;
+    if (is_packed(A.p.format)) b += 4 * A.n_words;
+    else b += (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8) * A.n_words;
+    if (A.rowptr) b += 8 * (A.n + 1);
+    return b;
+}
+
+void destroy_matrix(Matrix *A);
+
+}  // namespace packsell
+
+using namespace packsell;
+
+namespace {
+constexpr uint64_t kMagic = 0x314C4C4553434B50ull;  // "PKCSELL1"
+
+struct BlobHeader {
+    uint64_t magic;
+    int64_t n, m, nnz;
+    packsell_params p;
+    int64_t n_slices, n_words, n_dummies, n_pad;
+    int32_t max_width, perm_bytes;
+};
+
+inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+inline const Matrix *M(const packsell_matrix *A) { return reinterpret_cast<const Matrix *>(A); }
+}  // namespace
+
+extern "C" {
+
+void packsell_params_default(packsell_params *p) {
+    if (!p) return;
+    p->C = 32;
+    p->sigma = 256;
+    p->D = 15;
+    p->format = PACKSELL_FMT_FP16;
+    p->explicit_perm = 0;
+    p->keep_rowptr = 0;
+    p->k_left = -1;
+}
+
+const char *packsell_version(void) { return "packsell-gb300 0.1 (sm_103a)"; }
+
+const char *packsell_last_error(void) { return g_last_error.c_str(); }
+
+packsell_status packsell_encode(const packsell_params *params, int64_t n, int64_t m, int64_t nnz,
+                                const int64_t *rowptr, const int32_t *col, const void *val,
+                                int32_t val_is_f64, void *stream, packsell_matrix **out) {
+    clear_error();
+    if (!params) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: params is NULL");
+    Matrix *A = nullptr;
+    packsell_status st = encode_impl(*params, n, m, nnz, rowptr, col, val, val_is_f64,
+                                     as_stream(stream), &A);
+    if (out) *out = reinterpret_cast<packsell_matrix *>(A);
+    return st;
+}
+
+packsell_status packsell_destroy(packsell_matrix *A) {
+    clear_error();
+    if (!A) return PACKSELL_OK;
+    cudaDeviceSynchronize();
+    destroy_matrix(reinterpret_cast<Matrix *>(A));
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_get_info(const packsell_matrix *Ah, packsell_info *info) {
+    clear_error();
+    if (!Ah || !info) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_get_info: NULL argument");
+    const Matrix &A = *M(Ah);
+    memset(info, 0, sizeof(*info));
+    info->n = A.n;
+    info->m = A.m;
+    info->nnz = A.nnz;
+    info->params = A.p;
+    info->n_slices = A.n_slices;
+    info->n_words = A.n_words;
+    info->n_dummies = A.n_dummies;
+    info->n_pad = A.n_pad;
+    info->max_width = A.max_width;
+    info->perm_bytes = A.perm_bytes;
+    info->bytes = matrix_bytes(A);
+    info->pack = A.pack;
+    info->val = A.val;
+    info->col = A.col;
+    info->offset = A.offset;
+    info->perm = A.perm;
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t *bytes,
+                                void *stream) {
+    clear_error();
+    if (!Ah || !bytes) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: NULL argument");
+    const Matrix &A = *M(Ah);
+    size_t vb = is_packed(A.p.format) ? 4 : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
+    size_t need = sizeof(BlobHeader) + 8 * (A.n_slices + 1) + (size_t)A.perm_bytes * A.n +
+                  vb * (size_t)A.n_words;
+    if (!h_blob) {
+        *bytes = need;
+        return PACKSELL_OK;
+    }
+    if (*bytes < need) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: blob too small");
+    BlobHeader h{};
+    h.magic = kMagic;
+    h.n = A.n;
+    h.m = A.m;
+    h.nnz = A.nnz;
+    h.p = A.p;
+    h.p.keep_rowptr = 0;
+    h.n_slices = A.n_slices;
+    h.n_words = A.n_words;
+    h.n_dummies = A.n_dummies;
+    h.n_pad = A.n_pad;
+    h.max_width = A.max_width;
+    h.perm_bytes = A.perm_bytes;
+    char *dst = (char *)h_blob;
+    memcpy(dst, &h, sizeof(h));
+    dst += sizeof(h);
+    cudaStream_t s = as_stream(stream);
+    PS_CUDA(cudaMemcpyAsync(dst, A.offset, 8 * (A.n_slices + 1), cudaMemcpyDeviceToHost, s));
+    dst += 8 * (A.n_slices + 1);
+    if (A.perm_bytes) {
+        PS_CUDA(cudaMemcpyAsync(dst, A.perm, (size_t)A.perm_bytes * A.n, cudaMemcpyDeviceToHost, s));
+        dst += (size_t)A.perm_bytes * A.n;
+    }
+    if (is_packed(A.p.format)) {
+        PS_CUDA(cudaMemcpyAsync(dst, A.pack, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
+    } else {
+        size_t eb = A.p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
+        PS_CUDA(cudaMemcpyAsync(dst, A.val, eb * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
+        dst += eb * (size_t)A.n_words;
+        PS_CUDA(cudaMemcpyAsync(dst, A.col, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
+    }
+    PS_CUDA(cudaStreamSynchronize(s));
+    *bytes = need;
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
+                                packsell_matrix **out) {
+    clear_error();
+    if (!h_blob || !out || bytes < sizeof(BlobHeader))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_import: bad arguments");
+    *out = nullptr;
+    BlobHeader h;
+    memcpy(&h, h_blob, sizeof(h));
+    const packsell_params &p = h.p;
+    bool fmt_ok = is_packed(p.format) || is_sell(p.format);
+    if (h.magic != kMagic || !fmt_ok || h.n < 0 || h.n >= (1ll << 31) || h.m < 0 ||
+        h.m >= (1ll << 31) || p.C < 1 || p.C > 1024 || p.sigma < 1 || p.sigma > 65536 ||
+        (is_packed(p.format) && (p.D < 1 || p.D > 22)) || h.n_slices != (h.n + p.C - 1) / p.C ||
+        h.n_words < 0 || h.perm_bytes != (p.sigma == 1 ? 0 : (p.sigma <= 256 ? 1 : 2)) ||
+        p.k_left < 0)
+        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad header");
+    size_t vb = is_packed(p.format) ? 4 : (p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
+    size_t need = sizeof(BlobHeader) + 8 * (h.n_slices + 1) + (size_t)h.perm_bytes * h.n +
+                  vb * (size_t)h.n_words;
+    if (bytes < need) return fail(PACKSELL_ERR_CORRUPT, "packsell_import: blob truncated");
+    const char *src = (const char *)h_blob + sizeof(h);
+    const int64_t *offs = (const int64_t *)src;
+    if (offs[0] != 0 || offs[h.n_slices] != h.n_words)
+        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: offsets do not match the word count");
+    for (int64_t k = 0; k < h.n_slices; ++k)
+        if (offs[k + 1] < offs[k] || (offs[k + 1] - offs[k]) % p.C)
+            return fail(PACKSELL_ERR_CORRUPT, "packsell_import: offsets not C-aligned");
+
+    Matrix *A = new Matrix();
+    A->n = h.n;
+    A->m = h.m;
+    A->nnz = h.nnz;
+    A->p = p;
+    A->p.keep_rowptr = 0;
+    A->n_slices = h.n_slices;
+    A->n_words = h.n_words;
+    A->n_dummies = h.n_dummies;
+    A->n_pad = h.n_pad;
+    A->max_width = h.max_width;
+    A->perm_bytes = h.perm_bytes;
+    cudaGetDevice(&A->device);
+    cudaStream_t s = as_stream(stream);
+    auto bail = [&](packsell_status st) {
+        destroy_matrix(A);
+        return st;
+    };
+    if (cudaMalloc(&A->offset, 8 * (h.n_slices + 1)) != cudaSuccess ||
+        (h.perm_bytes && cudaMalloc(&A->perm, (size_t)h.perm_bytes * h.n) != cudaSuccess))
+        return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
+    if (cudaMemcpyAsync(A->offset, src, 8 * (h.n_slices + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
+    src += 8 * (h.n_slices + 1);
+    if (h.perm_bytes) {
+        cudaMemcpyAsync(A->perm, src, (size_t)h.perm_bytes * h.n, cudaMemcpyHostToDevice, s);
+        src += (size_t)h.perm_bytes * h.n;
+    }
+    size_t nw = (size_t)std::max<int64_t>(h.n_words, 1);
+    if (is_packed(p.format)) {
+        if (cudaMalloc(&A->pack, 4 * nw) != cudaSuccess)
+            return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
+        cudaMemcpyAsync(A->pack, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
+    } else {
+        size_t eb = p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
+        if (cudaMalloc(&A->val, eb * nw) != cudaSuccess || cudaMalloc(&A->col, 4 * nw) != cudaSuccess)
+            return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
+        cudaMemcpyAsync(A->val, src, eb * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
+        src += eb * (size_t)h.n_words;
+        cudaMemcpyAsync(A->col, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
+    }
+    packsell_status st = validate_impl(*A, s);
+    if (st != PACKSELL_OK) return bail(st);
+    *out = reinterpret_cast<packsell_matrix *>(A);
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y, void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: NULL argument");
+    return spmv_impl(*M(A), x, y, as_stream(stream));
+}
+
+packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
+                                  void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_f64: NULL argument");
+    return spmv_f64_impl(*M(A), x, y, as_stream(stream));
+}
+
+packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X, int64_t ldx,
+                              float *Y, int64_t ldy, void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !X) || (M(A)->n > 0 && !Y))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: NULL argument");
+    return spmm_impl(*M(A), k, X, ldx, Y, ldy, as_stream(stream));
+}
+
+packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *dy, float *dx,
+                                        void *stream) {
+    clear_error();
+    if (!A || (M(A)->n > 0 && !dy) || (M(A)->m > 0 && !dx))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_transpose: NULL argument");
+    return spmv_t_impl(*M(A), dy, dx, as_stream(stream));
+}
+
+packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, const float *u,
+                                       const float *v, float *out, void *stream) {
+    clear_error();
+    if (!A || (M(A)->nnz > 0 && (!u || !v || !out)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pattern_outer: NULL argument");
+    return pattern_outer_impl(*M(A), alpha, u, v, out, as_stream(stream));
+}
+
+}  // extern "C"

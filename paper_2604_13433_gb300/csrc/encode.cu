@@ -1,0 +1,657 @@
+// PackSELL / SELL encoder on the device.
+//
+// Steps (§4.1-§4.3, §3), each a kernel on the caller's stream:
+//   1. check the CSR (row pointer, sorted in-range columns) and take the
+//      lower bandwidth k_left = max(0, max_ij (i - j)) used by Eq. 4;
+//   2. quantise every value into its word's value field (§4.2.2);
+//   3. count stored words per row: nonzeros plus one dummy before every
+//      nonzero whose delta (Eq. 2, first delta from Eq. 4) needs more than D
+//      bits (§4.3);
+//   4. sort rows by stored words, descending and stable, inside blocks of
+//      sigma rows (§3, §4.3) -> perm;
+//   5. slice widths (max over C rows) and their exclusive scan -> offset;
+//   6. (host reads the word total once) scatter words column-major per slice,
+//      zero words as padding.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace packsell {
+namespace {
+
+constexpr int TPB = 256;
+
+inline int blocks_for(int64_t n, int tpb = TPB) {
+    int64_t b = (n + tpb - 1) / tpb;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 30));
+}
+
+__global__ void k_check_rows(int n, int64_t m, int64_t nnz, const int64_t *__restrict__ rowptr,
+                             const int32_t *__restrict__ col, unsigned long long *kl,
+                             DevStatus *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        if (rowptr[0] != 0) dev_fail(st, PACKSELL_ERR_INVALID_ARG, -1);
+        if (rowptr[n] != nnz) dev_fail(st, PACKSELL_ERR_INVALID_ARG, -2);
+    }
+    if (i >= n) return;
+    int64_t a = rowptr[i], b = rowptr[i + 1];
+    if (a < 0 || b < a || b > nnz) {
+        dev_fail(st, PACKSELL_ERR_INVALID_ARG, i);
+        return;
+    }
+    int prev = -1;
+    for (int64_t p = a; p < b; ++p) {
+        int c = col[p];
+        if (c < 0 || (int64_t)c >= m) {
+            dev_fail(st, PACKSELL_ERR_RANGE, p);
+            return;
+        }
+        if (c <= prev) {
+            dev_fail(st, PACKSELL_ERR_UNSORTED, p);
+            return;
+        }
+        prev = c;
+    }
+    if (b > a) {
+        long long d = (long long)i - (long long)col[a];
+        if (d > 0) atomicMax(kl, (unsigned long long)d);
+    }
+}
+
+// FP16 value field: binary16 in bits 16..31, round to nearest even.
+template <typename T>
+__device__ __forceinline__ int field_fp16(T v, uint32_t &field) {
+    if (!isfinite(v)) return PACKSELL_ERR_NONFINITE;
+    __half h = (sizeof(T) == 4) ? __float2half_rn((float)v) : __double2half((double)v);
+    if (__hisinf(h)) return PACKSELL_ERR_RANGE;
+    field = (uint32_t)__half_as_ushort(h) << 16;
+    return 0;
+}
+
+// E8MY value field from an FP32 value: round half away from zero at bit D+1
+// of the FP32 pattern by adding half a step to the magnitude and clearing
+// the low D+1 bits (a carry moves into the exponent on its own).
+__device__ __forceinline__ int field_e8my(float v, int D, uint32_t &field) {
+    uint32_t b = __float_as_uint(v);
+    uint32_t mag = b & 0x7fffffffu;
+    if (mag >= 0x7f800000u) return PACKSELL_ERR_NONFINITE;
+    uint32_t r = (mag + (1u << D)) & ~((2u << D) - 1u);
+    if (r >= 0x7f800000u) return PACKSELL_ERR_RANGE;
+    field = (b & 0x80000000u) | r;
+    return 0;
+}
+
+// E8MY value field from an FP64 value, rounded once from the double: the
+// step is 2^(e - 23 + D) for v in [2^(e-1), 2^e), with e held at FP32's
+// smallest normal binade below it; v / step is rounded half away from zero.
+__device__ __forceinline__ int field_e8my(double v, int D, uint32_t &field) {
+    if (!isfinite(v)) return PACKSELL_ERR_NONFINITE;
+    if (v == 0.0) {
+        field = signbit(v) ? 0x80000000u : 0u;
+        return 0;
+    }
+    int e;
+    frexp(v, &e);
+    if (e < -125) e = -125;
+    if (e > 129) return PACKSELL_ERR_RANGE;
+    double step = ldexp(1.0, e - 23 + D);
+    double r = round(v / step) * step;
+    if (fabs(r) >= 0x1p128) return PACKSELL_ERR_RANGE;
+    field = __float_as_uint((float)r) & ~((2u << D) - 1u);
+    return 0;
+}
+
+template <typename T>
+__global__ void k_quantize(int64_t nnz, const T *__restrict__ val, int fmt, int D,
+                           uint32_t *__restrict__ field, DevStatus *st) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f = 0;
+        int err = (fmt == PACKSELL_FMT_FP16) ? field_fp16(val[p], f) : field_e8my(val[p], D, f);
+        if (err) dev_fail(st, err, p);
+        field[p] = f;
+    }
+}
+
+__device__ __forceinline__ long long resolve_k_left(long long user, const unsigned long long *kl) {
+    return user >= 0 ? user : (long long)*kl;
+}
+
+// Stored words per original row; for SELL (packed = 0) just the row length.
+__global__ void k_count_words(int n, const int64_t *__restrict__ rowptr,
+                              const int32_t *__restrict__ col, int sigma, long long k_left_user,
+                              const unsigned long long *kl, int D, int packed,
+                              int32_t *__restrict__ words, unsigned long long *total,
+                              DevStatus *st) {
+    // a malformed row pointer (found by k_check_rows) must not be walked
+    if (st->code != 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    long long cnt = 0;
+    if (i < n) {
+        int64_t a = rowptr[i], b = rowptr[i + 1];
+        cnt = b - a;
+        if (packed) {
+            long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
+            long long lim = 1ll << D;
+            for (int64_t p = a; p < b; ++p) {
+                long long d = (long long)col[p] - prev;
+                if (d < 0) {
+                    dev_fail(st, PACKSELL_ERR_INVALID_ARG, p);
+                    break;
+                }
+                cnt += (d >= lim);
+                prev = col[p];
+            }
+        }
+        if (cnt > 0x7fffffffll) {
+            dev_fail(st, PACKSELL_ERR_RANGE, i);
+            cnt = 0;
+        }
+        words[i] = (int32_t)cnt;
+    }
+    // warp-reduce the word total, one atomic per warp
+    unsigned long long v = (unsigned long long)cnt;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+// Stable descending sort by stored words inside each block of sigma rows:
+// rank(t) = #{u : w_u > w_t} + #{u < t : w_u == w_t}. Storage row b0 + rank
+// holds original row b0 + t, recorded as perm[b0 + rank] = t (§3).
+constexpr int SORT_TILE = 4096;
+
+__global__ void k_sigma_sort(int n, int sigma, const int32_t *__restrict__ words, void *perm,
+                             int perm_bytes, int32_t *__restrict__ words_st) {
+    __shared__ int32_t tile[SORT_TILE];
+    int64_t b0 = (int64_t)blockIdx.x * sigma;
+    int len = (int)((n - b0 < sigma) ? (n - b0) : sigma);
+    for (int tb = 0; tb < len; tb += blockDim.x) {
+        int t = tb + threadIdx.x;
+        int key = (t < len) ? words[b0 + t] : 0;
+        int rank = 0;
+        for (int ub = 0; ub < len; ub += SORT_TILE) {
+            int cnt = (len - ub < SORT_TILE) ? (len - ub) : SORT_TILE;
+            __syncthreads();
+            for (int u = threadIdx.x; u < cnt; u += blockDim.x) tile[u] = words[b0 + ub + u];
+            __syncthreads();
+            if (t < len) {
+                for (int u = 0; u < cnt; ++u) {
+                    int ku = tile[u];
+                    rank += (ku > key) | ((ku == key) & (ub + u < t));
+                }
+            }
+        }
+        if (t < len) {
+            int64_t dst = b0 + rank;
+            words_st[dst] = key;
+            if (perm_bytes == 1) ((uint8_t *)perm)[dst] = (uint8_t)t;
+            else if (perm_bytes == 2) ((uint16_t *)perm)[dst] = (uint16_t)t;
+        }
+    }
+}
+
+__global__ void k_copy_words(int n, const int32_t *__restrict__ w, int32_t *__restrict__ o) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = w[i];
+}
+
+__global__ void k_slice_widths(int64_t S, int n, int C, const int32_t *__restrict__ words_st,
+                               int64_t *__restrict__ slice_words, int *max_width) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    int w = 0;
+    int64_t r0 = k * C, r1 = (r0 + C < n) ? r0 + C : n;
+    for (int64_t r = r0; r < r1; ++r) w = max(w, words_st[r]);
+    slice_words[k] = (int64_t)C * w;
+    atomicMax(max_width, w);
+}
+
+// ---- exclusive scan of int64 (3 phases, recursive on the block sums) ----
+constexpr int SCAN_TPB = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_CHUNK = SCAN_TPB * SCAN_ITEMS;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *warp_sums,
+                                                          long long &total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        long long s = (lane < nw) ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < nw) warp_sums[lane] = s;  // inclusive warp prefix
+    }
+    __syncthreads();
+    long long before = (wid > 0) ? warp_sums[wid - 1] : 0;
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + inc - v;
+}
+
+__global__ void k_scan_block_sums(int64_t S, const int64_t *__restrict__ in,
+                                  int64_t *__restrict__ sums) {
+    __shared__ long long ws[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    long long v = 0;
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < S) v += in[base + q];
+    long long total;
+    block_exclusive_scan(v, ws, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// out[i] = carry[block] + exclusive prefix inside the block; out[S] = total.
+__global__ void k_scan_apply(int64_t S, const int64_t *__restrict__ in,
+                             const int64_t *__restrict__ carry, int64_t *__restrict__ out) {
+    __shared__ long long ws[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    long long v[SCAN_ITEMS], s = 0;
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v[q] = (base + q < S) ? in[base + q] : 0;
+        s += v[q];
+    }
+    long long total;
+    long long pre = block_exclusive_scan(s, ws, total) + (carry ? carry[blockIdx.x] : 0);
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < S) out[base + q] = pre;
+        pre += v[q];
+    }
+    if (base < S && base + SCAN_ITEMS >= S) out[S] = pre;  // thread holding the last item
+}
+
+packsell_status scan_exclusive(const int64_t *in, int64_t *out, int64_t S, cudaStream_t s) {
+    if (S <= 0) {
+        PS_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return PACKSELL_OK;
+    }
+    int64_t B = (S + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (B == 1) {
+        k_scan_apply<<<1, SCAN_TPB, 0, s>>>(S, in, nullptr, out);
+        PS_LAUNCH_CHECK("k_scan_apply");
+        return PACKSELL_OK;
+    }
+    int64_t *sums = nullptr, *carry = nullptr;
+    PS_CUDA(cudaMallocAsync((void **)&sums, sizeof(int64_t) * B, s));
+    PS_CUDA(cudaMallocAsync((void **)&carry, sizeof(int64_t) * (B + 1), s));
+    k_scan_block_sums<<<(unsigned)B, SCAN_TPB, 0, s>>>(S, in, sums);
+    PS_LAUNCH_CHECK("k_scan_block_sums");
+    packsell_status st = scan_exclusive(sums, carry, B, s);
+    if (st != PACKSELL_OK) return st;
+    k_scan_apply<<<(unsigned)B, SCAN_TPB, 0, s>>>(S, in, carry, out);
+    PS_LAUNCH_CHECK("k_scan_apply");
+    PS_CUDA(cudaFreeAsync(sums, s));
+    PS_CUDA(cudaFreeAsync(carry, s));
+    return PACKSELL_OK;
+}
+
+// Scatter one storage row per thread into the column-major slice layout:
+// word j of storage row i sits at offset[k] + j*C + l (k = i / C, l = i % C).
+// Threads past n (phantom rows of the last slice) write padding only.
+__global__ void k_scatter_packed(int n, int64_t rows_total, int C, int sigma, long long k_left_user,
+                                 const unsigned long long *kl, int D,
+                                 const int64_t *__restrict__ rowptr,
+                                 const int32_t *__restrict__ col,
+                                 const uint32_t *__restrict__ field, const void *perm,
+                                 int perm_bytes, const int64_t *__restrict__ offset,
+                                 uint32_t *__restrict__ pack) {
+    int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ii >= rows_total) return;
+    int i = (int)ii;
+    int64_t k = ii / C;
+    int l = (int)(ii - k * C);
+    int64_t s = offset[k];
+    int64_t w = (offset[k + 1] - s) / C;
+    uint32_t *dst = pack + s + l;
+    int64_t j = 0;
+    if (i < n) {
+        int r = orig_row(i, sigma, perm, perm_bytes);
+        long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
+        long long lim = 1ll << D;
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+            long long d = (long long)col[p] - prev;
+            if (d >= lim) {
+                dst[j * C] = (uint32_t)d << 1;  // dummy: flag 0, 31-bit delta
+                ++j;
+                d = 0;
+            }
+            dst[j * C] = field[p] | ((uint32_t)d << 1) | 1u;
+            ++j;
+            prev = col[p];
+        }
+    }
+    for (; j < w; ++j) dst[j * C] = 0u;
+}
+
+template <typename TO, typename TI>
+__global__ void k_scatter_sell(int n, int64_t rows_total, int C, int sigma,
+                               const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                               const TI *__restrict__ val_in, const void *perm, int perm_bytes,
+                               const int64_t *__restrict__ offset, TO *__restrict__ val,
+                               int32_t *__restrict__ colo) {
+    int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ii >= rows_total) return;
+    int i = (int)ii;
+    int64_t k = ii / C;
+    int l = (int)(ii - k * C);
+    int64_t s = offset[k];
+    int64_t w = (offset[k + 1] - s) / C;
+    int64_t j = 0;
+    int last = 0;
+    if (i < n) {
+        int r = orig_row(i, sigma, perm, perm_bytes);
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p, ++j) {
+            val[s + j * C + l] = (TO)val_in[p];
+            last = col[p];
+            colo[s + j * C + l] = last;
+        }
+    }
+    for (; j < w; ++j) {  // padding: zero value at a valid column
+        val[s + j * C + l] = (TO)0;
+        colo[s + j * C + l] = last;
+    }
+}
+
+const char *status_text(int code) {
+    switch (code) {
+        case PACKSELL_ERR_INVALID_ARG: return "invalid row pointer or k_left below the bandwidth";
+        case PACKSELL_ERR_UNSORTED: return "columns not strictly increasing";
+        case PACKSELL_ERR_NONFINITE: return "non-finite value";
+        case PACKSELL_ERR_RANGE: return "column out of range or value overflows the format";
+        default: return "error";
+    }
+}
+
+struct Temps {
+    cudaStream_t s;
+    void *ptrs[16] = {};
+    int n = 0;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync((void **)p, std::max<size_t>(bytes, 16), s);
+        if (e == cudaSuccess) ptrs[n++] = *p;
+        return e;
+    }
+    ~Temps() {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], s);
+    }
+};
+
+void free_matrix_arrays(Matrix *A) {
+    cudaFree(A->pack);
+    cudaFree(A->val);
+    cudaFree(A->col);
+    cudaFree(A->offset);
+    cudaFree(A->perm);
+    cudaFree(A->rowptr);
+}
+
+}  // namespace
+
+packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int64_t nnz,
+                            const int64_t *rowptr, const int32_t *col, const void *val,
+                            int val_is_f64, cudaStream_t s, Matrix **out) {
+    const int fmt = p.format;
+    if (!out) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: out is NULL");
+    *out = nullptr;
+    if (!is_packed(fmt) && !is_sell(fmt))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: unknown format");
+    if (p.C < 1 || p.C > 1024) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: C must be in [1, 1024]");
+    if (p.sigma < 1 || p.sigma > 65536)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: sigma must be in [1, 65536]");
+    if (fmt == PACKSELL_FMT_FP16 && p.D != 15)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: FP16 needs D = 15");
+    if (fmt == PACKSELL_FMT_E8MY && (p.D < 1 || p.D > 22))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: E8MY needs D in [1, 22]");
+    if (n < 0 || m < 0 || nnz < 0 || n >= (1ll << 31) || m >= (1ll << 31))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: n and m must be in [0, 2^31)");
+    if (!rowptr || (nnz > 0 && (!col || !val)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: NULL array");
+    if (p.k_left < -1) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: k_left < -1");
+
+    const bool packed = is_packed(fmt);
+    const int D = packed ? p.D : 31;
+    const int64_t S = (n + p.C - 1) / p.C;
+    const int perm_bytes = (p.sigma == 1) ? 0 : (p.sigma <= 256 ? 1 : 2);
+
+    Matrix *A = new Matrix();
+    A->n = n;
+    A->m = m;
+    A->nnz = nnz;
+    A->p = p;
+    A->n_slices = S;
+    A->perm_bytes = perm_bytes;
+    cudaGetDevice(&A->device);
+    auto bail = [&](packsell_status st) {
+        free_matrix_arrays(A);
+        delete A;
+        return st;
+    };
+
+    {
+        Temps T(s);
+        DevStatus *st = nullptr;
+        unsigned long long *kl = nullptr, *total = nullptr;
+        int *maxw = nullptr;
+        uint32_t *field = nullptr;
+        int32_t *words = nullptr, *words_st = nullptr;
+        int64_t *slice_words = nullptr;
+        cudaError_t e = cudaSuccess;
+        if ((e = T.get(&st, sizeof(DevStatus))) || (e = T.get(&kl, 8)) || (e = T.get(&total, 8)) ||
+            (e = T.get(&maxw, 4)) || (e = T.get(&words, 4 * (size_t)n)) ||
+            (e = T.get(&words_st, 4 * (size_t)n)) || (e = T.get(&slice_words, 8 * (size_t)S)) ||
+            (packed && (e = T.get(&field, 4 * (size_t)nnz))))
+            return bail(e == cudaErrorMemoryAllocation
+                            ? fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: temporaries")
+                            : cuda_fail(e, "cudaMallocAsync"));
+        cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+        cudaMemsetAsync(kl, 0, 8, s);
+        cudaMemsetAsync(total, 0, 8, s);
+        cudaMemsetAsync(maxw, 0, 4, s);
+        if (cudaMalloc(&A->offset, sizeof(int64_t) * (S + 1)) != cudaSuccess ||
+            (perm_bytes && cudaMalloc(&A->perm, (size_t)perm_bytes * n) != cudaSuccess) ||
+            (p.keep_rowptr && cudaMalloc(&A->rowptr, sizeof(int64_t) * (n + 1)) != cudaSuccess))
+            return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: matrix arrays"));
+
+        k_check_rows<<<blocks_for(n), TPB, 0, s>>>((int)n, m, nnz, rowptr, col, kl, st);
+        if (packed && nnz > 0) {
+            int qb = blocks_for(nnz);
+            qb = std::min(qb, 152 * 64);
+            if (val_is_f64)
+                k_quantize<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, fmt, D, field, st);
+            else
+                k_quantize<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, fmt, D, field, st);
+        }
+        if (n > 0) {
+            k_count_words<<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, col, p.sigma, p.k_left, kl,
+                                                       D, packed ? 1 : 0, words, total, st);
+            if (p.sigma > 1) {
+                int64_t nb = (n + p.sigma - 1) / p.sigma;
+                int tpb = std::min(1024, ((std::min(p.sigma, 1024) + 31) / 32) * 32);
+                k_sigma_sort<<<(unsigned)nb, tpb, 0, s>>>((int)n, p.sigma, words, A->perm,
+                                                          perm_bytes, words_st);
+            } else {
+                k_copy_words<<<blocks_for(n), TPB, 0, s>>>((int)n, words, words_st);
+            }
+            k_slice_widths<<<blocks_for(S), TPB, 0, s>>>(S, (int)n, p.C, words_st, slice_words,
+                                                        maxw);
+        }
+        PS_LAUNCH_CHECK("packsell_encode: kernels");
+        packsell_status sst = scan_exclusive(slice_words, A->offset, S, s);
+        if (sst != PACKSELL_OK) return bail(sst);
+        if (p.keep_rowptr)
+            cudaMemcpyAsync(A->rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
+
+        DevStatus hst{};
+        unsigned long long hkl = 0, htotal = 0;
+        int hmaxw = 0;
+        int64_t nw = 0;
+        cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hkl, kl, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&htotal, total, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hmaxw, maxw, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&nw, A->offset + S, 8, cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "packsell_encode: synchronize"));
+        if (hst.code != 0)
+            return bail(fail((packsell_status)hst.code,
+                             std::string("packsell_encode: ") + status_text(hst.code) +
+                                 " (index " + std::to_string(hst.index) + ")"));
+        A->p.k_left = p.k_left >= 0 ? p.k_left : (int64_t)hkl;
+        A->n_words = nw;
+        A->n_dummies = packed ? (int64_t)htotal - nnz : 0;
+        A->n_pad = nw - (int64_t)htotal;
+        A->max_width = hmaxw;
+
+        if (packed) {
+            if (cudaMalloc(&A->pack, sizeof(uint32_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
+                return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
+            int64_t rows_total = S * p.C;
+            if (rows_total > 0)
+                k_scatter_packed<<<blocks_for(rows_total), TPB, 0, s>>>(
+                    (int)n, rows_total, p.C, p.sigma, A->p.k_left, kl, D, rowptr, col, field,
+                    A->perm, perm_bytes, A->offset, A->pack);
+        } else {
+            size_t vb = fmt == PACKSELL_FMT_SELL_F64 ? 8 : 4;
+            if (cudaMalloc(&A->val, vb * std::max<int64_t>(nw, 1)) != cudaSuccess ||
+                cudaMalloc(&A->col, 4 * std::max<int64_t>(nw, 1)) != cudaSuccess)
+                return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: value arrays"));
+            int64_t rows_total = S * p.C;
+            if (rows_total > 0) {
+                int g = blocks_for(rows_total);
+                if (fmt == PACKSELL_FMT_SELL_F64) {
+                    if (val_is_f64)
+                        k_scatter_sell<double, double><<<g, TPB, 0, s>>>(
+                            (int)n, rows_total, p.C, p.sigma, rowptr, col, (const double *)val,
+                            A->perm, perm_bytes, A->offset, (double *)A->val, A->col);
+                    else
+                        k_scatter_sell<double, float><<<g, TPB, 0, s>>>(
+                            (int)n, rows_total, p.C, p.sigma, rowptr, col, (const float *)val,
+                            A->perm, perm_bytes, A->offset, (double *)A->val, A->col);
+                } else {
+                    if (val_is_f64)
+                        k_scatter_sell<float, double><<<g, TPB, 0, s>>>(
+                            (int)n, rows_total, p.C, p.sigma, rowptr, col, (const double *)val,
+                            A->perm, perm_bytes, A->offset, (float *)A->val, A->col);
+                    else
+                        k_scatter_sell<float, float><<<g, TPB, 0, s>>>(
+                            (int)n, rows_total, p.C, p.sigma, rowptr, col, (const float *)val,
+                            A->perm, perm_bytes, A->offset, (float *)A->val, A->col);
+                }
+            }
+        }
+        PS_LAUNCH_CHECK("packsell_encode: scatter");
+        // Temps are released (stream-ordered) here; they outlive the scatter.
+    }
+    *out = A;
+    return PACKSELL_OK;
+}
+
+void destroy_matrix(Matrix *A) {
+    if (!A) return;
+    free_matrix_arrays(A);
+    delete A;
+}
+
+// ---- validation of imported matrices ----
+namespace {
+template <bool PACKED>
+__global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left, int D,
+                           const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                           const int32_t *__restrict__ colv, const void *perm, int perm_bytes,
+                           unsigned long long *count, DevStatus *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (perm_bytes) {
+        int q = perm_bytes == 1 ? ((const uint8_t *)perm)[i] : ((const uint16_t *)perm)[i];
+        int b = (i / sigma) * sigma;
+        if (q >= sigma || b + q >= n) {
+            dev_fail(st, PACKSELL_ERR_CORRUPT, i);
+            return;
+        }
+    }
+    int64_t k = i / C;
+    int l = i - (int)(k * C);
+    int64_t s = offset[k], e = offset[k + 1];
+    if (s < 0 || e < s || (e - s) % C) {
+        dev_fail(st, PACKSELL_ERR_CORRUPT, i);
+        return;
+    }
+    int64_t w = (e - s) / C;
+    unsigned long long cnt = 0;
+    if (PACKED) {
+        long long c = left_offset(i, sigma, k_left);
+        uint32_t dmask = (1u << D) - 1u;
+        for (int64_t j = 0; j < w; ++j) {
+            uint32_t wd = pack[s + j * C + l];
+            uint32_t flag = wd & 1u;
+            c += (wd >> 1) & (flag ? dmask : 0x7fffffffu);
+            bool pad = wd == 0;
+            if (!pad && c >= m) {
+                dev_fail(st, PACKSELL_ERR_CORRUPT, s + j * C + l);
+                return;
+            }
+            cnt += flag;
+        }
+    } else {
+        for (int64_t j = 0; j < w; ++j) {
+            int c = colv[s + j * C + l];
+            if (c < 0 || c >= m) {
+                dev_fail(st, PACKSELL_ERR_CORRUPT, s + j * C + l);
+                return;
+            }
+        }
+    }
+    if (cnt) atomicAdd(count, cnt);
+}
+}  // namespace
+
+packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
+    Temps T(s);
+    DevStatus *st = nullptr;
+    unsigned long long *cnt = nullptr;
+    PS_CUDA(T.get(&st, sizeof(DevStatus)));
+    PS_CUDA(T.get(&cnt, 8));
+    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    cudaMemsetAsync(cnt, 0, 8, s);
+    if (A.n > 0) {
+        int g = blocks_for(A.n);
+        if (is_packed(A.p.format))
+            k_validate<true><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left, A.p.D,
+                                               A.offset, A.pack, nullptr, A.perm, A.perm_bytes,
+                                               cnt, st);
+        else
+            k_validate<false><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left, 31,
+                                                A.offset, nullptr, A.col, A.perm, A.perm_bytes,
+                                                cnt, st);
+        PS_LAUNCH_CHECK("k_validate");
+    }
+    DevStatus hst{};
+    unsigned long long hc = 0;
+    cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&hc, cnt, 8, cudaMemcpyDeviceToHost, s);
+    PS_CUDA(cudaStreamSynchronize(s));
+    if (hst.code)
+        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad word, column or perm at index " +
+                                              std::to_string(hst.index));
+    if (is_packed(A.p.format) && (int64_t)hc != A.nnz)
+        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: value words do not match nnz");
+    return PACKSELL_OK;
+}
+
+}  // namespace packsell

@@ -1,0 +1,74 @@
+// Internal declarations of the PackSELL CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "packsell.h"
+
+namespace packsell {
+
+// Device status word written by kernels that validate input. The first
+// kernel to find a problem records its code and the offending index.
+struct DevStatus {
+    int code;      // packsell_status, 0 = fine
+    int pad;
+    long long index;
+};
+
+struct Matrix {
+    int64_t n = 0, m = 0, nnz = 0;
+    packsell_params p{};
+    int64_t n_slices = 0, n_words = 0, n_dummies = 0, n_pad = 0;
+    int32_t max_width = 0;
+    int32_t perm_bytes = 0;
+    int device = 0;
+    // device arrays
+    uint32_t *pack = nullptr;  // PackSELL words
+    void *val = nullptr;       // SELL values (float / double)
+    int32_t *col = nullptr;    // SELL columns
+    int64_t *offset = nullptr; // n_slices + 1
+    void *perm = nullptr;      // n entries of perm_bytes
+    int64_t *rowptr = nullptr; // optional copy of the CSR row pointer
+};
+
+inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
+inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PACKSELL_FMT_SELL_F64; }
+
+// thread-local error message
+packsell_status fail(packsell_status st, const std::string &msg);
+packsell_status cuda_fail(cudaError_t e, const char *where);
+void clear_error();
+
+int64_t matrix_bytes(const Matrix &A);
+
+// encode.cu
+packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int64_t nnz,
+                            const int64_t *rowptr, const int32_t *col, const void *val,
+                            int val_is_f64, cudaStream_t s, Matrix **out);
+packsell_status validate_impl(const Matrix &A, cudaStream_t s);
+
+// spmv.cu
+packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_t s);
+packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaStream_t s);
+packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, float *Y,
+                          int64_t ldy, cudaStream_t s);
+packsell_status spmv_t_impl(const Matrix &A, const float *dy, float *dx, cudaStream_t s);
+packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u, const float *v,
+                                   float *out, cudaStream_t s);
+
+}  // namespace packsell
+
+#define PS_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return packsell::cuda_fail(e_, #call);   \
+    } while (0)
+
+#define PS_LAUNCH_CHECK(where)                                          \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return packsell::cuda_fail(e_, where);   \
+    } while (0)

@@ -1,0 +1,278 @@
+"""Python binding of the PackSELL C ABI (``include/packsell.h``).
+
+Argument marshalling only: every function here checks tensor devices, dtypes
+and shapes, passes raw device pointers and the current CUDA stream to the
+library, and turns a non-zero status into :class:`PackSELLError`. Every
+computation runs in ``libpacksell.so``'s CUDA kernels; there is no CPU path,
+and a missing library raises at the first call.
+
+Function names follow the C ABI (``packsell_encode``, ``packsell_spmv`` ...).
+PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpacksell.so")
+
+FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64 = 1, 2, 3, 4
+_FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
+            "sell_f64": FMT_SELL_F64}
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
+          6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT"}
+
+
+class PackSELLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int32), ("sigma", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("format", ctypes.c_int32), ("explicit_perm", ctypes.c_int32),
+                ("keep_rowptr", ctypes.c_int32), ("k_left", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("params", Params), ("n_slices", ctypes.c_int64), ("n_words", ctypes.c_int64),
+                ("n_dummies", ctypes.c_int64), ("n_pad", ctypes.c_int64),
+                ("max_width", ctypes.c_int32), ("perm_bytes", ctypes.c_int32),
+                ("bytes", ctypes.c_int64), ("pack", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("offset", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
+
+
+_lib = None
+
+# symbol -> (restype, argtypes)
+_P, _I64, _I32, _F32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+SIGNATURES = {
+    "packsell_params_default": (None, [_P]),
+    "packsell_version": (ctypes.c_char_p, []),
+    "packsell_last_error": (ctypes.c_char_p, []),
+    "packsell_encode": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _I32, _P, _P]),
+    "packsell_destroy": (ctypes.c_int, [_P]),
+    "packsell_get_info": (ctypes.c_int, [_P, _P]),
+    "packsell_export": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_import": (ctypes.c_int, [_P, ctypes.c_size_t, _P, _P]),
+    "packsell_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_spmv_f64": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_spmm": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _I64, _P]),
+    "packsell_spmv_transpose": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_pattern_outer": (ctypes.c_int, [_P, _F32, _P, _P, _P, _P]),
+}
+
+
+def lib():
+    """Load ``libpacksell.so`` (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2604_13433_gb300.build` "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise PackSELLError(code, lib().packsell_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str, numel=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class PackSELLMatrix:
+    """Owner of an encoded matrix (a ``packsell_matrix*``)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        info = Info()
+        _check(lib().packsell_get_info(self._h, ctypes.byref(info)))
+        self.info = info
+        self.n, self.m, self.nnz = info.n, info.m, info.nnz
+        p = info.params
+        self.C, self.sigma, self.D, self.format = p.C, p.sigma, p.D, p.format
+        self.explicit_perm = bool(p.explicit_perm)
+        self.k_left = p.k_left
+        self.n_slices, self.n_words = info.n_slices, info.n_words
+        self.n_dummies, self.n_pad = info.n_dummies, info.n_pad
+        self.max_width, self.perm_bytes, self.bytes = info.max_width, info.perm_bytes, info.bytes
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().packsell_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        return (f"PackSELLMatrix(n={self.n}, m={self.m}, nnz={self.nnz}, C={self.C}, "
+                f"sigma={self.sigma}, D={self.D}, format={self.format}, words={self.n_words})")
+
+
+def packsell_version() -> str:
+    return lib().packsell_version().decode()
+
+
+def packsell_encode(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, n: int, m: int,
+                    *, C: int = 32, sigma: int = 256, D: int = 15, fmt="fp16",
+                    explicit_perm: bool = False, keep_rowptr: bool = False, k_left: int = -1,
+                    stream=None) -> PackSELLMatrix:
+    """Encode a CSR matrix held in CUDA tensors (rowptr int64 [n+1], col int32
+    [nnz], val float32/float64 [nnz]). Synchronises the stream once."""
+    fmt_code = _FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    nnz = col.numel()
+    prm = Params(C, sigma, D, fmt_code, int(explicit_perm), int(keep_rowptr), k_left)
+    if val.dtype not in (torch.float32, torch.float64):
+        raise TypeError("val must be float32 or float64")
+    h = ctypes.c_void_p()
+    _check(lib().packsell_encode(
+        ctypes.byref(prm), n, m, nnz, _dev(rowptr, torch.int64, "rowptr", n + 1),
+        _dev(col, torch.int32, "col") if nnz else None,
+        _dev(val, val.dtype, "val", nnz) if nnz else None, int(val.dtype == torch.float64),
+        _stream(stream), ctypes.byref(h)))
+    return PackSELLMatrix(h.value)
+
+
+def packsell_encode_csr(csr, device="cuda", **kw) -> PackSELLMatrix:
+    """Encode a host CSR (``inputs.CSR``): copy its arrays to the device first."""
+    rp = torch.from_numpy(csr.rowptr).to(device)
+    cl = torch.from_numpy(csr.col).to(device)
+    vl = torch.from_numpy(csr.val).to(device)
+    return packsell_encode(rp, cl, vl, csr.n, csr.m, **kw)
+
+
+def packsell_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """y = A x (float32)."""
+    if y is None:
+        y = torch.empty(A.n, dtype=torch.float32, device=x.device)
+    _check(lib().packsell_spmv(A.handle, _dev(x, torch.float32, "x", A.m),
+                               _dev(y, torch.float32, "y", A.n), _stream(stream)))
+    return y
+
+
+def packsell_spmv_f64(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """y = A x (float64, SELL_F64 matrices)."""
+    if y is None:
+        y = torch.empty(A.n, dtype=torch.float64, device=x.device)
+    _check(lib().packsell_spmv_f64(A.handle, _dev(x, torch.float64, "x", A.m),
+                                   _dev(y, torch.float64, "y", A.n), _stream(stream)))
+    return y
+
+
+def packsell_spmm(A: PackSELLMatrix, X: torch.Tensor, Y: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Y = A X with X row-major [m, k] (float32)."""
+    if X.dim() != 2 or X.shape[0] != A.m or X.stride(1) != 1:
+        raise ValueError("X must be [m, k] with unit column stride")
+    k = X.shape[1]
+    if Y is None:
+        Y = torch.empty((A.n, k), dtype=torch.float32, device=X.device)
+    if Y.shape != (A.n, k) or Y.stride(1) != 1:
+        raise ValueError("Y must be [n, k] with unit column stride")
+    if X.dtype != torch.float32 or Y.dtype != torch.float32 or not X.is_cuda or not Y.is_cuda:
+        raise TypeError("X and Y must be float32 CUDA tensors")
+    _check(lib().packsell_spmm(A.handle, k, X.data_ptr(), X.stride(0), Y.data_ptr(), Y.stride(0),
+                               _stream(stream)))
+    return Y
+
+
+def packsell_spmv_transpose(A: PackSELLMatrix, dy: torch.Tensor, dx: torch.Tensor | None = None,
+                            stream=None) -> torch.Tensor:
+    """dx = A^T dy (float32)."""
+    if dx is None:
+        dx = torch.empty(A.m, dtype=torch.float32, device=dy.device)
+    _check(lib().packsell_spmv_transpose(A.handle, _dev(dy, torch.float32, "dy", A.n),
+                                         _dev(dx, torch.float32, "dx", A.m), _stream(stream)))
+    return dx
+
+
+def packsell_pattern_outer(A: PackSELLMatrix, alpha: float, u: torch.Tensor, v: torch.Tensor,
+                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """out[q] = alpha * u_i * v_j for each stored nonzero a_ij (CSR order)."""
+    if out is None:
+        out = torch.empty(A.nnz, dtype=torch.float32, device=u.device)
+    _check(lib().packsell_pattern_outer(A.handle, float(alpha), _dev(u, torch.float32, "u", A.n),
+                                        _dev(v, torch.float32, "v", A.m),
+                                        _dev(out, torch.float32, "out", A.nnz), _stream(stream)))
+    return out
+
+
+def packsell_export(A: PackSELLMatrix, stream=None) -> bytes:
+    size = ctypes.c_size_t(0)
+    _check(lib().packsell_export(A.handle, None, ctypes.byref(size), _stream(stream)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().packsell_export(A.handle, buf, ctypes.byref(size), _stream(stream)))
+    return buf.raw[: size.value]
+
+
+def packsell_import(blob: bytes, stream=None) -> PackSELLMatrix:
+    h = ctypes.c_void_p()
+    _check(lib().packsell_import(blob, len(blob), _stream(stream), ctypes.byref(h)))
+    return PackSELLMatrix(h.value)
+
+
+def packsell_arrays(A: PackSELLMatrix):
+    """Host copies of the encoded arrays: dict with offset, perm, and pack
+    (PackSELL) or val/col (SELL), parsed from the export blob."""
+    import numpy as np
+
+    blob = packsell_export(A)
+    hdr = 8 + 3 * 8 + ctypes.sizeof(Params) + 4 * 8 + 2 * 4
+    pos = hdr
+    S = A.n_slices
+    out = {"offset": np.frombuffer(blob, np.int64, S + 1, pos)}
+    pos += 8 * (S + 1)
+    if A.perm_bytes:
+        dt = np.uint8 if A.perm_bytes == 1 else np.uint16
+        out["perm"] = np.frombuffer(blob, dt, A.n, pos).astype(np.int32)
+        pos += A.perm_bytes * A.n
+    else:
+        out["perm"] = np.zeros(A.n, np.int32)
+    if A.format in (FMT_FP16, FMT_E8MY):
+        out["pack"] = np.frombuffer(blob, np.uint32, A.n_words, pos)
+    else:
+        dt = np.float64 if A.format == FMT_SELL_F64 else np.float32
+        out["val"] = np.frombuffer(blob, dt, A.n_words, pos)
+        pos += np.dtype(dt).itemsize * A.n_words
+        out["col"] = np.frombuffer(blob, np.int32, A.n_words, pos)
+    return out

@@ -1,0 +1,136 @@
+"""GPU encoder vs the oracle: offsets, perm and every packed word bit-exact
+(§4.1-§4.3), plus error statuses and export/import (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_13433_gb300 import inputs as I
+
+from _gpu import FMT, P, assert_same_encoding, dev, encode_gpu, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # n, m, density, C, sigma, fmt, D, empty-row fraction, long gaps
+    (1, 1, 1.0, 32, 256, "fp16", 15, 0.0, False),
+    (37, 53, 0.2, 32, 256, "fp16", 15, 0.1, False),
+    (100, 100, 0.05, 4, 8, "e8my", 1, 0.2, True),
+    (200, 70, 0.3, 8, 16, "e8my", 2, 0.0, True),
+    (130, 400, 0.02, 32, 1, "e8my", 7, 0.3, True),
+    (1000, 1000, 0.01, 32, 256, "e8my", 11, 0.05, True),
+    (300, 90, 0.1, 1, 300, "e8my", 3, 0.0, True),
+    (64, 5000, 0.01, 16, 32, "e8my", 22, 0.0, True),
+    (2000, 3000, 0.005, 64, 512, "fp16", 15, 0.1, True),
+    (5000, 5000, 0.002, 32, 4096, "e8my", 9, 0.02, True),
+    (3000, 300, 0.02, 1024, 3000, "e8my", 5, 0.0, True),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_encode_matches_oracle(case):
+    need_gpu()
+    n, m, dens, C, sigma, fmt, D, empty, gaps = case
+    csr = I.random_csr(n, m, dens, seed=n + 7 * m, empty_rows=empty, long_gaps=gaps)
+    enc = O.encode(csr, C=C, sigma=sigma, D=D, fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, C=C, sigma=sigma, D=D)
+    assert_same_encoding(A, enc)
+
+
+@pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 15), ("e8my", 11), ("e8my", 7),
+                                   ("e8my", 1)])
+def test_encode_stencil27_32(fmt, D):
+    need_gpu()
+    csr = I.stencil27(32, seed=1)
+    enc = O.encode(csr, C=32, sigma=256, D=D, fmt=FMT[fmt])
+    assert_same_encoding(encode_gpu(csr, fmt=fmt, D=D), enc)
+
+
+def test_encode_f64_values_match_oracle():
+    need_gpu()
+    csr = I.poisson7_varcoef(12, seed=2)  # float64 values
+    for fmt, D in (("fp16", 15), ("e8my", 10), ("e8my", 1)):
+        enc = O.encode(csr, C=32, sigma=256, D=D, fmt=FMT[fmt])
+        assert_same_encoding(encode_gpu(csr, fmt=fmt, D=D), enc)
+
+
+def test_encode_config1_and_empty():
+    need_gpu()
+    a = I.poisson5(64)
+    for sigma in (1, 256):
+        A = encode_gpu(a, C=32, sigma=sigma)
+        assert (A.k_left, A.n_words, A.n_dummies, A.n_pad) == (64, 20352, 0, 128)
+        assert_same_encoding(A, O.encode(a, C=32, sigma=sigma))
+    e = I.CSR(n=5, m=7, rowptr=np.zeros(6, np.int64), col=np.zeros(0, np.int32),
+              val=np.zeros(0, np.float32))
+    A = encode_gpu(e, C=4, sigma=2)
+    assert A.n_words == 0 and list(P().packsell_arrays(A)["offset"]) == [0, 0, 0]
+
+
+def test_quantizer_exhaustive_sample():
+    """Every FP32 exponent, many mantissas: GPU value fields equal the oracle's."""
+    need_gpu()
+    rng = np.random.default_rng(0)
+    b = rng.integers(0, 2 ** 32, 400000, dtype=np.uint64).astype(np.uint32)
+    v = b.view(np.float32)
+    v = v[np.isfinite(v) & (np.abs(v) < 6e4)]
+    v = np.concatenate([v, np.float32([0.0, -0.0, 2 ** -24, 2 ** -25, 3 * 2 ** -25, 65504.0])])
+    nnz = v.size
+    # one row per value so each value is stored as a word of its own
+    csr = I.CSR(n=nnz, m=1, rowptr=np.arange(nnz + 1, dtype=np.int64),
+                col=np.zeros(nnz, np.int32), val=v)
+    for fmt, D in (("fp16", 15), ("e8my", 1), ("e8my", 7), ("e8my", 12), ("e8my", 22)):
+        enc = O.encode(csr, C=32, sigma=1, D=D, fmt=FMT[fmt])
+        A = encode_gpu(csr, fmt=fmt, C=32, sigma=1, D=D)
+        assert_same_encoding(A, enc)
+
+
+@pytest.mark.parametrize("kind", ["unsorted", "dup", "range", "fp16_overflow", "nan",
+                                  "k_left", "e8my_overflow"])
+def test_encode_errors(kind):
+    need_gpu()
+    packsell = P()
+    rowptr, col, val, kw = np.array([0, 2]), np.array([1, 3], np.int32), \
+        np.ones(2, np.float32), {}
+    code = {"unsorted": 2, "dup": 2, "range": 4, "fp16_overflow": 4, "nan": 3, "k_left": 1,
+            "e8my_overflow": 4}[kind]
+    if kind == "unsorted":
+        col = np.array([3, 1], np.int32)
+    elif kind == "dup":
+        col = np.array([2, 2], np.int32)
+    elif kind == "range":
+        col = np.array([1, 5], np.int32)
+    elif kind == "fp16_overflow":
+        val = np.array([1.0, 70000.0], np.float32)
+    elif kind == "nan":
+        val = np.array([1.0, np.nan], np.float32)
+    elif kind == "k_left":
+        rowptr, col, val = np.array([0, 1, 2]), np.array([1, 0], np.int32), np.ones(2, np.float32)
+        kw = {"k_left": 0, "sigma": 1}
+    elif kind == "e8my_overflow":
+        val = np.array([1.0, np.finfo(np.float32).max], np.float32)
+        kw = {"fmt": "e8my", "D": 1}
+    n = rowptr.size - 1
+    with pytest.raises(packsell.PackSELLError) as e:
+        packsell.packsell_encode(dev(rowptr.astype(np.int64)), dev(col), dev(val), n, 5, **kw)
+    assert e.value.code == code
+
+
+def test_export_import_roundtrip_and_corruption():
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(500, 600, 0.02, seed=5, long_gaps=True)
+    A = encode_gpu(csr, fmt="e8my", D=4, C=32, sigma=64)
+    blob = packsell.packsell_export(A)
+    B = packsell.packsell_import(blob)
+    assert (B.n, B.m, B.nnz, B.n_words, B.k_left) == (A.n, A.m, A.nnz, A.n_words, A.k_left)
+    x = dev(I.uniform(600, seed=1))
+    assert torch.equal(packsell.packsell_spmv(A, x), packsell.packsell_spmv(B, x))
+    # a dummy word whose delta jumps past the last column must be rejected
+    hdr = len(blob) - 4 * A.n_words
+    words = np.frombuffer(blob, np.uint32, A.n_words, hdr).copy()
+    words[int(np.nonzero(words & 1)[0][0])] = np.uint32(0x7FFFFFFE)
+    with pytest.raises(packsell.PackSELLError) as e:
+        packsell.packsell_import(blob[:hdr] + words.tobytes())
+    assert e.value.code == 9
+    with pytest.raises(packsell.PackSELLError):
+        packsell.packsell_import(blob[: len(blob) // 2])

@@ -1,0 +1,157 @@
+"""GPU products vs the oracle (through the C ABI).
+
+The thread-per-row SpMV sums each row in stored order with FP32 fused
+multiply-adds, so it must equal the oracle's FP32 twin (csr_spmv_fma_f32 on
+the quantised values) bit for bit; it is also held to the FP32 forward error
+bound against the FP64 oracle on the same quantised values (§4.4, Eq. 1).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_13433_gb300 import inputs as I
+
+from _gpu import FMT, P, dev, encode_gpu, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6  # ||y - y_oracle||_inf / ||y_oracle||_inf for FP32 accumulation
+
+
+def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0):
+    packsell = P()
+    enc = O.encode(csr, C=C, sigma=sigma, D=D, fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, C=C, sigma=sigma, D=D, explicit_perm=explicit)
+    x = I.uniform(csr.m, seed=seed)
+    y = packsell.packsell_spmv(A, dev(x)).cpu().numpy()
+    twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), x)
+    ref = O.csr_spmv_f64(csr, enc.deq, x.astype(np.float64))
+    if explicit:
+        rows = O.storage_rows(enc)
+        twin, ref = twin[rows], ref[rows]
+    assert np.array_equal(y.view(np.uint32), twin.view(np.uint32)), \
+        f"{int((y != twin).sum())} rows differ from the FP32 twin"
+    bound = O.spmv_error_bound(csr, enc.deq, x, enc.words)
+    if explicit:
+        bound = bound[O.storage_rows(enc)]
+    assert np.all(np.abs(y - ref) <= bound)
+    if np.abs(ref).max() > 0:
+        assert np.abs(y - ref).max() / np.abs(ref).max() <= REL_TOL
+    return A, enc, x, y
+
+
+CASES = [
+    (33, 47, 0.2, 32, 256, "fp16", 15),
+    (1000, 1000, 0.01, 32, 256, "e8my", 11),
+    (777, 1500, 0.02, 32, 64, "e8my", 2),
+    (4099, 4099, 0.003, 32, 256, "e8my", 1),
+    (300, 90, 0.1, 8, 16, "e8my", 5),
+    (2000, 3000, 0.005, 64, 512, "fp16", 15),
+    (130, 400, 0.02, 32, 1, "e8my", 7),
+    (64, 5000, 0.01, 16, 32, "e8my", 22),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_spmv_random(case):
+    need_gpu()
+    n, m, dens, C, sigma, fmt, D = case
+    csr = I.random_csr(n, m, dens, seed=n, empty_rows=0.1, long_gaps=True)
+    check_spmv(csr, fmt, D, C, sigma)
+
+
+@pytest.mark.parametrize("explicit", [False, True])
+def test_spmv_poisson5_64(explicit):
+    need_gpu()
+    a = I.poisson5(64)
+    A, enc, x, y = check_spmv(a, "fp16", 15, sigma=1, explicit=explicit)
+    if not explicit:  # closed form: 4 x_i minus the four neighbours
+        g = np.pad(x.astype(np.float64).reshape(64, 64), 1)
+        ref = 4 * g[1:-1, 1:-1] - g[:-2, 1:-1] - g[2:, 1:-1] - g[1:-1, :-2] - g[1:-1, 2:]
+        assert np.allclose(y, ref.ravel(), rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 15), ("e8my", 11), ("e8my", 7)])
+def test_spmv_stencil27_48(fmt, D):
+    need_gpu()
+    check_spmv(I.stencil27(48, seed=3), fmt, D)
+
+
+def test_spmv_stencil27_128_full_size():
+    """The 2.1M-row, 55.7M-nonzero HPCG_7_7_7 pattern at the benchmark's
+    launch configuration: all rows bitwise against the FP32 twin."""
+    need_gpu()
+    check_spmv(I.stencil27(128, seed=0), "fp16", 15)
+
+
+def test_spmv_padding_dummies_do_not_touch_x():
+    """Padding and dummy words read no x: NaN in x at columns no row uses
+    (and at the dummy targets' neighbours) leaves y finite (§4.3 reading)."""
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(200, 400, 0.02, seed=11, long_gaps=True)
+    used = np.zeros(400, bool)
+    used[csr.col] = True
+    x = I.uniform(400, seed=2)
+    x[~used] = np.nan
+    A = encode_gpu(csr, fmt="e8my", D=3, C=32, sigma=32)
+    assert A.n_dummies > 0 and A.n_pad > 0
+    y = packsell.packsell_spmv(A, dev(x)).cpu().numpy()
+    assert np.all(np.isfinite(y))
+
+
+def test_sell_f32_and_f64():
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(3000, 2500, 0.004, seed=4, empty_rows=0.05)
+    x = I.uniform(2500, seed=5)
+    A = encode_gpu(csr, fmt="sell_f32")
+    y = packsell.packsell_spmv(A, dev(x)).cpu().numpy()
+    twin = O.csr_spmv_fma_f32(csr, csr.val, x)
+    assert np.array_equal(y.view(np.uint32), twin.view(np.uint32))
+    B = encode_gpu(csr, fmt="sell_f64")
+    y64 = packsell.packsell_spmv_f64(B, dev(x.astype(np.float64))).cpu().numpy()
+    ref = O.csr_spmv_f64(csr, csr.val.astype(np.float64), x.astype(np.float64))
+    assert np.allclose(y64, ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("fmt,D,k", [("fp16", 15, 1), ("e8my", 11, 4), ("e8my", 2, 16),
+                                     ("fp16", 15, 64), ("sell_f32", 0, 5)])
+def test_spmm(fmt, D, k):
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(1500, 1200, 0.005, seed=k, empty_rows=0.05, long_gaps=True)
+    A = encode_gpu(csr, fmt=fmt, D=D if D else 15)
+    deq = csr.val.astype(np.float64) if fmt == "sell_f32" else O.encode(
+        csr, D=D, fmt=FMT[fmt]).deq
+    X = np.random.default_rng(k).uniform(-1, 1, (1200, k)).astype(np.float32)
+    Y = packsell.packsell_spmm(A, dev(X)).cpu().numpy()
+    ref = O.csr_spmm_f64(csr, deq, X.astype(np.float64))
+    for r in range(k):  # each column is an SpMV: bitwise equal to the twin
+        twin = O.csr_spmv_fma_f32(csr, deq.astype(np.float32), np.ascontiguousarray(X[:, r]))
+        assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32))
+    assert np.abs(Y - ref).max() <= REL_TOL * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 3), ("sell_f32", 15)])
+def test_transpose_and_pattern_outer(fmt, D):
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(700, 900, 0.01, seed=8, empty_rows=0.05, long_gaps=True)
+    A = encode_gpu(csr, fmt=fmt, D=D, C=32, sigma=64, keep_rowptr=True)
+    deq = csr.val.astype(np.float64) if fmt == "sell_f32" else O.encode(
+        csr, C=32, sigma=64, D=D, fmt=FMT[fmt]).deq
+    dy = I.uniform(700, seed=9)
+    dx = packsell.packsell_spmv_transpose(A, dev(dy)).cpu().numpy()
+    ref = O.csr_spmv_t_f64(csr, deq, dy.astype(np.float64))
+    # FP32 products and atomic sums in any order: |error_j| <= gamma_(c_j + 1)
+    # sum_i |a_ij dy_i| with c_j the nonzeros of column j
+    absum = O.csr_spmv_t_f64(csr, np.abs(deq), np.abs(dy).astype(np.float64))
+    cnt = np.bincount(csr.col, minlength=csr.m) + 1.0
+    u = 2.0 ** -24
+    assert np.all(np.abs(dx - ref) <= cnt * u / (1 - cnt * u) * absum)
+    x = I.uniform(900, seed=10)
+    out = packsell.packsell_pattern_outer(A, -1.0, dev(dy), dev(x)).cpu().numpy()
+    row = np.repeat(np.arange(700), csr.row_lengths())
+    want = (np.float32(-1.0) * dy[row]) * x[csr.col]
+    assert np.array_equal(out.view(np.uint32), want.astype(np.float32).view(np.uint32))
