@@ -50,7 +50,9 @@ typedef enum packsell_status {
     PACKSELL_ERR_NOT_CONVERGED = 6, /* solver hit its iteration limit */
     PACKSELL_ERR_BREAKDOWN = 7,     /* solver: p^T A p <= 0 or a non-finite residual */
     PACKSELL_ERR_NO_MEMORY = 8,     /* device allocation failed */
-    PACKSELL_ERR_CORRUPT = 9        /* imported data fails validation */
+    PACKSELL_ERR_CORRUPT = 9,       /* imported data fails validation */
+    PACKSELL_ERR_TIMEOUT = 10       /* a kernel's bounded wait ran out (see
+                                       packsell_check_status) */
 } packsell_status;
 
 /* Value formats.
@@ -170,6 +172,33 @@ packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, dou
  * of each word feeds k multiply-adds. PackSELL and SELL_F32 matrices. */
 packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X,
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
+
+/* SpMV kernel variants (all compute the same bits):
+ *   0 auto (the plan's or the tuner's choice),
+ *   1 thread-per-row with direct loads (the paper's mapping, §5.1.1),
+ *   2, 3, 4 bulk-staged: every warp streams its contiguous range of slices
+ *     through a circular ring of shared-memory chunks filled by
+ *     cp.async.bulk (TMA engine) and completed on mbarriers; the three differ
+ *     in warps per block, chunks per warp and chunk size (8/4/2 KB, 4/4/2 KB,
+ *     8/2/4 KB). Bulk variants need a PackSELL matrix with C = 32;
+ *   5, 6 thread-per-row with row register prefetch: 16 (5) or 32 (6) words
+ *     of a row are loaded at once before any is decoded (PackSELL matrices,
+ *     C = 32). */
+packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
+
+/* Autotune the SpMV variant for this matrix: time every available variant
+ * (`reps` launches each after a warm-up, CUDA events on `stream`) on the
+ * caller's x [m] and y [n], and make variant 0 run the fastest. Writes y.
+ * Synchronises `stream`. If h_times is not NULL it receives the average
+ * milliseconds per launch of variants 1..6 (0 where unavailable). */
+packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
+                                   float *h_times, void *stream);
+
+/* Read and clear the matrix's device status word (synchronises `stream`).
+ * Returns PACKSELL_ERR_TIMEOUT if a kernel's bounded wait on a shared-memory
+ * stage ran out since the last check (the kernel then skipped the rest of
+ * its work), else PACKSELL_OK. */
+packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Backward (adjoint) products                                              */

@@ -234,7 +234,87 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     }
     packsell_status st = validate_impl(*A, s);
     if (st != PACKSELL_OK) return bail(st);
+    st = plan_spmv(*A, s);
+    if (st != PACKSELL_OK) return bail(st);
     *out = reinterpret_cast<packsell_matrix *>(A);
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
+    clear_error();
+    if (!A || variant < 0 || variant > 3 + Matrix::kBulkVariants)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: bad argument");
+    Matrix *m = reinterpret_cast<Matrix *>(A);
+    if (variant >= 2 && variant <= 4 && !m->part[variant - 2])
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
+    if (variant >= 5 && (!is_packed(m->p.format) || m->p.C != 32))
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_set_spmv_variant: the prefetch kernel needs a PackSELL matrix with C = 32");
+    m->variant = variant;
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
+                                   float *h_times, void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y) || reps < 1)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
+    Matrix *m = reinterpret_cast<Matrix *>(A);
+    cudaStream_t s = as_stream(stream);
+    const int nvar = 3 + Matrix::kBulkVariants;
+    if (h_times)
+        for (int v = 0; v < nvar; ++v) h_times[v] = 0.f;
+    cudaEvent_t e0, e1;
+    PS_CUDA(cudaEventCreate(&e0));
+    PS_CUDA(cudaEventCreate(&e1));
+    const int keep = m->variant;
+    int best = m->auto_variant;
+    float best_ms = 0.f;
+    packsell_status st = PACKSELL_OK;
+    for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
+        if (var >= 2 && !is_packed(m->p.format)) continue;
+        if (var >= 5 && m->p.C != 32) continue;
+        if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;
+        m->variant = var;
+        for (int r = 0; r < 3 && st == PACKSELL_OK; ++r) st = spmv_impl(*m, x, y, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == PACKSELL_OK; ++r) st = spmv_impl(*m, x, y, s);
+        cudaEventRecord(e1, s);
+        if (st != PACKSELL_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(PACKSELL_ERR_CUDA, "packsell_tune_spmv: timing failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (h_times) h_times[var - 1] = ms;
+        if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = var;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->variant = keep;
+    if (st == PACKSELL_OK) m->auto_variant = best;
+    return st;
+}
+
+packsell_status packsell_check_status(const packsell_matrix *A, void *stream) {
+    clear_error();
+    if (!A) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_check_status: NULL matrix");
+    const Matrix *m = M(A);
+    if (!m->status) return PACKSELL_OK;
+    DevStatus h{};
+    cudaStream_t s = as_stream(stream);
+    PS_CUDA(cudaMemcpyAsync(&h, m->status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaMemsetAsync(m->status, 0, sizeof(DevStatus), s));
+    PS_CUDA(cudaStreamSynchronize(s));
+    if (h.code)
+        return fail((packsell_status)h.code,
+                    "packsell_check_status: a bounded wait ran out in warp " + std::to_string(h.index));
     return PACKSELL_OK;
 }
 

@@ -399,6 +399,8 @@ void free_matrix_arrays(Matrix *A) {
     cudaFree(A->offset);
     cudaFree(A->perm);
     cudaFree(A->rowptr);
+    cudaFree(A->status);
+    for (int v = 0; v < Matrix::kBulkVariants; ++v) cudaFree(A->part[v]);
 }
 
 }  // namespace
@@ -556,6 +558,8 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
             }
         }
         PS_LAUNCH_CHECK("packsell_encode: scatter");
+        packsell_status pst = plan_spmv(*A, s);
+        if (pst != PACKSELL_OK) return bail(pst);
         // Temps are released (stream-ordered) here; they outlive the scatter.
     }
     *out = A;

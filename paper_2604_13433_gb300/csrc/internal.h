@@ -32,6 +32,15 @@ struct Matrix {
     int64_t *offset = nullptr; // n_slices + 1
     void *perm = nullptr;      // n entries of perm_bytes
     int64_t *rowptr = nullptr; // optional copy of the CSR row pointer
+    DevStatus *status = nullptr; // device status word of the SpMV kernels
+    // SpMV launch plan: the variant in use and, for each bulk-staged
+    // configuration, the per-warp slice partition of a persistent grid
+    static constexpr int kBulkVariants = 3;
+    int variant = 0;       // 0 auto, 1 thread-per-row, 2.. bulk-staged configs
+    int auto_variant = 1;  // what variant 0 runs (set by the plan or the tuner)
+    int32_t *part[kBulkVariants] = {};  // part_warps + 1 slice boundaries
+    int part_warps[kBulkVariants] = {};
+    int part_blocks[kBulkVariants] = {};
 };
 
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
@@ -51,6 +60,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
 packsell_status validate_impl(const Matrix &A, cudaStream_t s);
 
 // spmv.cu
+packsell_status plan_spmv(Matrix &A, cudaStream_t s);
 packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_t s);
 packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaStream_t s);
 packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, float *Y,

@@ -73,6 +73,337 @@ __global__ void __launch_bounds__(TPB)
     y[orig_row(i, sigma, perm, perm_bytes)] = t;
 }
 
+// One word: add its delta to c; if it carries a value, gather x_c.
+template <int FMT>
+__device__ __forceinline__ void word_gather(uint32_t wd, Decode dc, const float *__restrict__ x,
+                                            int &c, bool &f, float &xv) {
+    f = (wd & 1u) != 0u;
+    c += (int)((wd >> 1) & (f ? dc.dmask : 0x7fffffffu));
+    if (f) xv = __ldg(x + c);
+}
+
+template <int FMT>
+__device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
+    if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
+    return __uint_as_float(wd & dc.vmask);
+}
+
+// Thread-per-row SpMV with row register prefetch: each thread first issues
+// the loads of up to PF words of its row at once (plain loads the compiler
+// can predicate on j < w), then decodes them, issues their x
+// gathers, and finally runs the fused multiply-adds in stored order. A row of
+// up to PF words costs one memory round trip for its words and one for its
+// gathers. Words past the row's slice width are taken as 0 (padding).
+template <int FMT, int PF, int C, int MINB>
+__global__ void __launch_bounds__(TPB, MINB)
+    k_spmv_prefetch(int n, int sigma, int sig_shift, long long k_left,
+                    const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                    const void *__restrict__ perm, int perm_bytes, Decode dc,
+                    const float *__restrict__ x, float *__restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = i / C, l = i - k * C;
+    int64_t s = offset[k];
+    int w = (int)((offset[k + 1] - s) / C);
+    const uint32_t *__restrict__ pp = pack + s + l;
+    const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
+    int c = (k_left < blk) ? (int)(blk - k_left) : 0;
+    float t = 0.f;
+    for (int j0 = 0; j0 < w; j0 += PF) {
+        const int wr = w - j0;
+        // loads predicated on the width; a word past it acts as padding
+        uint32_t wd[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
+        bool f[PF];
+        float xv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+    }
+    int io = i;
+    if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
+    else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
+    y[io] = t;
+}
+
+template <int FMT, int PF, int MINB>
+packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const float *x,
+                                float *y, cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sig_shift = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    k_spmv_prefetch<FMT, PF, 32, MINB><<<grid_for(A.n), TPB, 0, s>>>(
+        (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+    PS_LAUNCH_CHECK("packsell_spmv (prefetch)");
+    return PACKSELL_OK;
+}
+
+// Bulk-staged PackSELL SpMV (C = 32).
+//
+// Warp gw owns the contiguous slices [part[gw], part[gw+1]): one contiguous
+// run of words (a "stream"), which it copies into a circular shared-memory
+// ring of NS chunks of SW words with cp.async.bulk (TMA engine); chunk g of
+// the stream lands in ring words [(g*SW) & MASK, ...) and completes on
+// mbarrier g % NS. Lane 0 keeps up to NS chunks in flight; the whole warp
+// waits on a chunk's mbarrier (bounded) before reading it, and lane 0
+// re-issues a slot once the warp has moved past its chunk. Bytes in flight
+// per warp are up to NS * SW * 4, independent of registers.
+//
+// Lane l decodes row l of each slice; its word j sits at stream position
+// s0 + 32 j + l, i.e. ring[(s0 + 32 j + l) & MASK]: 32 consecutive words per
+// column, one bank per lane. A slice is processed in one pass once all chunks
+// it touches have landed (slices up to (NS-1)*SW/32 columns wide); wider
+// slices are processed chunk by chunk. Rows are summed in stored order with
+// one fused multiply-add per value word, so the result equals the
+// thread-per-row kernel's bits (a word without a value adds 0 * 0, which
+// leaves a sum that starts at +0 unchanged).
+template <int NS, int SW>
+struct BulkRing {
+    static constexpr int RING = NS * SW;
+    static_assert((SW & (SW - 1)) == 0 && SW % 32 == 0, "SW: power of two, whole columns");
+    // ring word of stream position q: chunk q / SW sits in slot (q / SW) % NS
+    __device__ static __forceinline__ int at(int q) { return ((q / SW) % NS) * SW + (q & (SW - 1)); }
+};
+
+template <int NS, int SW>
+__device__ __forceinline__ int bulk_issue(int lane, int next, int lim, int total,
+                                          const uint32_t *__restrict__ src, uint32_t *ring,
+                                          uint64_t *bar, uint64_t pol) {
+    if (lane == 0) {
+        for (int g = next; g < lim; ++g) {
+            const int q = g % NS;
+            const int w0 = g * SW;
+            const int cnt = total - w0 < SW ? total - w0 : SW;
+            const uint32_t bytes = (uint32_t)cnt * 4u;
+            mbar_expect_tx(&bar[q], bytes);
+            bulk_g2s(ring + q * SW, src + w0, bytes, &bar[q], pol);
+        }
+    }
+    return lim > next ? lim : next;
+}
+
+// Accumulate columns [j0, j1) of one row from ring words at p + 32 j (the
+// caller's ring base already includes the lane): full groups of 8 with all
+// loads and gathers first, then the group's fused multiply-adds in order,
+// and a word-at-a-time tail.
+struct RowState {
+    int c;
+    float t;
+};
+
+template <int FMT>
+__device__ __forceinline__ RowState row_run(const uint32_t *ring, int p, int j0, int j1, Decode dc,
+                                            const float *__restrict__ x, RowState r) {
+    int c = r.c;
+    float t = r.t;
+    int j = j0;
+    for (; j + 8 <= j1; j += 8) {
+        uint32_t wd[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wd[u] = ring[p + 32 * (j + u)];
+        bool f[8];
+        float xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+    }
+    for (; j < j1; ++j) {
+        const uint32_t wd = ring[p + 32 * j];
+        bool f;
+        float xv;
+        word_gather<FMT>(wd, dc, x, c, f, xv);
+        if (f) t = fmaf(word_value<FMT>(wd, dc), xv, t);
+    }
+    return RowState{c, t};
+}
+
+// The run above as a real call (fewer registers in the caller) or inlined.
+template <int FMT>
+__device__ __noinline__ RowState row_run_call(const uint32_t *ring, int p, int j0, int j1,
+                                              Decode dc, const float *__restrict__ x, RowState r) {
+    return row_run<FMT>(ring, p, j0, j1, dc, x, r);
+}
+
+template <int FMT, bool INL>
+__device__ __forceinline__ RowState bulk_row_run(const uint32_t *ring, int p, int j0, int j1,
+                                                 Decode dc, const float *__restrict__ x,
+                                                 RowState r) {
+    return INL ? row_run<FMT>(ring, p, j0, j1, dc, x, r) : row_run_call<FMT>(ring, p, j0, j1, dc, x, r);
+}
+
+template <int FMT, int NW, int NS, int SW, int MINB, bool INL>
+__global__ void __launch_bounds__(NW * 32, MINB)
+    k_spmv_bulk(int n, int sigma, int sig_shift, long long k_left,
+                const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                const void *__restrict__ perm, int perm_bytes, Decode dc,
+                const float *__restrict__ x, float *__restrict__ y,
+                const int32_t *__restrict__ part, DevStatus *st) {
+    using R = BulkRing<NS, SW>;
+    extern __shared__ __align__(128) uint32_t ring_all[];
+    __shared__ __align__(8) uint64_t bars[NW][NS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * NW + warp;
+    const int k0 = part[gw], k1 = part[gw + 1];
+    if (k0 >= k1) return;  // warp-uniform
+    uint32_t *ring = ring_all + warp * R::RING;
+    uint64_t *bar = bars[warp];
+    const int64_t base = offset[k0];
+    const int total = (int)(offset[k1] - base);  // words of this warp's stream
+    const uint32_t *src = pack + base;
+    const int nchunks = (total + SW - 1) / SW;
+    const uint64_t pol = policy_evict_first();
+    if (lane == 0) {
+        for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    int issued = bulk_issue<NS, SW>(lane, 0, NS < nchunks ? NS : nchunks, total, src, ring, bar, pol);
+    int waited = 0;    // chunks [0, waited) have landed
+    int released = 0;  // chunks [0, released) are consumed
+
+    // wait for chunks up to and including g (in order); false on timeout
+    auto wait_upto = [&](int g) -> bool {
+        for (; waited <= g; ++waited) {
+            bool ok = mbar_wait(&bar[waited % NS], (uint32_t)((waited / NS) & 1));
+            if (!__all_sync(0xffffffffu, ok)) return false;
+        }
+        return true;
+    };
+    // the warp no longer reads chunks below g: refill their slots
+    auto release_below = [&](int g) {
+        if (g > released) {
+            released = g;
+            __syncwarp();
+            if (lane == 0) fence_proxy_async_smem();
+            const int lim = released + NS < nchunks ? released + NS : nchunks;
+            issued = bulk_issue<NS, SW>(lane, issued, lim, total, src, ring, bar, pol);
+        }
+    };
+
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int nk = (k1 - kb < 32) ? (k1 - kb) : 32;
+        const int o_lo = (lane < nk) ? (int)(offset[kb + lane] - base) : 0;
+        const int o_hi = (lane < nk) ? (int)(offset[kb + lane + 1] - base) : 0;
+        for (int q = 0; q < nk; ++q) {
+            const int s0 = __shfl_sync(0xffffffffu, o_lo, q);
+            const int s1 = __shfl_sync(0xffffffffu, o_hi, q);
+            const int w = (s1 - s0) >> 5;
+            const int row = (kb + q) * 32 + lane;
+            const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
+            RowState rs{(k_left < blk) ? (int)(blk - k_left) : 0, 0.f};
+            int yo = row;
+            if (perm_bytes == 1) yo = blk + (int)((const uint8_t *)perm)[min(row, n - 1)];
+            else if (perm_bytes == 2) yo = blk + (int)((const uint16_t *)perm)[min(row, n - 1)];
+            if (w > 0) {
+                if (s1 - s0 <= (NS - 1) * SW) {
+                    // whole slice resident at once; a slice that runs past the
+                    // ring's last word continues at ring word 0
+                    if (!wait_upto((s1 - 1) / SW)) goto timeout;
+                    const int r0 = R::at(s0);
+                    const int room = (R::RING - r0) >> 5;  // columns before the ring's end
+                    if (w <= room) {
+                        rs = bulk_row_run<FMT, INL>(ring, r0 + lane, 0, w, dc, x, rs);
+                    } else {
+                        rs = bulk_row_run<FMT, INL>(ring, r0 + lane, 0, room, dc, x, rs);
+                        rs = bulk_row_run<FMT, INL>(ring, lane - 32 * room, room, w, dc, x, rs);
+                    }
+                    release_below(s1 / SW);
+                } else {
+                    // wide slice: one chunk at a time
+                    int j = 0;
+                    while (j < w) {
+                        const int pos = s0 + 32 * j;
+                        const int g = pos / SW;
+                        if (!wait_upto(g)) goto timeout;
+                        const int jend = min(w, j + (((g + 1) * SW - pos) >> 5));
+                        rs = bulk_row_run<FMT, INL>(ring, R::at(pos) + lane - 32 * j, j, jend, dc, x, rs);
+                        j = jend;
+                        release_below(s0 + 32 * j < s1 ? (s0 + 32 * j) / SW : s1 / SW);
+                    }
+                }
+            }
+            if (row < n) y[yo] = rs.t;
+        }
+    }
+    return;
+timeout:
+    if (lane == 0) dev_fail(st, PACKSELL_ERR_TIMEOUT, gw);
+    // let every copy already issued land before the block's shared memory goes
+    for (int g = waited; g < issued; ++g) mbar_wait(&bar[g % NS], (uint32_t)((g / NS) & 1));
+}
+
+// Bulk kernel configurations (warps per block, chunks per warp, words per
+// chunk), selected as SpMV variants 2, 3 and 4.
+struct BulkCfg {
+    int nw, ns, sw;
+    size_t smem() const { return sizeof(uint32_t) * (size_t)nw * ns * sw; }
+};
+constexpr BulkCfg kBulkCfg[3] = {{8, 3, 512}, {4, 3, 512}, {8, 2, 1024}};
+
+template <int FMT, int V>
+struct BulkKernel;
+// MINB: blocks per SM that the configuration's shared memory allows, so
+// the register budget matches the occupancy the ring sizes permit
+#define PS_BULK_KERNEL(V, NW, NS, SW, MINB, INL)                                        \
+    template <int FMT>                                                                  \
+    struct BulkKernel<FMT, V> {                                                         \
+        static constexpr auto fn = k_spmv_bulk<FMT, NW, NS, SW, MINB, INL>;             \
+    };
+PS_BULK_KERNEL(0, 8, 3, 512, 4, false)
+PS_BULK_KERNEL(1, 4, 3, 512, 9, false)
+PS_BULK_KERNEL(2, 8, 2, 1024, 3, true)
+#undef PS_BULK_KERNEL
+
+// part[g] = first slice whose word offset reaches g * N_w / G, g = 0..G.
+__global__ void k_partition(int64_t S, const int64_t *__restrict__ offset, int G,
+                            int32_t *__restrict__ part) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > G) return;
+    int64_t total = offset[S];
+    int64_t target = (int64_t)((__int128)total * g / G);
+    int64_t lo = 0, hi = S;  // first k in [0, S] with offset[k] >= target
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (offset[mid] >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    part[g] = (int32_t)(g == G ? S : lo);
+}
+
+template <int FMT>
+void *bulk_fn(int v) {
+    switch (v) {
+        case 0: return (void *)BulkKernel<FMT, 0>::fn;
+        case 1: return (void *)BulkKernel<FMT, 1>::fn;
+        default: return (void *)BulkKernel<FMT, 2>::fn;
+    }
+}
+
+template <int FMT>
+packsell_status launch_bulk(const Matrix &A, int v, const void *perm, int pb, const float *x,
+                            float *y, cudaStream_t s) {
+    const int sg = A.p.sigma;
+    int sig_shift = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    int n = (int)A.n;
+    long long kl = A.p.k_left;
+    Decode dc = make_decode(A);
+    const int32_t *part = A.part[v];
+    DevStatus *st = A.status;
+    const BulkCfg &cf = kBulkCfg[v];
+    int sigma = sg;
+    const int64_t *offset = A.offset;
+    const uint32_t *pack = A.pack;
+    void *kargs[] = {&n, &sigma, &sig_shift, &kl, (void *)&offset, (void *)&pack, (void *)&perm,
+                     &pb, &dc, (void *)&x, (void *)&y, (void *)&part, (void *)&st};
+    PS_CUDA(cudaLaunchKernel(bulk_fn<FMT>(v), dim3(A.part_blocks[v]), dim3(cf.nw * 32), kargs,
+                             cf.smem(), s));
+    return PACKSELL_OK;
+}
+
 // Plain SELL-C-sigma (§3): value and column streams, padding multiplies 0.
 template <typename T>
 __global__ void __launch_bounds__(TPB)
@@ -261,11 +592,65 @@ __global__ void __launch_bounds__(TPB)
 
 }  // namespace
 
+// Launch plan of the bulk-staged kernels: for each configuration a
+// persistent grid of as many blocks as fit on the device, and the per-warp
+// slice partition balanced by words. Variant 0 then runs configuration 0.
+packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
+    if (!A.status) {
+        PS_CUDA(cudaMalloc(&A.status, sizeof(DevStatus)));
+        PS_CUDA(cudaMemsetAsync(A.status, 0, sizeof(DevStatus), s));
+    }
+    A.auto_variant = 1;
+    // the bulk kernel indexes a warp's words with 32-bit integers
+    if (!is_packed(A.p.format) || A.p.C != 32 || A.n == 0 || A.n_words >= (1ll << 31) - 4096)
+        return PACKSELL_OK;
+    int dev = 0, sms = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int v = 0; v < Matrix::kBulkVariants; ++v) {
+        const BulkCfg &cf = kBulkCfg[v];
+        void *fn = A.p.format == PACKSELL_FMT_FP16 ? bulk_fn<PACKSELL_FMT_FP16>(v)
+                                                   : bulk_fn<PACKSELL_FMT_E8MY>(v);
+        PS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem()));
+        int per_sm = 0;
+        PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cf.nw * 32, cf.smem()));
+        if (per_sm < 1) continue;
+        const int blocks = sms * per_sm, G = blocks * cf.nw;
+        if (A.part[v]) cudaFree(A.part[v]);
+        A.part[v] = nullptr;
+        PS_CUDA(cudaMalloc(&A.part[v], sizeof(int32_t) * (G + 1)));
+        k_partition<<<(G + 1 + 255) / 256, 256, 0, s>>>(A.n_slices, A.offset, G, A.part[v]);
+        PS_LAUNCH_CHECK("k_partition");
+        A.part_blocks[v] = blocks;
+        A.part_warps[v] = G;
+    }
+    if (A.part[0]) A.auto_variant = 2;
+    return PACKSELL_OK;
+}
+
 packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_t s) {
     if (A.n == 0) return PACKSELL_OK;
     const void *perm = A.p.explicit_perm ? nullptr : A.perm;
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     int g = grid_for(A.n);
+    const int var = A.variant == 0 ? A.auto_variant : A.variant;
+    if ((var == 5 || var == 6) && is_packed(A.p.format)) {
+        if (A.p.C != 32)
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the prefetch variants need C = 32");
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        if (var == 5)
+            return h ? launch_prefetch<PACKSELL_FMT_FP16, 16, 5>(A, perm, pb, x, y, s)
+                     : launch_prefetch<PACKSELL_FMT_E8MY, 16, 5>(A, perm, pb, x, y, s);
+        return h ? launch_prefetch<PACKSELL_FMT_FP16, 32, 4>(A, perm, pb, x, y, s)
+                 : launch_prefetch<PACKSELL_FMT_E8MY, 32, 4>(A, perm, pb, x, y, s);
+    }
+    if (var >= 2 && var <= 4 && is_packed(A.p.format)) {
+        const int v = var - 2;
+        if (v >= Matrix::kBulkVariants || !A.part[v])
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: bulk-staged variant unavailable");
+        return A.p.format == PACKSELL_FMT_FP16 ? launch_bulk<PACKSELL_FMT_FP16>(A, v, perm, pb, x, y, s)
+                                               : launch_bulk<PACKSELL_FMT_E8MY>(A, v, perm, pb, x, y, s);
+    }
     switch (A.p.format) {
         case PACKSELL_FMT_FP16:
             k_spmv_packed<PACKSELL_FMT_FP16><<<g, TPB, 0, s>>>(

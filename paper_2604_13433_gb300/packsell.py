@@ -24,7 +24,10 @@ _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
             "sell_f64": FMT_SELL_F64}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
-          6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT"}
+          6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
+SPMV_AUTO, SPMV_ROWTHREAD, SPMV_BULK = 0, 1, 2
+SPMV_BULK_VARIANTS = (2, 3, 4)
+SPMV_PREFETCH = (5, 6)
 
 
 class PackSELLError(RuntimeError):
@@ -67,6 +70,9 @@ SIGNATURES = {
     "packsell_spmm": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _I64, _P]),
     "packsell_spmv_transpose": (ctypes.c_int, [_P, _P, _P, _P]),
     "packsell_pattern_outer": (ctypes.c_int, [_P, _F32, _P, _P, _P, _P]),
+    "packsell_set_spmv_variant": (ctypes.c_int, [_P, _I32]),
+    "packsell_check_status": (ctypes.c_int, [_P, _P]),
+    "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
 }
 
 
@@ -177,6 +183,29 @@ def packsell_encode_csr(csr, device="cuda", **kw) -> PackSELLMatrix:
     cl = torch.from_numpy(csr.col).to(device)
     vl = torch.from_numpy(csr.val).to(device)
     return packsell_encode(rp, cl, vl, csr.n, csr.m, **kw)
+
+
+def packsell_set_spmv_variant(A: PackSELLMatrix, variant: int) -> None:
+    """0 auto, 1 thread-per-row, 2-4 bulk-staged configurations, 5-6 row prefetch."""
+    _check(lib().packsell_set_spmv_variant(A.handle, int(variant)))
+
+
+def packsell_tune_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
+                       reps: int = 20, stream=None) -> dict:
+    """Time every SpMV variant on (x, y) and make variant 0 use the fastest.
+    Returns {variant: ms per launch} for the variants that ran."""
+    if y is None:
+        y = torch.empty(A.n, dtype=torch.float32, device=x.device)
+    times = (ctypes.c_float * 6)()
+    _check(lib().packsell_tune_spmv(A.handle, _dev(x, torch.float32, "x", A.m),
+                                    _dev(y, torch.float32, "y", A.n), int(reps), times,
+                                    _stream(stream)))
+    return {v + 1: times[v] for v in range(6) if times[v] > 0}
+
+
+def packsell_check_status(A: PackSELLMatrix, stream=None) -> None:
+    """Raise if a kernel's bounded wait ran out since the last check."""
+    _check(lib().packsell_check_status(A.handle, _stream(stream)))
 
 
 def packsell_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
