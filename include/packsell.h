@@ -218,6 +218,58 @@ packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *d
 packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, const float *u,
                                        const float *v, float *out, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Solvers (§5.2.2): FP64 PCG and the mixed-precision inner-outer CG        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct packsell_solve_opts {
+    double rtol;         /* stop when ||b - A x||_2 / ||b||_2 < rtol, checked on the
+                            true residual in FP64 */
+    int32_t m_in;        /* inner FP32 PCG iterations per outer step (IO-CG);
+                            0 = plain FP64 Jacobi PCG on A_outer */
+    int32_t max_iters;   /* outer iterations (PCG iterations when m_in = 0) */
+    int32_t check_every; /* iterations per graph replay between host checks; the
+                            device idles once converged, so counts stay exact */
+    int32_t use_graph;   /* 1: replay the iteration body as a captured CUDA graph */
+} packsell_solve_opts;
+
+typedef struct packsell_solve_result {
+    int32_t iters;       /* outer (or PCG) iterations done */
+    int32_t inner_iters; /* inner iterations done (IO-CG) */
+    double relres;       /* recurrence residual ||r|| / ||b|| at exit */
+    double relres_true;  /* true residual ||b - A x|| / ||b|| at exit (FP64) */
+    double seconds;      /* device time of the solve (CUDA events) */
+} packsell_solve_result;
+
+/* Device workspace bytes packsell_pcg needs for n unknowns (has_diag: a Jacobi
+ * preconditioner is passed). */
+size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag,
+                                    int32_t max_iters);
+
+/* Solve A x = b for SPD A.
+ *   A_outer : SELL_F64 matrix (square, implicit permutation): the FP64
+ *             operator of the outer iteration and of the residual check
+ *   A_inner : PackSELL (FP16 / E8MY) or SELL_F32 copy of the same matrix for
+ *             the inner FP32 PCG (ignored when m_in = 0)
+ *   inv_diag: NULL or double [n], the Jacobi preconditioner 1 / a_ii
+ *   b       : double [n]; x: double [n], the initial guess on entry, the
+ *             solution on exit
+ *   work    : device workspace of at least packsell_pcg_workspace_bytes, or
+ *             NULL to let the call allocate (stream-ordered) and free it
+ *   h_hist  : NULL or host double [max_iters + 1]: recurrence residual after
+ *             each outer (PCG) iteration, entry 0 the initial one
+ * IO-CG: flexible CG (one previous direction) in FP64; its preconditioner is
+ * m_in PCG iterations in FP32 from zero on r / ||r||_2 with A_inner. Dot
+ * products accumulate in FP64; the residual is replaced by the true one if
+ * the recurrence claims convergence before b - A x does.
+ * Runs on a private stream after the caller's pending work; SYNCHRONISES.
+ * Returns NOT_CONVERGED after max_iters (x holds the last iterate),
+ * BREAKDOWN on p^T A p <= 0 or a non-finite residual. */
+packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matrix *A_inner,
+                             const double *inv_diag, const double *b, double *x,
+                             const packsell_solve_opts *opts, void *work, size_t work_bytes,
+                             double *h_hist, packsell_solve_result *result, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -357,4 +357,19 @@ packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, co
     return pattern_outer_impl(*M(A), alpha, u, v, out, as_stream(stream));
 }
 
+size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag, int32_t max_iters) {
+    if (n < 0 || m_in < 0 || max_iters < 0) return 0;
+    return solve_workspace_bytes(n, m_in, has_diag, max_iters);
+}
+
+packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matrix *A_inner,
+                             const double *inv_diag, const double *b, double *x,
+                             const packsell_solve_opts *opts, void *work, size_t work_bytes,
+                             double *h_hist, packsell_solve_result *result, void *stream) {
+    clear_error();
+    if (!A_outer || !opts) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: NULL argument");
+    return solve_impl(M(A_outer), A_inner ? M(A_inner) : nullptr, inv_diag, b, x, *opts, work,
+                      work_bytes, h_hist, result, as_stream(stream));
+}
+
 }  // extern "C"

@@ -69,6 +69,21 @@ packsell_status spmv_t_impl(const Matrix &A, const float *dy, float *dx, cudaStr
 packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u, const float *v,
                                    float *out, cudaStream_t s);
 
+// solve.cu
+size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters);
+packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
+                           const double *b, double *x, const packsell_solve_opts &o, void *work,
+                           size_t work_bytes, double *h_hist, packsell_solve_result *res,
+                           cudaStream_t caller);
+
+// solver support (spmv.cu): SpMV fused with a deterministic dot reduction
+struct Red;
+int spmv_dot_blocks(const Matrix &A);
+packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
+                             cudaStream_t s);
+packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
+                             const Red &red, cudaStream_t s);
+
 }  // namespace packsell
 
 #define PS_CUDA(call)                                                   \

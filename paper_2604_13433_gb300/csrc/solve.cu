@@ -1,0 +1,434 @@
+// Solvers: FP64 Jacobi-preconditioned CG, and the inner-outer CG (IO-CG) of
+// §5.2.2 - flexible CG in FP64 whose preconditioner is m_in iterations of
+// PCG in FP32 on a PackSELL (or FP32 SELL) copy of the matrix.
+//
+// Every step is a kernel on a private stream; scalars (alpha, beta, norms)
+// stay on the device in a SolveScalars record written by the last block of
+// each reducing kernel (deterministic, see reduce.cuh). One outer iteration
+// (IO-CG) or `check_every` PCG iterations are captured once as a CUDA graph
+// and replayed; the host reads the scalars after each replay. When the
+// recurrence residual drops below rtol the device sets `done` and the
+// remaining kernels of the replay idle, so iteration counts are exact. The
+// host then checks the true residual ||b - A x||_2 / ||b||_2 in FP64; if it is
+// not yet below rtol the residual is replaced by the true one and the outer
+// method restarts from the current x.
+//
+// Readings of §5.2.2 (which gives the scheme, not its details): flexible CG
+// keeps one previous direction (FCG(1)); the inner PCG starts from zero, runs
+// exactly m_in iterations and solves for r / ||r||_2 (scaled back after),
+// so FP32 never sees the outer residual's magnitude; the Jacobi
+// preconditioner (if given) acts inside the inner PCG.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace packsell {
+namespace {
+
+constexpr int VTPB = 256;
+
+// grid-stride loop over [0, n)
+#define PS_FOR(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// r = b - Ax (Ax given). s1 = b.b, s2 = r.r; r written when r != nullptr.
+__global__ void __launch_bounds__(VTPB)
+    k_residual(int64_t n, const double *__restrict__ b, const double *__restrict__ ax,
+               double *__restrict__ r, Red red) {
+    double bb = 0.0, rr = 0.0;
+    PS_FOR(i, n) {
+        const double bi = b[i], ri = bi - ax[i];
+        if (r) r[i] = ri;
+        bb += bi * bi;
+        rr += ri * ri;
+    }
+    reduce_publish(red, red.fin == FIN_RT ? rr : bb, rr);
+}
+
+// PCG start (type T): z = M r, p = z, s1 = r.z
+template <typename T>
+__global__ void __launch_bounds__(VTPB)
+    k_pcg_init(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
+               Red red) {
+    double rz = 0.0;
+    PS_FOR(i, n) {
+        const T z = M ? M[i] * r[i] : r[i];
+        p[i] = z;
+        rz += (double)r[i] * (double)z;
+    }
+    reduce_publish(red, rz, 0.0);
+}
+
+// Inner PCG start: r_in = r / ||r|| (rounded to FP32), x_in = 0, p = M r_in.
+__global__ void __launch_bounds__(VTPB)
+    k_inner_init(int64_t n, const double *__restrict__ r64, const float *__restrict__ M,
+                 float *__restrict__ xi, float *__restrict__ ri, float *__restrict__ pi, Red red) {
+    if (red.sc->done) return;
+    const double inv = red.sc->rnorm > 0.0 ? 1.0 / red.sc->rnorm : 0.0;
+    double rz = 0.0;
+    PS_FOR(i, n) {
+        const float r = (float)(r64[i] * inv);
+        const float z = M ? M[i] * r : r;
+        xi[i] = 0.f;
+        ri[i] = r;
+        pi[i] = z;
+        rz += (double)r * (double)z;
+    }
+    reduce_publish(red, rz, 0.0);
+}
+
+// x += alpha p, r -= alpha q; s1 = r.z (z = M r), s2 = r.r
+template <typename T>
+__global__ void __launch_bounds__(VTPB)
+    k_update(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+             const T *__restrict__ q, const T *__restrict__ M, Red red) {
+    if (red.sc->done) return;
+    const T a = (T)red.sc->alpha;
+    double rz = 0.0, rr = 0.0;
+    PS_FOR(i, n) {
+        x[i] = fma(a, p[i], x[i]);
+        const T ri = fma(-a, q[i], r[i]);
+        r[i] = ri;
+        const T z = M ? M[i] * ri : ri;
+        rz += (double)ri * (double)z;
+        rr += (double)ri * (double)ri;
+    }
+    reduce_publish(red, rz, rr);
+}
+
+// p = M r + beta p
+template <typename T>
+__global__ void __launch_bounds__(VTPB)
+    k_pupdate(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
+              const SolveScalars *sc) {
+    if (sc->done) return;
+    const T b = (T)sc->beta;
+    PS_FOR(i, n) {
+        const T z = M ? M[i] * r[i] : r[i];
+        p[i] = fma(b, p[i], z);
+    }
+}
+
+// Outer: z = ||r|| x_in (FP64), s1 = z.q (q = A p of the previous direction)
+__global__ void __launch_bounds__(VTPB)
+    k_outer_z(int64_t n, const float *__restrict__ xi, double *__restrict__ z,
+              const double *__restrict__ q, Red red) {
+    if (red.sc->done) return;
+    const double rn = red.sc->rnorm;
+    double zq = 0.0;
+    PS_FOR(i, n) {
+        const double zi = rn * (double)xi[i];
+        z[i] = zi;
+        zq += zi * q[i];
+    }
+    reduce_publish(red, zq, 0.0);
+}
+
+// Outer: p = z - beta_o p (beta_o = 0 right after a (re)start)
+__global__ void __launch_bounds__(VTPB)
+    k_outer_p(int64_t n, const double *__restrict__ z, double *__restrict__ p,
+              const SolveScalars *sc) {
+    if (sc->done) return;
+    const double b = sc->beta_o;
+    PS_FOR(i, n) p[i] = (b == 0.0) ? z[i] : z[i] - b * p[i];
+}
+
+// Outer: x += alpha_o p, r -= alpha_o q; s1 = r.r
+__global__ void __launch_bounds__(VTPB)
+    k_outer_xr(int64_t n, double *__restrict__ x, double *__restrict__ r,
+               const double *__restrict__ p, const double *__restrict__ q, Red red) {
+    if (red.sc->done) return;
+    const double a = red.sc->alpha_o;
+    double rr = 0.0;
+    PS_FOR(i, n) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        rr += ri * ri;
+    }
+    reduce_publish(red, rr, 0.0);
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    PS_FOR(i, n) b[i] = (float)a[i];
+}
+
+inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Work {
+    double *r, *z, *p, *q;        // FP64 vectors
+    float *xi, *ri, *pi, *qi, *M32;  // FP32 inner vectors (IO-CG)
+    double *partials;
+    unsigned *counter;
+    SolveScalars *sc;
+    double *hist;
+    size_t bytes;
+};
+
+Work carve(void *base, int64_t n, bool inner, bool has_m, int max_iters, int pblocks) {
+    Work w{};
+    char *p = (char *)base;
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += al(b);
+        return (void *)q;
+    };
+    w.r = (double *)take(8 * n);
+    w.z = (double *)take(8 * n);
+    w.p = (double *)take(8 * n);
+    w.q = (double *)take(8 * n);
+    if (inner) {
+        w.xi = (float *)take(4 * n);
+        w.ri = (float *)take(4 * n);
+        w.pi = (float *)take(4 * n);
+        w.qi = (float *)take(4 * n);
+        if (has_m) w.M32 = (float *)take(4 * n);
+    }
+    w.partials = (double *)take(16 * (size_t)pblocks);
+    w.counter = (unsigned *)take(64);
+    w.sc = (SolveScalars *)take(sizeof(SolveScalars));
+    w.hist = (double *)take(8 * (size_t)(max_iters + 2));
+    w.bytes = (size_t)(p - (char *)base);
+    return w;
+}
+
+// fixed grid of the vector kernels (4 blocks per SM): the reductions are
+// deterministic for a given device
+int vec_blocks() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 160;  // no device yet: size for a large part
+    }
+    return std::max(1, sms * 4);
+}
+
+}  // namespace
+
+size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters) {
+    const int pblocks = std::max<int>((int)((n + 255) / 256), vec_blocks());
+    return carve(nullptr, n, m_in > 0, has_m != 0, max_iters, pblocks).bytes + 256;
+}
+
+packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
+                           const double *b, double *x, const packsell_solve_opts &o, void *work,
+                           size_t work_bytes, double *h_hist, packsell_solve_result *res,
+                           cudaStream_t caller) {
+    const bool io = o.m_in > 0;
+    if (!A64 || A64->p.format != PACKSELL_FMT_SELL_F64)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: A_outer must be a SELL_F64 matrix");
+    const int64_t n = A64->n;
+    if (A64->m != n || A64->p.explicit_perm)
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_pcg: A_outer must be square with rows in original order");
+    if (io) {
+        if (!Ain || Ain->n != n || Ain->m != n || Ain->p.explicit_perm ||
+            !(is_packed(Ain->p.format) || Ain->p.format == PACKSELL_FMT_SELL_F32))
+            return fail(PACKSELL_ERR_INVALID_ARG,
+                        "packsell_pcg: A_inner must be a square PackSELL or SELL_F32 matrix "
+                        "of the same size, rows in original order");
+    }
+    if (o.max_iters < 1 || o.check_every < 1 || !(o.rtol > 0.0) || o.m_in < 0)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: bad options");
+    if (n == 0) {
+        if (res) *res = packsell_solve_result{};
+        return PACKSELL_OK;
+    }
+    if (!b || !x) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: NULL vector");
+
+    const int pblocks = std::max<int>(spmv_dot_blocks(*A64), vec_blocks());
+    const size_t need = solve_workspace_bytes(n, o.m_in, inv_diag != nullptr, o.max_iters);
+    void *own = nullptr;
+    cudaStream_t s = nullptr;
+    PS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    packsell_status st = PACKSELL_OK;
+    Work w{};
+    SolveScalars h{};
+    int iters = 0;
+    bool converged = false;
+    double relres_true = -1.0;
+
+    // the caller's pending work on its stream comes first
+    cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
+    cudaEventRecord(ev0, caller);
+    cudaStreamWaitEvent(s, ev0, 0);
+    cudaEventDestroy(ev0);
+    ev0 = nullptr;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+
+    if (work) {
+        if (work_bytes < need) {
+            st = fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: workspace too small (need " +
+                                                    std::to_string(need) + " bytes)");
+            goto out;
+        }
+        w = carve((void *)(((uintptr_t)work + 255) & ~(uintptr_t)255), n, io, inv_diag != nullptr,
+                  o.max_iters, pblocks);
+    } else {
+        if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
+            st = fail(PACKSELL_ERR_NO_MEMORY, "packsell_pcg: workspace allocation");
+            goto out;
+        }
+        w = carve((void *)(((uintptr_t)own + 255) & ~(uintptr_t)255), n, io, inv_diag != nullptr,
+                  o.max_iters, pblocks);
+    }
+    {
+        const int G = vec_blocks();
+        auto red = [&](int fin) { return Red{w.partials, w.counter, w.sc, w.hist, fin}; };
+        SolveScalars init{};
+        init.rtol = o.rtol;
+        init.max_iters = o.max_iters;
+        init.restart = 1;
+        cudaMemcpyAsync(w.sc, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(w.counter, 0, 64, s);
+        cudaMemsetAsync(w.q, 0, 8 * n, s);
+        cudaEventRecord(ev0, s);
+        if (io && inv_diag) k_f64_to_f32<<<G, VTPB, 0, s>>>(n, inv_diag, w.M32);
+
+        // r = b - A x, ||b||, ||r||
+        auto residual = [&](double *r_out, int fin) -> packsell_status {
+            packsell_status e = spmv_f64_impl(*A64, x, w.z, s);
+            if (e != PACKSELL_OK) return e;
+            k_residual<<<G, VTPB, 0, s>>>(n, b, w.z, r_out, red(fin));
+            PS_LAUNCH_CHECK("k_residual");
+            return PACKSELL_OK;
+        };
+        st = residual(w.r, FIN_BB_RR);
+        if (st != PACKSELL_OK) goto out;
+        if (!io) {
+            k_pcg_init<double><<<G, VTPB, 0, s>>>(n, w.r, inv_diag, w.p, red(FIN_RZ_INIT));
+        }
+
+        // one replay = `chunk` outer (IO-CG) or PCG iterations
+        const int chunk = std::min(o.check_every, o.max_iters);
+        auto body = [&](cudaStream_t q) -> packsell_status {
+            for (int c = 0; c < chunk; ++c) {
+                if (io) {
+                    k_inner_init<<<G, VTPB, 0, q>>>(n, w.r, w.M32, w.xi, w.ri, w.pi, red(FIN_RZ_INIT));
+                    for (int k = 0; k < o.m_in; ++k) {
+                        packsell_status e = spmv_dot_f32(*Ain, w.pi, w.qi, red(FIN_PQ_ALPHA), q);
+                        if (e != PACKSELL_OK) return e;
+                        k_update<float><<<G, VTPB, 0, q>>>(n, w.xi, w.ri, w.pi, w.qi, w.M32,
+                                                           red(FIN_RZ_BETA));
+                        if (k + 1 < o.m_in)
+                            k_pupdate<float><<<G, VTPB, 0, q>>>(n, w.ri, w.M32, w.pi, w.sc);
+                    }
+                    k_outer_z<<<G, VTPB, 0, q>>>(n, w.xi, w.z, w.q, red(FIN_ZQ_BETA));
+                    k_outer_p<<<G, VTPB, 0, q>>>(n, w.z, w.p, w.sc);
+                    packsell_status e = spmv_dot_f64(*A64, w.p, w.q, w.r, red(FIN_OUTER_ALPHA), q);
+                    if (e != PACKSELL_OK) return e;
+                    k_outer_xr<<<G, VTPB, 0, q>>>(n, x, w.r, w.p, w.q, red(FIN_RR));
+                } else {
+                    packsell_status e = spmv_dot_f64(*A64, w.p, w.q, nullptr, red(FIN_PQ_ALPHA_64), q);
+                    if (e != PACKSELL_OK) return e;
+                    k_update<double><<<G, VTPB, 0, q>>>(n, x, w.r, w.p, w.q, inv_diag,
+                                                        red(FIN_RZ_BETA_RR));
+                    k_pupdate<double><<<G, VTPB, 0, q>>>(n, w.r, inv_diag, w.p, w.sc);
+                }
+            }
+            PS_LAUNCH_CHECK("packsell_pcg: iteration");
+            return PACKSELL_OK;
+        };
+        if (o.use_graph) {
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                st = fail(PACKSELL_ERR_CUDA, "packsell_pcg: stream capture failed to start");
+                goto out;
+            }
+            packsell_status e = body(s);
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (e != PACKSELL_OK) { st = e; goto out; }
+            if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                st = fail(PACKSELL_ERR_CUDA, "packsell_pcg: graph capture failed");
+                goto out;
+            }
+        }
+        while (iters < o.max_iters) {
+            if (o.use_graph) {
+                if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+                    st = fail(PACKSELL_ERR_CUDA, "packsell_pcg: graph launch failed");
+                    goto out;
+                }
+            } else {
+                st = body(s);
+                if (st != PACKSELL_OK) goto out;
+            }
+            cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "packsell_pcg: iteration");
+                goto out;
+            }
+            iters = h.iter;
+            if (h.status) {
+                st = fail(PACKSELL_ERR_BREAKDOWN, "packsell_pcg: breakdown (p^T A p <= 0 or "
+                                                  "a non-finite residual)");
+                goto out;
+            }
+            if (h.done && h.relres < o.rtol) {
+                // the recurrence says converged: check the true residual
+                st = residual(nullptr, FIN_RT);
+                if (st != PACKSELL_OK) goto out;
+                cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+                cudaStreamSynchronize(s);
+                relres_true = h.bb > 0.0 ? sqrt(h.rt / h.bb) : 0.0;
+                if (relres_true < o.rtol) {
+                    converged = true;
+                    break;
+                }
+                // replace the residual by the true one and restart the directions
+                st = residual(w.r, FIN_BB_RR);
+                if (st != PACKSELL_OK) goto out;
+                if (!io) k_pcg_init<double><<<G, VTPB, 0, s>>>(n, w.r, inv_diag, w.p, red(FIN_RZ_INIT));
+                int one = 1, zero = 0;
+                cudaMemcpyAsync(&w.sc->restart, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(&w.sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+                cudaStreamSynchronize(s);
+            }
+        }
+        cudaEventRecord(ev1, s);
+        cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+        PS_CUDA(cudaStreamSynchronize(s));
+        if (h_hist)
+            PS_CUDA(cudaMemcpy(h_hist, w.hist, sizeof(double) * (size_t)(std::min(h.iter, o.max_iters) + 1),
+                               cudaMemcpyDeviceToHost));
+        if (relres_true < 0.0) {
+            st = residual(nullptr, FIN_RT);
+            if (st != PACKSELL_OK) goto out;
+            SolveScalars h2{};
+            cudaMemcpyAsync(&h2, w.sc, sizeof(h2), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            relres_true = h2.bb > 0.0 ? sqrt(h2.rt / h2.bb) : 0.0;
+        }
+        if (res) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            res->iters = h.iter;
+            res->inner_iters = h.inner;
+            res->relres = h.relres;
+            res->relres_true = relres_true;
+            res->seconds = ms * 1e-3;
+        }
+        if (!converged)
+            st = fail(PACKSELL_ERR_NOT_CONVERGED,
+                      "packsell_pcg: no convergence in " + std::to_string(o.max_iters) + " iterations");
+    }
+out:
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (own) cudaFreeAsync(own, s);
+    cudaStreamSynchronize(s);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaStreamDestroy(s);
+    return st;
+}
+
+}  // namespace packsell

@@ -12,6 +12,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace packsell {
 namespace {
@@ -94,39 +95,44 @@ __device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
 // gathers, and finally runs the fused multiply-adds in stored order. A row of
 // up to PF words costs one memory round trip for its words and one for its
 // gathers. Words past the row's slice width are taken as 0 (padding).
-template <int FMT, int PF, int C, int MINB>
+template <int FMT, int PF, int C, int MINB, bool DOT = false>
 __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_prefetch(int n, int sigma, int sig_shift, long long k_left,
                     const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                     const void *__restrict__ perm, int perm_bytes, Decode dc,
-                    const float *__restrict__ x, float *__restrict__ y) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int k = i / C, l = i - k * C;
-    int64_t s = offset[k];
-    int w = (int)((offset[k + 1] - s) / C);
-    const uint32_t *__restrict__ pp = pack + s + l;
-    const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
-    int c = (k_left < blk) ? (int)(blk - k_left) : 0;
-    float t = 0.f;
-    for (int j0 = 0; j0 < w; j0 += PF) {
-        const int wr = w - j0;
-        // loads predicated on the width; a word past it acts as padding
-        uint32_t wd[PF];
+                    const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
+    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d1 = 0.0;
+    if (i < n) {
+        const int k = i / C, l = i - k * C;
+        const int64_t s = offset[k];
+        const int w = (int)((offset[k + 1] - s) / C);
+        const uint32_t *__restrict__ pp = pack + s + l;
+        const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
+        int c = (k_left < blk) ? (int)(blk - k_left) : 0;
+        float t = 0.f;
+        for (int j0 = 0; j0 < w; j0 += PF) {
+            const int wr = w - j0;
+            // loads predicated on the width; a word past it acts as padding
+            uint32_t wd[PF];
 #pragma unroll
-        for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
-        bool f[PF];
-        float xv[PF];
+            for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
+            bool f[PF];
+            float xv[PF];
 #pragma unroll
-        for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
+            for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
 #pragma unroll
-        for (int u = 0; u < PF; ++u)
-            if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+            for (int u = 0; u < PF; ++u)
+                if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+        }
+        int io = i;
+        if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
+        else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
+        y[io] = t;
+        if (DOT) d1 = (double)x[io] * (double)t;
     }
-    int io = i;
-    if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
-    else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
-    y[io] = t;
+    if (DOT) reduce_publish(red, d1, 0.0);
 }
 
 template <int FMT, int PF, int MINB>
@@ -405,37 +411,78 @@ packsell_status launch_bulk(const Matrix &A, int v, const void *perm, int pb, co
 }
 
 // Plain SELL-C-sigma (§3): value and column streams, padding multiplies 0.
-template <typename T>
+// With DOT the kernel also reduces sum_i x_i y_i and sum_i x_i b_i over the
+// output rows (square matrices, original order).
+template <typename T, bool DOT = false>
 __global__ void __launch_bounds__(TPB)
     k_spmv_sell(int n, int C, int sigma, const int64_t *__restrict__ offset,
                 const T *__restrict__ val, const int32_t *__restrict__ col,
                 const void *__restrict__ perm, int perm_bytes, const T *__restrict__ x,
-                T *__restrict__ y) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int k = i / C, l = i - k * C;
-    int64_t s = offset[k];
-    int w = (int)((offset[k + 1] - s) / C);
-    const T *vp = val + s + l;
-    const int32_t *cp = col + s + l;
-    T t = 0;
-    int j = 0;
-    for (; j + UNROLL <= w; j += UNROLL) {
-        T v[UNROLL];
-        int cc[UNROLL];
+                T *__restrict__ y, const T *__restrict__ b = nullptr, Red red = Red{}) {
+    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d1 = 0.0, d2 = 0.0;
+    if (i < n) {
+        const int k = i / C, l = i - k * C;
+        const int64_t s = offset[k];
+        const int w = (int)((offset[k + 1] - s) / C);
+        const T *vp = val + s + l;
+        const int32_t *cp = col + s + l;
+        T t = 0;
+        int j = 0;
+        for (; j + UNROLL <= w; j += UNROLL) {
+            T v[UNROLL];
+            int cc[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            v[u] = __ldcs(vp + (int64_t)(j + u) * C);
-            cc[u] = __ldcs(cp + (int64_t)(j + u) * C);
+            for (int u = 0; u < UNROLL; ++u) {
+                v[u] = __ldcs(vp + (int64_t)(j + u) * C);
+                cc[u] = __ldcs(cp + (int64_t)(j + u) * C);
+            }
+            T xv[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) xv[u] = __ldg(x + cc[u]);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) t = fma(v[u], xv[u], t);
         }
-        T xv[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) xv[u] = __ldg(x + cc[u]);
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) t = fma(v[u], xv[u], t);
+        for (; j < w; ++j) t = fma(__ldcs(vp + (int64_t)j * C), __ldg(x + __ldcs(cp + (int64_t)j * C)), t);
+        const int io = orig_row(i, sigma, perm, perm_bytes);
+        y[io] = t;
+        if (DOT) {
+            d1 = (double)x[io] * (double)t;
+            if (b) d2 = (double)x[io] * (double)b[io];
+        }
     }
-    for (; j < w; ++j) t = fma(__ldcs(vp + (int64_t)j * C), __ldg(x + __ldcs(cp + (int64_t)j * C)), t);
-    y[orig_row(i, sigma, perm, perm_bytes)] = t;
+    if (DOT) reduce_publish(red, d1, d2);
+}
+
+// Thread-per-row PackSELL SpMV fused with sum_i x_i y_i (solver use, any C).
+template <int FMT>
+__global__ void __launch_bounds__(TPB)
+    k_spmv_packed_dot(int n, int C, int sigma, long long k_left,
+                      const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                      const void *__restrict__ perm, int perm_bytes, Decode dc,
+                      const float *__restrict__ x, float *__restrict__ y, Red red) {
+    if (red.sc->done) return;  // solver converged: idle (grid-uniform)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d1 = 0.0;
+    if (i < n) {
+        const int k = i / C, l = i - k * C;
+        const int64_t s = offset[k];
+        const int w = (int)((offset[k + 1] - s) / C);
+        int c = left_offset(i, sigma, k_left);
+        float t = 0.f;
+        for (int j = 0; j < w; ++j) {
+            bool f;
+            float xv;
+            const uint32_t wd = pack[s + (int64_t)j * C + l];
+            word_gather<FMT>(wd, dc, x, c, f, xv);
+            if (f) t = fmaf(word_value<FMT>(wd, dc), xv, t);
+        }
+        const int io = orig_row(i, sigma, perm, perm_bytes);
+        y[io] = t;
+        d1 = (double)x[io] * (double)t;
+    }
+    reduce_publish(red, d1, 0.0);
 }
 
 // SpMM, k right-hand sides in chunks of KT accumulators per thread.
@@ -767,6 +814,48 @@ packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u,
             break;
     }
     PS_LAUNCH_CHECK("packsell_pattern_outer");
+    return PACKSELL_OK;
+}
+
+// ---- fused SpMV + dot launchers for the solvers (square, original order) ----
+int spmv_dot_blocks(const Matrix &A) { return grid_for(A.n); }
+
+packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
+                             cudaStream_t s) {
+    const int g = grid_for(A.n);
+    const void *perm = A.perm;
+    const int pb = A.perm_bytes;
+    if (A.p.format == PACKSELL_FMT_SELL_F32) {
+        k_spmv_sell<float, true><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
+                                                   (const float *)A.val, A.col, perm, pb, x, y,
+                                                   nullptr, red);
+    } else if (A.p.C == 32) {
+        const int sg = A.p.sigma;
+        const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+        if (A.p.format == PACKSELL_FMT_FP16)
+            k_spmv_prefetch<PACKSELL_FMT_FP16, 16, 32, 5, true><<<g, TPB, 0, s>>>(
+                (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
+        else
+            k_spmv_prefetch<PACKSELL_FMT_E8MY, 16, 32, 5, true><<<g, TPB, 0, s>>>(
+                (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
+    } else {
+        if (A.p.format == PACKSELL_FMT_FP16)
+            k_spmv_packed_dot<PACKSELL_FMT_FP16><<<g, TPB, 0, s>>>(
+                (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
+        else
+            k_spmv_packed_dot<PACKSELL_FMT_E8MY><<<g, TPB, 0, s>>>(
+                (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
+    }
+    PS_LAUNCH_CHECK("spmv_dot_f32");
+    return PACKSELL_OK;
+}
+
+packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
+                             const Red &red, cudaStream_t s) {
+    k_spmv_sell<double, true><<<grid_for(A.n), TPB, 0, s>>>(
+        (int)A.n, A.p.C, A.p.sigma, A.offset, (const double *)A.val, A.col, A.perm, A.perm_bytes, x,
+        y, b, red);
+    PS_LAUNCH_CHECK("spmv_dot_f64");
     return PACKSELL_OK;
 }
 

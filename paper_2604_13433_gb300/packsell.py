@@ -52,6 +52,18 @@ class Info(ctypes.Structure):
                 ("col", ctypes.c_void_p), ("offset", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
 
 
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("m_in", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("relres_true", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
 _lib = None
 
 # symbol -> (restype, argtypes)
@@ -73,6 +85,8 @@ SIGNATURES = {
     "packsell_set_spmv_variant": (ctypes.c_int, [_P, _I32]),
     "packsell_check_status": (ctypes.c_int, [_P, _P]),
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
+    "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
+    "packsell_pcg": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
 }
 
 
@@ -305,3 +319,48 @@ def packsell_arrays(A: PackSELLMatrix):
         pos += np.dtype(dt).itemsize * A.n_words
         out["col"] = np.frombuffer(blob, np.int32, A.n_words, pos)
     return out
+
+
+def packsell_pcg_workspace_bytes(n: int, m_in: int = 0, has_diag: bool = False,
+                                 max_iters: int = 1000) -> int:
+    return int(lib().packsell_pcg_workspace_bytes(n, m_in, int(has_diag), max_iters))
+
+
+def packsell_pcg(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tensor | None = None, *,
+                 A_inner: PackSELLMatrix | None = None, inv_diag: torch.Tensor | None = None,
+                 rtol: float = 1e-10, m_in: int = 0, max_iters: int = 1000,
+                 check_every: int | None = None, use_graph: bool = True,
+                 workspace: torch.Tensor | None = None, history: bool = False,
+                 check: bool = True, stream=None):
+    """Solve A x = b (see the C header). m_in = 0: FP64 Jacobi PCG on A_outer;
+    m_in > 0: inner-outer CG with m_in FP32 PCG iterations on A_inner.
+
+    Returns (x, info) with info = dict(iters, inner_iters, relres, relres_true,
+    seconds, status[, hist]). With check=True a status other than OK raises.
+    """
+    n = A_outer.n
+    if x is None:
+        x = torch.zeros(n, dtype=torch.float64, device=b.device)
+    if check_every is None:
+        check_every = 1 if m_in > 0 else 10
+    opts = SolveOpts(float(rtol), int(m_in), int(max_iters), int(check_every), int(use_graph))
+    res = SolveResult()
+    hist = (ctypes.c_double * (max_iters + 1))() if history else None
+    wptr, wbytes = None, 0
+    if workspace is not None:
+        if not workspace.is_cuda:
+            raise TypeError("workspace must be a CUDA tensor")
+        wptr, wbytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    code = lib().packsell_pcg(
+        A_outer.handle, A_inner.handle if A_inner is not None else None,
+        _dev(inv_diag, torch.float64, "inv_diag", n) if inv_diag is not None else None,
+        _dev(b, torch.float64, "b", n), _dev(x, torch.float64, "x", n), ctypes.byref(opts),
+        wptr, wbytes, hist, ctypes.byref(res), _stream(stream))
+    info = {"iters": res.iters, "inner_iters": res.inner_iters, "relres": res.relres,
+            "relres_true": res.relres_true, "seconds": res.seconds,
+            "status": STATUS.get(code, str(code))}
+    if history:
+        info["hist"] = [hist[i] for i in range(min(res.iters, max_iters) + 1)]
+    if check and code != 0:
+        raise PackSELLError(code, lib().packsell_last_error().decode())
+    return x, info
