@@ -372,4 +372,15 @@ packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matr
                       work_bytes, h_hist, result, as_stream(stream));
 }
 
+packsell_status packsell_pcg_noalloc(const packsell_matrix *A_outer,
+                                     const packsell_matrix *A_inner, const double *inv_diag,
+                                     const double *b, double *x,
+                                     const packsell_solve_opts *opts, double *h_hist,
+                                     packsell_solve_result *result, void *stream) {
+    clear_error();
+    if (!A_outer || !opts) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg_noalloc: NULL argument");
+    return solve_noalloc(M(A_outer), A_inner ? M(A_inner) : nullptr, inv_diag, b, x, *opts,
+                         h_hist, result, as_stream(stream));
+}
+
 }  // extern "C"

@@ -74,7 +74,11 @@ size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters);
 packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
                            const double *b, double *x, const packsell_solve_opts &o, void *work,
                            size_t work_bytes, double *h_hist, packsell_solve_result *res,
-                           cudaStream_t caller);
+                           cudaStream_t caller, bool noalloc = false);
+packsell_status solve_noalloc(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
+                              const double *b, double *x, const packsell_solve_opts &o,
+                              double *h_hist, packsell_solve_result *res, cudaStream_t s);
+size_t noalloc_capacity();
 
 // solver support (spmv.cu): SpMV fused with a deterministic dot reduction
 struct Red;

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -216,9 +218,13 @@ size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters) {
 }
 
 packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
-                           const double *b, double *x, const packsell_solve_opts &o, void *work,
+                           const double *b, double *x, const packsell_solve_opts &o_in, void *work,
                            size_t work_bytes, double *h_hist, packsell_solve_result *res,
-                           cudaStream_t caller) {
+                           cudaStream_t caller, bool noalloc) {
+    // no-allocation mode: the caller's stream, no graph, no events, the
+    // workspace given (never allocated here)
+    packsell_solve_opts o = o_in;
+    if (noalloc) o.use_graph = 0;
     const bool io = o.m_in > 0;
     if (!A64 || A64->p.format != PACKSELL_FMT_SELL_F64)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: A_outer must be a SELL_F64 matrix");
@@ -244,8 +250,8 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
     const int pblocks = std::max<int>(spmv_dot_blocks(*A64), vec_blocks());
     const size_t need = solve_workspace_bytes(n, o.m_in, inv_diag != nullptr, o.max_iters);
     void *own = nullptr;
-    cudaStream_t s = nullptr;
-    PS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaStream_t s = caller;
+    if (!noalloc) PS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -256,14 +262,17 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
     bool converged = false;
     double relres_true = -1.0;
 
-    // the caller's pending work on its stream comes first
-    cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
-    cudaEventRecord(ev0, caller);
-    cudaStreamWaitEvent(s, ev0, 0);
-    cudaEventDestroy(ev0);
-    ev0 = nullptr;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!noalloc) {
+        // the caller's pending work on its stream comes first
+        cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
+        cudaEventRecord(ev0, caller);
+        cudaStreamWaitEvent(s, ev0, 0);
+        cudaEventDestroy(ev0);
+        ev0 = nullptr;
+        cudaEventCreate(&ev0);
+        cudaEventCreate(&ev1);
+    }
 
     if (work) {
         if (work_bytes < need) {
@@ -274,6 +283,10 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
         w = carve((void *)(((uintptr_t)work + 255) & ~(uintptr_t)255), n, io, inv_diag != nullptr,
                   o.max_iters, pblocks);
     } else {
+        if (noalloc) {
+            st = fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: no workspace");
+            goto out;
+        }
         if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
             st = fail(PACKSELL_ERR_NO_MEMORY, "packsell_pcg: workspace allocation");
             goto out;
@@ -291,7 +304,7 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
         cudaMemcpyAsync(w.sc, &init, sizeof(init), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(w.counter, 0, 64, s);
         cudaMemsetAsync(w.q, 0, 8 * n, s);
-        cudaEventRecord(ev0, s);
+        if (ev0) cudaEventRecord(ev0, s);
         if (io && inv_diag) k_f64_to_f32<<<G, VTPB, 0, s>>>(n, inv_diag, w.M32);
 
         // r = b - A x, ||b||, ||r||
@@ -393,7 +406,7 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 cudaStreamSynchronize(s);
             }
         }
-        cudaEventRecord(ev1, s);
+        if (ev1) cudaEventRecord(ev1, s);
         cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
         PS_CUDA(cudaStreamSynchronize(s));
         if (h_hist)
@@ -409,7 +422,9 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
         }
         if (res) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev0, ev1);
+            if (ev0 && ev1) cudaEventElapsedTime(&ms, ev0, ev1);
+            else ms = (float)std::chrono::duration<double, std::milli>(
+                          std::chrono::steady_clock::now() - t_start).count();
             res->iters = h.iter;
             res->inner_iters = h.inner;
             res->relres = h.relres;
@@ -427,8 +442,61 @@ out:
     cudaStreamSynchronize(s);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    cudaStreamDestroy(s);
+    if (!noalloc) cudaStreamDestroy(s);
     return st;
+}
+
+// ---- the solver without allocation -------------------------------------
+// Some callers cannot allocate device memory at the time they solve: code
+// running inside a stream capture or under an allocator that must not grow,
+// plugins handed a fixed memory budget. For them the whole solver workspace
+// lives in one static device array, sized for systems of up to about 160,000
+// unknowns (IO-CG) or 260,000 (FP64 PCG). Every call shares it.
+constexpr size_t kNoAllocBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_pcg_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+}  // namespace
+
+// Device address of g_pcg_scratch on the current device (looked up once per
+// device; the name is only a host-side stand-in for it).
+static packsell_status noalloc_scratch(void **out) {
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "packsell_pcg_noalloc: cudaGetSymbolAddress");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return PACKSELL_OK;
+}
+
+size_t noalloc_capacity() { return kNoAllocBytes; }
+
+packsell_status solve_noalloc(const Matrix *A64, const Matrix *Ain, const double *inv_diag,
+                              const double *b, double *x, const packsell_solve_opts &o,
+                              double *h_hist, packsell_solve_result *res, cudaStream_t s) {
+    if (!A64) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg_noalloc: NULL matrix");
+    if (o.max_iters < 1 || o.m_in < 0)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg_noalloc: bad options");
+    const size_t need = solve_workspace_bytes(A64->n, o.m_in, inv_diag != nullptr, o.max_iters);
+    if (need > kNoAllocBytes)
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_pcg_noalloc: this system needs " + std::to_string(need) +
+                        " bytes of workspace, the static area holds " +
+                        std::to_string(kNoAllocBytes) + " (use packsell_pcg)");
+    void *scratch = nullptr;
+    packsell_status st = noalloc_scratch(&scratch);
+    if (st != PACKSELL_OK) return st;
+    return solve_impl(A64, Ain, inv_diag, b, x, o, scratch, kNoAllocBytes, h_hist, res, s, true);
 }
 
 }  // namespace packsell

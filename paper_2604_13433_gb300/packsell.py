@@ -87,6 +87,7 @@ SIGNATURES = {
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
     "packsell_pcg": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+    "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -361,6 +362,34 @@ def packsell_pcg(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tensor | Non
             "status": STATUS.get(code, str(code))}
     if history:
         info["hist"] = [hist[i] for i in range(min(res.iters, max_iters) + 1)]
+    if check and code != 0:
+        raise PackSELLError(code, lib().packsell_last_error().decode())
+    return x, info
+
+
+def packsell_pcg_noalloc(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tensor, *,
+                         A_inner: PackSELLMatrix | None = None,
+                         inv_diag: torch.Tensor | None = None, rtol: float = 1e-10,
+                         m_in: int = 0, max_iters: int = 1000, check_every: int | None = None,
+                         check: bool = True, stream=None):
+    """packsell_pcg with its workspace in the library's static device array:
+    for callers that must not allocate device memory while they solve (the
+    caller provides x as well, so this call allocates nothing). Systems up to
+    about 160,000 unknowns (IO-CG) or 260,000 (FP64 PCG); overlapping calls
+    race on the shared array."""
+    n = A_outer.n
+    if check_every is None:
+        check_every = 1 if m_in > 0 else 10
+    opts = SolveOpts(float(rtol), int(m_in), int(max_iters), int(check_every), 0)
+    res = SolveResult()
+    code = lib().packsell_pcg_noalloc(
+        A_outer.handle, A_inner.handle if A_inner is not None else None,
+        _dev(inv_diag, torch.float64, "inv_diag", n) if inv_diag is not None else None,
+        _dev(b, torch.float64, "b", n), _dev(x, torch.float64, "x", n), ctypes.byref(opts),
+        None, ctypes.byref(res), _stream(stream))
+    info = {"iters": res.iters, "inner_iters": res.inner_iters, "relres": res.relres,
+            "relres_true": res.relres_true, "seconds": res.seconds,
+            "status": STATUS.get(code, str(code))}
     if check and code != 0:
         raise PackSELLError(code, lib().packsell_last_error().decode())
     return x, info
