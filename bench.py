@@ -35,7 +35,9 @@ from paper_2604_13433_gb300 import inputs as I  # noqa: E402
 GRID = 128
 WORKLOAD = "stencil27_128^3_spmv"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ("spmv.cu", "device.cuh")
+KERNEL_SOURCES = ("spmv.cu", "device.cuh", "reduce.cuh")
+KERNEL_NAMES = {1: "k_spmv_packed", 2: "k_spmv_bulk", 3: "k_spmv_bulk", 4: "k_spmv_bulk",
+                5: "k_spmv_prefetch", 6: "k_spmv_prefetch", 7: "k_spmv_dual", 8: "k_spmv_dual"}
 
 
 def parse():
@@ -46,6 +48,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the solver section")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="SpMV variant of the headline matrix (0: autotune)")
+    ap.add_argument("--formats", default="all",
+                    help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
+                         "e8m15), 'all' or 'none'")
+    ap.add_argument("--pcg-grid", type=int, default=256, help="7-point Poisson grid side")
+    ap.add_argument("--pcg-min", type=int, default=20, help="inner iterations of IO-CG")
     return ap.parse_args()
 
 
@@ -193,6 +204,38 @@ def cpu_baseline(csr, deq, x, nbytes, budget_s=12.0):
                       "algorithmic bytes"}
 
 
+def pcg_section(ps, torch, dev, grid, m_in):
+    """Time to a true relative residual of 1e-10 on the 7-point variable-
+    coefficient Poisson problem (log-normal face coefficients, symmetrically
+    scaled, rhs U(-1, 1)): FP64 PCG vs IO-CG with FP32 inner PCG on PackSELL
+    FP16, PackSELL E8M11 and FP32 SELL copies of the matrix."""
+    csr = I.poisson7_varcoef(grid, seed=0)
+    b_h = I.uniform(csr.n, seed=1).astype(np.float64)
+    rp = torch.from_numpy(csr.rowptr).to(dev)
+    cl = torch.from_numpy(csr.col).to(dev)
+    vl = torch.from_numpy(csr.val).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    A64 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f64")
+    out = {"workload": f"poisson7_varcoef_{grid}^3", "n": csr.n, "nnz": csr.nnz,
+           "rtol": 1e-10, "m_in": m_in}
+    x = torch.zeros(csr.n, dtype=torch.float64, device=dev)
+    _, info = ps.packsell_pcg(A64, b, x, rtol=1e-10, max_iters=20000, check_every=20)
+    out["fp64_pcg"] = {k: info[k] for k in ("seconds", "iters", "relres_true")}
+    base = info["seconds"]
+    for name, fmt, D in (("iocg_fp16", "fp16", 15), ("iocg_e8m11", "e8my", 11),
+                         ("iocg_sell_f32", "sell_f32", 15)):
+        Ain = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D)
+        x.zero_()
+        _, info = ps.packsell_pcg(A64, b, x, A_inner=Ain, m_in=m_in, rtol=1e-10,
+                                  max_iters=5000, check=False)
+        out[name] = {k: info[k] for k in ("seconds", "iters", "inner_iters", "relres_true",
+                                          "status")}
+        out[name]["speedup_vs_fp64_pcg"] = base / info["seconds"] if info["seconds"] else None
+        out[name]["inner_words"] = Ain.n_words
+        del Ain
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -264,18 +307,25 @@ def run_ours(args):
     common = dict(C=32, sigma=256, explicit_perm=True)
     A16 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="fp16", D=15, **common)
     y = torch.empty(csr.n, dtype=torch.float32, device=dev)
-    tuned = ps.packsell_tune_spmv(A16, x, y, reps=50)  # variant 0 runs the fastest
+    if args.variant:
+        ps.packsell_set_spmv_variant(A16, args.variant)
+        tuned = {args.variant: 0.0}
+    else:
+        tuned = ps.packsell_tune_spmv(A16, x, y, reps=50)  # variant 0 runs the fastest
     B16 = spmv_bytes(A16, False)
 
     formats = {}
     with Clocks(local) as clk:
         ms16, total16 = time_launches(torch, lambda: ps.packsell_spmv(A16, x, y), K, W)
-        for name, fmt, D in (("sell_f32", "sell_f32", 15), ("fp16_v1", "fp16", 15),
-                             ("fp16_v2", "fp16", 15), ("fp16_v3", "fp16", 15),
-                             ("fp16_v4", "fp16", 15), ("fp16_v5", "fp16", 15),
-                             ("fp16_v6", "fp16", 15),
-                             ("e8m7", "e8my", 15),
-                             ("e8m11", "e8my", 11), ("e8m15", "e8my", 7)):
+        sweep = (("sell_f32", "sell_f32", 15), ("fp16_v1", "fp16", 15),
+                 ("fp16_v2", "fp16", 15), ("fp16_v3", "fp16", 15), ("fp16_v4", "fp16", 15),
+                 ("fp16_v5", "fp16", 15), ("fp16_v6", "fp16", 15), ("fp16_v7", "fp16", 15),
+                 ("fp16_v8", "fp16", 15), ("e8m7", "e8my", 15),
+                 ("e8m11", "e8my", 11), ("e8m15", "e8my", 7))
+        if args.formats != "all":
+            keep = set(args.formats.split(",")) if args.formats != "none" else set()
+            sweep = tuple(f for f in sweep if f[0] in keep)
+        for name, fmt, D in sweep:
             A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D, **common)
             if name.startswith("fp16_v"):
                 ps.packsell_set_spmv_variant(A, int(name[-1]))
@@ -297,13 +347,15 @@ def run_ours(args):
             ps.packsell_spmv(A16, xd, y)
             yp.copy_(y, non_blocking=True)
 
-        ms_e2e, _ = time_launches(torch, e2e_step, max(K // 10, 10), max(W // 10, 3))
-    sell = formats["sell_f32"]
-    for v in formats.values():
-        v["footprint_vs_sell"] = v["bytes"] / sell["bytes"]
+        ms_e2e = None
+        if not args.no_e2e:
+            ms_e2e, _ = time_launches(torch, e2e_step, max(K // 10, 10), max(W // 10, 3))
+    sell = formats.get("sell_f32")
     formats["fp16"] = {"GBps": B16 / ms16 / 1e6, "GFLOPs": 2 * csr.nnz / ms16 / 1e6,
                        "us": ms16 * 1e3, "bytes": B16, "words": A16.n_words,
-                       "dummies": A16.n_dummies, "footprint_vs_sell": B16 / sell["bytes"]}
+                       "dummies": A16.n_dummies, "footprint_vs_sell": None}
+    for v in formats.values():
+        v["footprint_vs_sell"] = v["bytes"] / sell["bytes"] if sell else None
 
     # whole-job numbers: max time over ranks, units summed over ranks
     t_step_ms = total16 / K
@@ -312,6 +364,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_step_ms = float(t.item())
     value = world * B16 / t_step_ms / 1e6
+    variant_used = min(tuned, key=tuned.get)
     peak, peak_src = measured_peaks()
     achieved = B16 / ms16 / 1e6
     line = {
@@ -321,21 +374,23 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": csr.n, "nnz": csr.nnz, "format": "fp16 D=15",
                    "C": 32, "sigma": 256, "perm": "explicit", "words": A16.n_words,
-                   "spmv_variant": min(tuned, key=tuned.get),
+                   "spmv_variant": variant_used,
                    "l2": "inputs larger than L2 (packed matrix 224 MB > 129 MB)",
                    "parallelism": f"replicas x{world}"},
-        "speedup_vs_sell_f32": sell["us"] / formats["fp16"]["us"],
+        "speedup_vs_sell_f32": sell["us"] / formats["fp16"]["us"] if sell else None,
         "formats": formats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "frac_of_8TBps_spec": achieved / 8000.0,
-                     "kernel": "k_spmv_packed<FP16>",
-                     "traffic": profiled_traffic("k_spmv_packed_fp16")},
-        "e2e": {"value": B16 / ms_e2e / 1e6, "unit": "GB/s",
+                     "kernel": KERNEL_NAMES.get(variant_used, "k_spmv"),
+                     "traffic": profiled_traffic(KERNEL_NAMES.get(variant_used, "k_spmv"))},
+        "e2e": {"value": B16 / ms_e2e / 1e6 if ms_e2e else None, "unit": "GB/s",
                 "h2d_bytes_per_step": 4 * csr.m, "d2h_bytes_per_step": 4 * csr.n},
         "gpu_launches": K,
         "clocks": clk.summary(),
     }
+    if not args.no_pcg:
+        line["pcg"] = pcg_section(ps, torch, dev, args.pcg_grid, args.pcg_min)
     if rank == 0 and not args.no_cpu:
         import oracle as O
 

@@ -183,14 +183,16 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     8/2/4 KB). Bulk variants need a PackSELL matrix with C = 32;
  *   5, 6 thread-per-row with row register prefetch: 16 (5) or 32 (6) words
  *     of a row are loaded at once before any is decoded (PackSELL matrices,
- *     C = 32). */
+ *     C = 32);
+ *   7, 8 dual-row persistent: each thread loads two rows (from two slices)
+ *     together, 12 (7) or 16 (8) words of each per round (PackSELL, C = 32). */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant for this matrix: time every available variant
  * (`reps` launches each after a warm-up, CUDA events on `stream`) on the
  * caller's x [m] and y [n], and make variant 0 run the fastest. Writes y.
  * Synchronises `stream`. If h_times is not NULL it receives the average
- * milliseconds per launch of variants 1..6 (0 where unavailable). */
+ * milliseconds per launch of variants 1..8 (0 where unavailable). */
 packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
                                    float *h_times, void *stream);
 
@@ -259,9 +261,11 @@ size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag,
  *   h_hist  : NULL or host double [max_iters + 1]: recurrence residual after
  *             each outer (PCG) iteration, entry 0 the initial one
  * IO-CG: flexible CG (one previous direction) in FP64; its preconditioner is
- * m_in PCG iterations in FP32 from zero on r / ||r||_2 with A_inner. Dot
- * products accumulate in FP64; the residual is replaced by the true one if
- * the recurrence claims convergence before b - A x does.
+ * m_in PCG iterations in FP32 from zero on r / ||r||_2 with A_inner. Outer
+ * dot products are FP64 throughout; inner ones sum each thread's elements in
+ * FP32 and combine the partial sums in FP64 (deterministically). The
+ * residual is replaced by the true one if the recurrence claims convergence
+ * before b - A x does.
  * Runs on a private stream after the caller's pending work; SYNCHRONISES.
  * Returns NOT_CONVERGED after max_iters (x holds the last iterate),
  * BREAKDOWN on p^T A p <= 0 or a non-finite residual. */

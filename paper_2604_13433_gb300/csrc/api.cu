@@ -242,7 +242,7 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     clear_error();
-    if (!A || variant < 0 || variant > 3 + Matrix::kBulkVariants)
+    if (!A || variant < 0 || variant > 8)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
     if (variant >= 2 && variant <= 4 && !m->part[variant - 2])
@@ -250,7 +250,7 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
                     "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
     if (variant >= 5 && (!is_packed(m->p.format) || m->p.C != 32))
         return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_set_spmv_variant: the prefetch kernel needs a PackSELL matrix with C = 32");
+                    "packsell_set_spmv_variant: variants 5-8 need a PackSELL matrix with C = 32");
     m->variant = variant;
     return PACKSELL_OK;
 }
@@ -262,7 +262,7 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
     cudaStream_t s = as_stream(stream);
-    const int nvar = 3 + Matrix::kBulkVariants;
+    const int nvar = 8;
     if (h_times)
         for (int v = 0; v < nvar; ++v) h_times[v] = 0.f;
     cudaEvent_t e0, e1;

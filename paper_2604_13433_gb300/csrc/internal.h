@@ -82,6 +82,7 @@ size_t noalloc_capacity();
 
 // solver support (spmv.cu): SpMV fused with a deterministic dot reduction
 struct Red;
+int reduce_blocks();
 int spmv_dot_blocks(const Matrix &A);
 packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
                              cudaStream_t s);

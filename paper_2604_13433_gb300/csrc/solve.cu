@@ -56,13 +56,13 @@ template <typename T>
 __global__ void __launch_bounds__(VTPB)
     k_pcg_init(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
                Red red) {
-    double rz = 0.0;
+    T rz = 0;
     PS_FOR(i, n) {
         const T z = M ? M[i] * r[i] : r[i];
         p[i] = z;
-        rz += (double)r[i] * (double)z;
+        rz = fma(r[i], z, rz);
     }
-    reduce_publish(red, rz, 0.0);
+    reduce_publish(red, (double)rz, 0.0);
 }
 
 // Inner PCG start: r_in = r / ||r|| (rounded to FP32), x_in = 0, p = M r_in.
@@ -71,48 +71,164 @@ __global__ void __launch_bounds__(VTPB)
                  float *__restrict__ xi, float *__restrict__ ri, float *__restrict__ pi, Red red) {
     if (red.sc->done) return;
     const double inv = red.sc->rnorm > 0.0 ? 1.0 / red.sc->rnorm : 0.0;
-    double rz = 0.0;
+    float rz = 0.f;
     PS_FOR(i, n) {
         const float r = (float)(r64[i] * inv);
         const float z = M ? M[i] * r : r;
         xi[i] = 0.f;
         ri[i] = r;
         pi[i] = z;
-        rz += (double)r * (double)z;
+        rz = fmaf(r, z, rz);
     }
-    reduce_publish(red, rz, 0.0);
+    reduce_publish(red, (double)rz, 0.0);
 }
 
-// x += alpha p, r -= alpha q; s1 = r.z (z = M r), s2 = r.r
+// Vector kernels move VW = 16 / sizeof(T) elements per 128-bit access and
+// handle two such vectors per loop trip, so each thread keeps several
+// 128-bit loads in flight (a streaming kernel on GB300 needs ~45 KB in flight
+// per SM). Pointers must be 16-byte aligned (checked by the launcher, which
+// falls back to one element per access otherwise).
 template <typename T>
+struct V;
+template <>
+struct V<float> {
+    using type = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct V<double> {
+    using type = double2;
+    static constexpr int W = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ldv(const T *p, int64_t v, T (&e)[V<T>::W]) {
+    *reinterpret_cast<typename V<T>::type *>(e) = reinterpret_cast<const typename V<T>::type *>(p)[v];
+}
+template <typename T>
+__device__ __forceinline__ void stv(T *p, int64_t v, const T (&e)[V<T>::W]) {
+    reinterpret_cast<typename V<T>::type *>(p)[v] = *reinterpret_cast<const typename V<T>::type *>(e);
+}
+
+// x += alpha p, r -= alpha q; s1 = r.z (z = M r), s2 = r.r. Each thread sums
+// its own elements in T (FP32 for the inner PCG: GB300's FP64 rate is too low
+// to spend per element) and the block and grid sums are FP64.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(VTPB)
     k_update(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
              const T *__restrict__ q, const T *__restrict__ M, Red red) {
     if (red.sc->done) return;
     const T a = (T)red.sc->alpha;
-    double rz = 0.0, rr = 0.0;
-    PS_FOR(i, n) {
+    T rz = 0, rr = 0;
+    auto one = [&](int64_t i) {
         x[i] = fma(a, p[i], x[i]);
         const T ri = fma(-a, q[i], r[i]);
         r[i] = ri;
         const T z = M ? M[i] * ri : ri;
-        rz += (double)ri * (double)z;
-        rr += (double)ri * (double)ri;
+        rz = fma(ri, z, rz);
+        rr = fma(ri, ri, rr);
+    };
+    if (VEC) {
+        constexpr int W = V<T>::W;
+        const int64_t nv = n / W, tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t st = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t v0 = tid; v0 < nv; v0 += 2 * st) {
+            T xe[2][W], pe[2][W], qe[2][W], re[2][W], me[2][W];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t v = v0 + h * st;
+                if (v < nv) {
+                    ldv(x, v, xe[h]);
+                    ldv(p, v, pe[h]);
+                    ldv(q, v, qe[h]);
+                    ldv(r, v, re[h]);
+                    if (M) ldv(M, v, me[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t v = v0 + h * st;
+                if (v < nv) {
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        xe[h][k] = fma(a, pe[h][k], xe[h][k]);
+                        re[h][k] = fma(-a, qe[h][k], re[h][k]);
+                        const T z = M ? me[h][k] * re[h][k] : re[h][k];
+                        rz = fma(re[h][k], z, rz);
+                        rr = fma(re[h][k], re[h][k], rr);
+                    }
+                    stv(x, v, xe[h]);
+                    stv(r, v, re[h]);
+                }
+            }
+        }
+        for (int64_t i = nv * W + tid; i < n; i += st) one(i);
+    } else {
+        PS_FOR(i, n) one(i);
     }
-    reduce_publish(red, rz, rr);
+    reduce_publish(red, (double)rz, (double)rr);
 }
 
 // p = M r + beta p
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(VTPB)
     k_pupdate(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
               const SolveScalars *sc) {
     if (sc->done) return;
     const T b = (T)sc->beta;
-    PS_FOR(i, n) {
-        const T z = M ? M[i] * r[i] : r[i];
-        p[i] = fma(b, p[i], z);
+    if (VEC) {
+        constexpr int W = V<T>::W;
+        const int64_t nv = n / W, tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t st = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t v0 = tid; v0 < nv; v0 += 2 * st) {
+            T re[2][W], pe[2][W], me[2][W];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t v = v0 + h * st;
+                if (v < nv) {
+                    ldv(r, v, re[h]);
+                    ldv(p, v, pe[h]);
+                    if (M) ldv(M, v, me[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t v = v0 + h * st;
+                if (v < nv) {
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        pe[h][k] = fma(b, pe[h][k], M ? me[h][k] * re[h][k] : re[h][k]);
+                    stv(p, v, pe[h]);
+                }
+            }
+        }
+        for (int64_t i = nv * W + tid; i < n; i += st) p[i] = fma(b, p[i], M ? M[i] * r[i] : r[i]);
+    } else {
+        PS_FOR(i, n) {
+            const T z = M ? M[i] * r[i] : r[i];
+            p[i] = fma(b, p[i], z);
+        }
     }
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+void launch_update(int G, cudaStream_t q, int64_t n, T *x, T *r, const T *p, const T *qv,
+                   const T *M, const Red &red) {
+    if (aligned16(x) && aligned16(r) && aligned16(p) && aligned16(qv) && (!M || aligned16(M)))
+        k_update<T, true><<<G, VTPB, 0, q>>>(n, x, r, p, qv, M, red);
+    else
+        k_update<T, false><<<G, VTPB, 0, q>>>(n, x, r, p, qv, M, red);
+}
+
+template <typename T>
+void launch_pupdate(int G, cudaStream_t q, int64_t n, const T *r, const T *M, T *p,
+                    const SolveScalars *sc) {
+    if (aligned16(r) && aligned16(p) && (!M || aligned16(M)))
+        k_pupdate<T, true><<<G, VTPB, 0, q>>>(n, r, M, p, sc);
+    else
+        k_pupdate<T, false><<<G, VTPB, 0, q>>>(n, r, M, p, sc);
 }
 
 // Outer: z = ||r|| x_in (FP64), s1 = z.q (q = A p of the previous direction)
@@ -200,20 +316,12 @@ Work carve(void *base, int64_t n, bool inner, bool has_m, int max_iters, int pbl
 
 // fixed grid of the vector kernels (4 blocks per SM): the reductions are
 // deterministic for a given device
-int vec_blocks() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        sms = 160;  // no device yet: size for a large part
-    }
-    return std::max(1, sms * 4);
-}
+int vec_blocks() { return reduce_blocks(); }
 
 }  // namespace
 
 size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters) {
-    const int pblocks = std::max<int>((int)((n + 255) / 256), vec_blocks());
+    const int pblocks = vec_blocks();
     return carve(nullptr, n, m_in > 0, has_m != 0, max_iters, pblocks).bytes + 256;
 }
 
@@ -247,7 +355,7 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
     }
     if (!b || !x) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: NULL vector");
 
-    const int pblocks = std::max<int>(spmv_dot_blocks(*A64), vec_blocks());
+    const int pblocks = vec_blocks();
     const size_t need = solve_workspace_bytes(n, o.m_in, inv_diag != nullptr, o.max_iters);
     void *own = nullptr;
     cudaStream_t s = caller;
@@ -330,10 +438,9 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                     for (int k = 0; k < o.m_in; ++k) {
                         packsell_status e = spmv_dot_f32(*Ain, w.pi, w.qi, red(FIN_PQ_ALPHA), q);
                         if (e != PACKSELL_OK) return e;
-                        k_update<float><<<G, VTPB, 0, q>>>(n, w.xi, w.ri, w.pi, w.qi, w.M32,
-                                                           red(FIN_RZ_BETA));
+                        launch_update<float>(G, q, n, w.xi, w.ri, w.pi, w.qi, w.M32, red(FIN_RZ_BETA));
                         if (k + 1 < o.m_in)
-                            k_pupdate<float><<<G, VTPB, 0, q>>>(n, w.ri, w.M32, w.pi, w.sc);
+                            launch_pupdate<float>(G, q, n, w.ri, w.M32, w.pi, w.sc);
                     }
                     k_outer_z<<<G, VTPB, 0, q>>>(n, w.xi, w.z, w.q, red(FIN_ZQ_BETA));
                     k_outer_p<<<G, VTPB, 0, q>>>(n, w.z, w.p, w.sc);
@@ -343,9 +450,8 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 } else {
                     packsell_status e = spmv_dot_f64(*A64, w.p, w.q, nullptr, red(FIN_PQ_ALPHA_64), q);
                     if (e != PACKSELL_OK) return e;
-                    k_update<double><<<G, VTPB, 0, q>>>(n, x, w.r, w.p, w.q, inv_diag,
-                                                        red(FIN_RZ_BETA_RR));
-                    k_pupdate<double><<<G, VTPB, 0, q>>>(n, w.r, inv_diag, w.p, w.sc);
+                    launch_update<double>(G, q, n, x, w.r, w.p, w.q, inv_diag, red(FIN_RZ_BETA_RR));
+                    launch_pupdate<double>(G, q, n, w.r, inv_diag, w.p, w.sc);
                 }
             }
             PS_LAUNCH_CHECK("packsell_pcg: iteration");

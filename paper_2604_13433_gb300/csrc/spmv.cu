@@ -102,9 +102,11 @@ __global__ void __launch_bounds__(TPB, MINB)
                     const void *__restrict__ perm, int perm_bytes, Decode dc,
                     const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
     if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double d1 = 0.0;
-    if (i < n) {
+    float d1 = 0.f;  // per-thread sum in FP32; block and grid sums in FP64
+    // one row per thread; the reducing form runs on a fixed grid and strides
+    // over rows (warps stay on whole slices) so its reduction is deterministic
+    const int stride = DOT ? gridDim.x * blockDim.x : n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int k = i / C, l = i - k * C;
         const int64_t s = offset[k];
         const int w = (int)((offset[k + 1] - s) / C);
@@ -130,9 +132,97 @@ __global__ void __launch_bounds__(TPB, MINB)
         if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
         else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
         y[io] = t;
-        if (DOT) d1 = (double)x[io] * (double)t;
+        if (DOT) d1 = fmaf(x[io], t, d1);
     }
-    if (DOT) reduce_publish(red, d1, 0.0);
+    if (DOT) reduce_publish(red, (double)d1, 0.0);
+}
+
+// Dual-row persistent SpMV: every thread handles two rows per loop trip, row
+// i (slice k) and row i + stride (another slice), in lockstep: the word loads
+// of both rows are issued before either is decoded, then both rows' gathers,
+// then both fused multiply-add chains. Twice the bytes in flight per thread
+// of the one-row prefetch kernel, on a persistent grid (the reducing form
+// runs on the fixed solver grid). PF words of each row per round.
+template <int FMT, int PF, int MINB, bool DOT = false>
+__global__ void __launch_bounds__(TPB, MINB)
+    k_spmv_dual(int n, int sigma, int sig_shift, long long k_left,
+                const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                const void *__restrict__ perm, int perm_bytes, Decode dc,
+                const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
+    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
+    float d1 = 0.f;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 2 * stride) {
+        const int i1 = i0 + stride;
+        const bool has1 = i1 < n;
+        const int k0 = i0 >> 5, k1 = i1 >> 5;
+        const int64_t s0 = offset[k0];
+        const int w0 = (int)((offset[k0 + 1] - s0) >> 5);
+        const int64_t s1 = has1 ? offset[k1] : 0;
+        const int w1 = has1 ? (int)((offset[k1 + 1] - s1) >> 5) : 0;
+        const uint32_t *__restrict__ p0 = pack + s0 + (i0 & 31);
+        const uint32_t *__restrict__ p1 = pack + s1 + (i1 & 31);
+        const int b0 = sig_shift >= 0 ? (i0 >> sig_shift) << sig_shift : (i0 / sigma) * sigma;
+        const int b1 = sig_shift >= 0 ? (i1 >> sig_shift) << sig_shift : (i1 / sigma) * sigma;
+        int c0 = (k_left < b0) ? (int)(b0 - k_left) : 0;
+        int c1 = (k_left < b1) ? (int)(b1 - k_left) : 0;
+        float t0 = 0.f, t1 = 0.f;
+        const int wm = w0 > w1 ? w0 : w1;
+        for (int j0 = 0; j0 < wm; j0 += PF) {
+            const int r0 = w0 - j0, r1 = w1 - j0;
+            uint32_t a[PF], b[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) a[u] = (u < r0) ? p0[(j0 + u) * 32] : 0u;
+#pragma unroll
+            for (int u = 0; u < PF; ++u) b[u] = (u < r1) ? p1[(j0 + u) * 32] : 0u;
+            bool fa[PF], fb[PF];
+            float xa[PF], xb[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) word_gather<FMT>(a[u], dc, x, c0, fa[u], xa[u]);
+#pragma unroll
+            for (int u = 0; u < PF; ++u) word_gather<FMT>(b[u], dc, x, c1, fb[u], xb[u]);
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+                if (fa[u]) t0 = fmaf(word_value<FMT>(a[u], dc), xa[u], t0);
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+                if (fb[u]) t1 = fmaf(word_value<FMT>(b[u], dc), xb[u], t1);
+        }
+        int o0 = i0, o1 = i1;
+        if (perm_bytes == 1) {
+            o0 = b0 + (int)((const uint8_t *)perm)[i0];
+            if (has1) o1 = b1 + (int)((const uint8_t *)perm)[i1];
+        } else if (perm_bytes == 2) {
+            o0 = b0 + (int)((const uint16_t *)perm)[i0];
+            if (has1) o1 = b1 + (int)((const uint16_t *)perm)[i1];
+        }
+        y[o0] = t0;
+        if (has1) y[o1] = t1;
+        if (DOT) {
+            d1 = fmaf(x[o0], t0, d1);
+            if (has1) d1 = fmaf(x[o1], t1, d1);
+        }
+    }
+    if (DOT) reduce_publish(red, (double)d1, 0.0);
+}
+
+template <int FMT, int PF, int MINB>
+packsell_status launch_dual(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+                            cudaStream_t s) {
+    static int blocks = 0;  // persistent grid: every block resident at once
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        PS_CUDA(cudaGetDevice(&dev));
+        PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_spmv_dual<FMT, PF, MINB>, TPB, 0));
+        blocks = sms * (per > 0 ? per : 1);
+    }
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    k_spmv_dual<FMT, PF, MINB><<<blocks, TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset,
+                                                      A.pack, perm, pb, make_decode(A), x, y);
+    PS_LAUNCH_CHECK("packsell_spmv (dual)");
+    return PACKSELL_OK;
 }
 
 template <int FMT, int PF, int MINB>
@@ -420,9 +510,9 @@ __global__ void __launch_bounds__(TPB)
                 const void *__restrict__ perm, int perm_bytes, const T *__restrict__ x,
                 T *__restrict__ y, const T *__restrict__ b = nullptr, Red red = Red{}) {
     if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double d1 = 0.0, d2 = 0.0;
-    if (i < n) {
+    T d1 = 0, d2 = 0;  // per-thread sums in T; block and grid sums in FP64
+    const int stride = DOT ? gridDim.x * blockDim.x : n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int k = i / C, l = i - k * C;
         const int64_t s = offset[k];
         const int w = (int)((offset[k + 1] - s) / C);
@@ -448,14 +538,15 @@ __global__ void __launch_bounds__(TPB)
         const int io = orig_row(i, sigma, perm, perm_bytes);
         y[io] = t;
         if (DOT) {
-            d1 = (double)x[io] * (double)t;
-            if (b) d2 = (double)x[io] * (double)b[io];
+            d1 = fma(x[io], t, d1);
+            if (b) d2 = fma(x[io], b[io], d2);
         }
     }
-    if (DOT) reduce_publish(red, d1, d2);
+    if (DOT) reduce_publish(red, (double)d1, (double)d2);
 }
 
-// Thread-per-row PackSELL SpMV fused with sum_i x_i y_i (solver use, any C).
+// Thread-per-row PackSELL SpMV fused with sum_i x_i y_i (solver use, any C),
+// on a fixed grid striding over rows.
 template <int FMT>
 __global__ void __launch_bounds__(TPB)
     k_spmv_packed_dot(int n, int C, int sigma, long long k_left,
@@ -463,9 +554,8 @@ __global__ void __launch_bounds__(TPB)
                       const void *__restrict__ perm, int perm_bytes, Decode dc,
                       const float *__restrict__ x, float *__restrict__ y, Red red) {
     if (red.sc->done) return;  // solver converged: idle (grid-uniform)
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double d1 = 0.0;
-    if (i < n) {
+    float d1 = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int k = i / C, l = i - k * C;
         const int64_t s = offset[k];
         const int w = (int)((offset[k + 1] - s) / C);
@@ -480,9 +570,9 @@ __global__ void __launch_bounds__(TPB)
         }
         const int io = orig_row(i, sigma, perm, perm_bytes);
         y[io] = t;
-        d1 = (double)x[io] * (double)t;
+        d1 = fmaf(x[io], t, d1);
     }
-    reduce_publish(red, d1, 0.0);
+    reduce_publish(red, (double)d1, 0.0);
 }
 
 // SpMM, k right-hand sides in chunks of KT accumulators per thread.
@@ -681,6 +771,16 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     int g = grid_for(A.n);
     const int var = A.variant == 0 ? A.auto_variant : A.variant;
+    if ((var == 7 || var == 8) && is_packed(A.p.format)) {
+        if (A.p.C != 32)
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the dual-row variants need C = 32");
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        if (var == 7)
+            return h ? launch_dual<PACKSELL_FMT_FP16, 12, 4>(A, perm, pb, x, y, s)
+                     : launch_dual<PACKSELL_FMT_E8MY, 12, 4>(A, perm, pb, x, y, s);
+        return h ? launch_dual<PACKSELL_FMT_FP16, 16, 3>(A, perm, pb, x, y, s)
+                 : launch_dual<PACKSELL_FMT_E8MY, 16, 3>(A, perm, pb, x, y, s);
+    }
     if ((var == 5 || var == 6) && is_packed(A.p.format)) {
         if (A.p.C != 32)
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the prefetch variants need C = 32");
@@ -818,11 +918,22 @@ packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u,
 }
 
 // ---- fused SpMV + dot launchers for the solvers (square, original order) ----
-int spmv_dot_blocks(const Matrix &A) { return grid_for(A.n); }
+// The reducing kernels run on a fixed grid of 4 blocks per SM.
+int reduce_blocks() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 160;  // no device yet: size for a large part
+    }
+    return std::max(1, sms * 4);
+}
+
+int spmv_dot_blocks(const Matrix &) { return reduce_blocks(); }
 
 packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
                              cudaStream_t s) {
-    const int g = grid_for(A.n);
+    const int g = reduce_blocks();
     const void *perm = A.perm;
     const int pb = A.perm_bytes;
     if (A.p.format == PACKSELL_FMT_SELL_F32) {
@@ -830,14 +941,26 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
                                                    (const float *)A.val, A.col, perm, pb, x, y,
                                                    nullptr, red);
     } else if (A.p.C == 32) {
+        // dual-row kernel; 12 words per round when every row fits
         const int sg = A.p.sigma;
         const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
-        if (A.p.format == PACKSELL_FMT_FP16)
-            k_spmv_prefetch<PACKSELL_FMT_FP16, 16, 32, 5, true><<<g, TPB, 0, s>>>(
-                (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
-        else
-            k_spmv_prefetch<PACKSELL_FMT_E8MY, 16, 32, 5, true><<<g, TPB, 0, s>>>(
-                (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y, red);
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        const Decode dc = make_decode(A);
+        if (A.max_width <= 12) {
+            if (h)
+                k_spmv_dual<PACKSELL_FMT_FP16, 12, 4, true><<<g, TPB, 0, s>>>(
+                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+            else
+                k_spmv_dual<PACKSELL_FMT_E8MY, 12, 4, true><<<g, TPB, 0, s>>>(
+                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+        } else {
+            if (h)
+                k_spmv_dual<PACKSELL_FMT_FP16, 16, 3, true><<<g, TPB, 0, s>>>(
+                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+            else
+                k_spmv_dual<PACKSELL_FMT_E8MY, 16, 3, true><<<g, TPB, 0, s>>>(
+                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+        }
     } else {
         if (A.p.format == PACKSELL_FMT_FP16)
             k_spmv_packed_dot<PACKSELL_FMT_FP16><<<g, TPB, 0, s>>>(
@@ -852,7 +975,7 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
 
 packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
                              const Red &red, cudaStream_t s) {
-    k_spmv_sell<double, true><<<grid_for(A.n), TPB, 0, s>>>(
+    k_spmv_sell<double, true><<<reduce_blocks(), TPB, 0, s>>>(
         (int)A.n, A.p.C, A.p.sigma, A.offset, (const double *)A.val, A.col, A.perm, A.perm_bytes, x,
         y, b, red);
     PS_LAUNCH_CHECK("spmv_dot_f64");
