@@ -203,6 +203,37 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batched SpMV: many matrices, one persistent launch                       */
+/* ---------------------------------------------------------------------- */
+/* The paper runs one matrix per launch; batching many small or uneven
+ * matrices into one launch is this library's extension of §4.4. */
+
+typedef struct packsell_batch packsell_batch; /* opaque plan */
+
+/* Build a plan for y_i = A_i x_i, i < count. A: host array of PackSELL
+ * matrices with C = 32 (FP16 and E8MY may be mixed); x, y: host arrays of
+ * device pointers (x_i float [m_i], y_i float [n_i]) bound to the plan. The
+ * plan uploads one descriptor per matrix and a work list of (matrix, slice
+ * range) items of about equal word counts; warps of one persistent launch
+ * take items round-robin. Reads each matrix's offsets (SYNCHRONISES
+ * `stream`). The matrices and vectors must outlive the plan. */
+packsell_status packsell_batch_create(int32_t count, const packsell_matrix *const *A,
+                                      const float *const *x, float *const *y, void *stream,
+                                      packsell_batch **out);
+
+/* One launch computing every y_i = A_i x_i of the plan (asynchronous; no
+ * allocation, so it can be captured in a CUDA graph). Each row is summed as
+ * packsell_spmv sums it (same bits). */
+packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream);
+
+/* Work-list statistics: total stored words, algorithmic bytes of one launch
+ * (words, offsets, perm, x and y once), number of work items. */
+packsell_status packsell_batch_info(const packsell_batch *B, int64_t *words, int64_t *bytes,
+                                    int32_t *items);
+
+packsell_status packsell_batch_destroy(packsell_batch *B);
+
+/* ---------------------------------------------------------------------- */
 /* Backward (adjoint) products                                              */
 /* ---------------------------------------------------------------------- */
 
@@ -219,6 +250,15 @@ packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *d
  * Needs a matrix encoded with keep_rowptr = 1. */
 packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, const float *u,
                                        const float *v, float *out, void *stream);
+
+/* out[q] = alpha * u_i * v_j in double for a SELL_F64 matrix encoded with
+ * keep_rowptr = 1 (u: double [n], v: double [m], out: double [nnz], CSR
+ * order): dL/dA on the pattern of x = A^-1 b is pattern_outer(-1, lam, x)
+ * with lam the adjoint solution of A^T lam = dL/dx. */
+packsell_status packsell_pattern_outer_f64(const packsell_matrix *A, double alpha,
+                                           const double *u, const double *v, double *out,
+                                           void *stream);
+
 
 /* ---------------------------------------------------------------------- */
 /* Solvers (§5.2.2): FP64 PCG and the mixed-precision inner-outer CG        */
@@ -242,6 +282,11 @@ typedef struct packsell_solve_result {
     double relres_true;  /* true residual ||b - A x|| / ||b|| at exit (FP64) */
     double seconds;      /* device time of the solve (CUDA events) */
 } packsell_solve_result;
+
+/* out[i] = 1 / a_ii (double [n]) for a square SELL_F64 matrix, in the
+ * original row order: the Jacobi preconditioner of packsell_pcg. Rows whose
+ * diagonal is missing or zero get 1. */
+packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream);
 
 /* Device workspace bytes packsell_pcg needs for n unknowns (has_diag: a Jacobi
  * preconditioner is passed). */

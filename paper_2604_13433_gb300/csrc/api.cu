@@ -357,6 +357,58 @@ packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, co
     return pattern_outer_impl(*M(A), alpha, u, v, out, as_stream(stream));
 }
 
+packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream) {
+    clear_error();
+    if (!A || (M(A)->n > 0 && !out)) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_inv_diag: NULL argument");
+    return inv_diag_impl(*M(A), out, as_stream(stream));
+}
+
+packsell_status packsell_pattern_outer_f64(const packsell_matrix *A, double alpha,
+                                           const double *u, const double *v, double *out,
+                                           void *stream) {
+    clear_error();
+    if (!A || (M(A)->nnz > 0 && (!u || !v || !out)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pattern_outer_f64: NULL argument");
+    return pattern_outer_f64_impl(*M(A), alpha, u, v, out, as_stream(stream));
+}
+
+packsell_status packsell_batch_create(int32_t count, const packsell_matrix *const *A,
+                                      const float *const *x, float *const *y, void *stream,
+                                      packsell_batch **out) {
+    clear_error();
+    if (!out || !A || !x || !y || count < 1)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create: bad argument");
+    *out = nullptr;
+    Batch *B = nullptr;
+    packsell_status st = batch_create(count, reinterpret_cast<const Matrix *const *>(A), x, y,
+                                      as_stream(stream), &B);
+    *out = reinterpret_cast<packsell_batch *>(B);
+    return st;
+}
+
+packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream) {
+    clear_error();
+    if (!B) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_spmv: NULL plan");
+    return batch_spmv(*reinterpret_cast<const Batch *>(B), as_stream(stream));
+}
+
+packsell_status packsell_batch_info(const packsell_batch *B, int64_t *words, int64_t *bytes,
+                                    int32_t *items) {
+    clear_error();
+    if (!B) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_info: NULL plan");
+    batch_stats(*reinterpret_cast<const Batch *>(B), words, bytes, items);
+    return PACKSELL_OK;
+}
+
+packsell_status packsell_batch_destroy(packsell_batch *B) {
+    clear_error();
+    if (B) {
+        cudaDeviceSynchronize();
+        batch_free(reinterpret_cast<Batch *>(B));
+    }
+    return PACKSELL_OK;
+}
+
 size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag, int32_t max_iters) {
     if (n < 0 || m_in < 0 || max_iters < 0) return 0;
     return solve_workspace_bytes(n, m_in, has_diag, max_iters);

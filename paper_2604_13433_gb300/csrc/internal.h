@@ -68,6 +68,17 @@ packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, f
 packsell_status spmv_t_impl(const Matrix &A, const float *dy, float *dx, cudaStream_t s);
 packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u, const float *v,
                                    float *out, cudaStream_t s);
+packsell_status inv_diag_impl(const Matrix &A, double *out, cudaStream_t s);
+packsell_status pattern_outer_f64_impl(const Matrix &A, double alpha, const double *u,
+                                       const double *v, double *out, cudaStream_t s);
+
+// batch.cu
+struct Batch;
+packsell_status batch_create(int count, const Matrix *const *A, const float *const *x,
+                             float *const *y, cudaStream_t s, Batch **out);
+packsell_status batch_spmv(const Batch &B, cudaStream_t s);
+void batch_free(Batch *B);
+void batch_stats(const Batch &B, int64_t *words, int64_t *bytes, int32_t *items);
 
 // solve.cu
 size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters);

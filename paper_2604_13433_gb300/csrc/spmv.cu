@@ -711,18 +711,19 @@ __global__ void __launch_bounds__(TPB)
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(TPB)
     k_pattern_outer_sell(int n, int C, int sigma, const int64_t *__restrict__ offset,
                          const int32_t *__restrict__ col, const void *__restrict__ perm,
-                         int perm_bytes, const int64_t *__restrict__ rowptr, float alpha,
-                         const float *__restrict__ u, const float *__restrict__ v,
-                         float *__restrict__ out) {
+                         int perm_bytes, const int64_t *__restrict__ rowptr, T alpha,
+                         const T *__restrict__ u, const T *__restrict__ v,
+                         T *__restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = i / C, l = i - k * C;
     int64_t s = offset[k];
     int io = orig_row(i, sigma, perm, perm_bytes);
-    float a = alpha * u[io];
+    T a = alpha * u[io];
     int64_t q0 = rowptr[io], len = rowptr[io + 1] - q0;
     for (int64_t j = 0; j < len; ++j) out[q0 + j] = a * v[col[s + j * C + l]];
 }
@@ -909,8 +910,11 @@ packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u,
                 A.rowptr, alpha, u, v, out);
             break;
         default:
-            k_pattern_outer_sell<<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset, A.col, perm,
-                                                   pb, A.rowptr, alpha, u, v, out);
+            if (A.p.format != PACKSELL_FMT_SELL_F32)
+                return fail(PACKSELL_ERR_INVALID_ARG,
+                            "packsell_pattern_outer: SELL_F64 needs packsell_pattern_outer_f64");
+            k_pattern_outer_sell<float><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset, A.col,
+                                                          perm, pb, A.rowptr, alpha, u, v, out);
             break;
     }
     PS_LAUNCH_CHECK("packsell_pattern_outer");
@@ -979,6 +983,51 @@ packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const 
         (int)A.n, A.p.C, A.p.sigma, A.offset, (const double *)A.val, A.col, A.perm, A.perm_bytes, x,
         y, b, red);
     PS_LAUNCH_CHECK("spmv_dot_f64");
+    return PACKSELL_OK;
+}
+
+packsell_status pattern_outer_f64_impl(const Matrix &A, double alpha, const double *u,
+                                       const double *v, double *out, cudaStream_t s) {
+    if (A.p.format != PACKSELL_FMT_SELL_F64)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pattern_outer_f64: matrix is not SELL_F64");
+    if (!A.rowptr)
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_pattern_outer_f64: matrix was encoded without keep_rowptr");
+    if (A.n == 0 || A.nnz == 0) return PACKSELL_OK;
+    k_pattern_outer_sell<double><<<grid_for(A.n), TPB, 0, s>>>(
+        (int)A.n, A.p.C, A.p.sigma, A.offset, A.col, A.perm, A.perm_bytes, A.rowptr, alpha, u, v, out);
+    PS_LAUNCH_CHECK("packsell_pattern_outer_f64");
+    return PACKSELL_OK;
+}
+
+namespace {
+// 1 / a_ii of a square SELL_F64 matrix (1 where the diagonal is absent or 0)
+__global__ void __launch_bounds__(TPB)
+    k_inv_diag(int n, int C, int sigma, const int64_t *__restrict__ offset,
+               const double *__restrict__ val, const int32_t *__restrict__ col,
+               const void *__restrict__ perm, int perm_bytes, double *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = i / C, l = i - k * C;
+    int64_t s = offset[k];
+    int w = (int)((offset[k + 1] - s) / C);
+    int io = orig_row(i, sigma, perm, perm_bytes);
+    double d = 0.0;
+    for (int j = 0; j < w; ++j) {
+        const int64_t p = s + (int64_t)j * C + l;
+        if (col[p] == io && val[p] != 0.0) d = val[p];
+    }
+    out[io] = d != 0.0 ? 1.0 / d : 1.0;
+}
+}  // namespace
+
+packsell_status inv_diag_impl(const Matrix &A, double *out, cudaStream_t s) {
+    if (A.p.format != PACKSELL_FMT_SELL_F64 || A.n != A.m)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_inv_diag: needs a square SELL_F64 matrix");
+    if (A.n == 0) return PACKSELL_OK;
+    k_inv_diag<<<grid_for(A.n), TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
+                                             (const double *)A.val, A.col, A.perm, A.perm_bytes, out);
+    PS_LAUNCH_CHECK("packsell_inv_diag");
     return PACKSELL_OK;
 }
 

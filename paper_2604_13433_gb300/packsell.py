@@ -89,6 +89,12 @@ SIGNATURES = {
     "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
     "packsell_pcg": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "packsell_pattern_outer_f64": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
+    "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
+    "packsell_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
+    "packsell_batch_spmv": (ctypes.c_int, [_P, _P]),
+    "packsell_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -282,6 +288,30 @@ def packsell_pattern_outer(A: PackSELLMatrix, alpha: float, u: torch.Tensor, v: 
     return out
 
 
+def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """1 / a_ii of a square SELL_F64 matrix (Jacobi preconditioner)."""
+    if out is None:
+        out = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    _check(lib().packsell_inv_diag(A.handle, _dev(out, torch.float64, "out", A.n),
+                                   _stream(stream)))
+    return out
+
+
+def packsell_pattern_outer_f64(A: PackSELLMatrix, alpha: float, u: torch.Tensor,
+                               v: torch.Tensor, out: torch.Tensor | None = None,
+                               stream=None) -> torch.Tensor:
+    """out[q] = alpha * u_i * v_j in double on the pattern (SELL_F64 matrix)."""
+    if out is None:
+        out = torch.empty(A.nnz, dtype=torch.float64, device=u.device)
+    _check(lib().packsell_pattern_outer_f64(A.handle, float(alpha),
+                                            _dev(u, torch.float64, "u", A.n),
+                                            _dev(v, torch.float64, "v", A.m),
+                                            _dev(out, torch.float64, "out", A.nnz),
+                                            _stream(stream)))
+    return out
+
+
 def packsell_export(A: PackSELLMatrix, stream=None) -> bytes:
     size = ctypes.c_size_t(0)
     _check(lib().packsell_export(A.handle, None, ctypes.byref(size), _stream(stream)))
@@ -394,3 +424,44 @@ def packsell_pcg_noalloc(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tens
     if check and code != 0:
         raise PackSELLError(code, lib().packsell_last_error().decode())
     return x, info
+
+
+class PackSELLBatch:
+    """A batched-SpMV plan (``packsell_batch*``) with its matrices and vectors
+    kept alive."""
+
+    def __init__(self, mats, xs, ys, stream=None):
+        if not (len(mats) == len(xs) == len(ys)) or not mats:
+            raise ValueError("need equally many matrices, x and y (at least one)")
+        cnt = len(mats)
+        A = (ctypes.c_void_p * cnt)(*[m.handle.value for m in mats])
+        X = (ctypes.c_void_p * cnt)(*[_dev(x, torch.float32, "x", m.m) for m, x in zip(mats, xs)])
+        Y = (ctypes.c_void_p * cnt)(*[_dev(y, torch.float32, "y", m.n) for m, y in zip(mats, ys)])
+        h = ctypes.c_void_p()
+        _check(lib().packsell_batch_create(cnt, A, X, Y, _stream(stream), ctypes.byref(h)))
+        self._h, self.mats, self.xs, self.ys = h, list(mats), list(xs), list(ys)
+        w, b, it = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().packsell_batch_info(h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(it)))
+        self.words, self.bytes, self.items = w.value, b.value, it.value
+
+    def spmv(self, stream=None):
+        _check(lib().packsell_batch_spmv(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().packsell_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def packsell_batch_create(mats, xs, ys, stream=None) -> PackSELLBatch:
+    return PackSELLBatch(mats, xs, ys, stream)
+
+
+def packsell_batch_spmv(B: PackSELLBatch, stream=None) -> None:
+    B.spmv(stream)
