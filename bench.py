@@ -37,7 +37,8 @@ WORKLOAD = "stencil27_128^3_spmv"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ("spmv.cu", "device.cuh", "reduce.cuh")
 KERNEL_NAMES = {1: "k_spmv_packed", 2: "k_spmv_bulk", 3: "k_spmv_bulk", 4: "k_spmv_bulk",
-                5: "k_spmv_prefetch", 6: "k_spmv_prefetch", 7: "k_spmv_dual", 8: "k_spmv_dual"}
+                5: "k_spmv_prefetch", 6: "k_spmv_prefetch", 7: "k_spmv_dual", 8: "k_spmv_dual",
+                9: "k_spmv_stage", 10: "k_spmv_stage"}
 
 
 def parse():
@@ -320,7 +321,8 @@ def run_ours(args):
         sweep = (("sell_f32", "sell_f32", 15), ("fp16_v1", "fp16", 15),
                  ("fp16_v2", "fp16", 15), ("fp16_v3", "fp16", 15), ("fp16_v4", "fp16", 15),
                  ("fp16_v5", "fp16", 15), ("fp16_v6", "fp16", 15), ("fp16_v7", "fp16", 15),
-                 ("fp16_v8", "fp16", 15), ("e8m7", "e8my", 15),
+                 ("fp16_v8", "fp16", 15), ("fp16_v9", "fp16", 15), ("fp16_v10", "fp16", 15),
+                 ("e8m7", "e8my", 15),
                  ("e8m11", "e8my", 11), ("e8m15", "e8my", 7))
         if args.formats != "all":
             keep = set(args.formats.split(",")) if args.formats != "none" else set()
@@ -328,7 +330,7 @@ def run_ours(args):
         for name, fmt, D in sweep:
             A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D, **common)
             if name.startswith("fp16_v"):
-                ps.packsell_set_spmv_variant(A, int(name[-1]))
+                ps.packsell_set_spmv_variant(A, int(name.split("_v")[1]))
             elif fmt != "sell_f32":
                 ps.packsell_tune_spmv(A, x, y, reps=20)
             nb = spmv_bytes(A, fmt == "sell_f32")

@@ -181,18 +181,23 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     cp.async.bulk (TMA engine) and completed on mbarriers; the three differ
  *     in warps per block, chunks per warp and chunk size (8/4/2 KB, 4/4/2 KB,
  *     8/2/4 KB). Bulk variants need a PackSELL matrix with C = 32;
- *   5, 6 thread-per-row with row register prefetch: 16 (5) or 32 (6) words
- *     of a row are loaded at once before any is decoded (PackSELL matrices,
- *     C = 32);
+ *   5, 6 thread-per-row with row register prefetch: the words of a round
+ *     are loaded at once before any is decoded; 5 sizes the round to the
+ *     widest slice (8, 10, 12 or 16 words), 6 uses 32 (PackSELL, C = 32);
  *   7, 8 dual-row persistent: each thread loads two rows (from two slices)
- *     together, 12 (7) or 16 (8) words of each per round (PackSELL, C = 32). */
+ *     together, rounds of 8-12 words fitted to the widest slice (7) or 16
+ *     (8) (PackSELL, C = 32);
+ *   9, 10 stage-planned TMA: at encode time each warp's slices are cut into
+ *     stages of whole slices (at most 4 KB (9) or 2 KB (10)); one
+ *     cp.async.bulk per stage into a double-buffered shared-memory slot with
+ *     an mbarrier; the consumer waits once per stage (PackSELL, C = 32). */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant for this matrix: time every available variant
  * (`reps` launches each after a warm-up, CUDA events on `stream`) on the
  * caller's x [m] and y [n], and make variant 0 run the fastest. Writes y.
  * Synchronises `stream`. If h_times is not NULL it receives the average
- * milliseconds per launch of variants 1..8 (0 where unavailable). */
+ * milliseconds per launch of variants 1..10 (0 where unavailable). */
 packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
                                    float *h_times, void *stream);
 

@@ -242,7 +242,7 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     clear_error();
-    if (!A || variant < 0 || variant > 8)
+    if (!A || variant < 0 || variant > 10)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
     if (variant >= 2 && variant <= 4 && !m->part[variant - 2])
@@ -250,7 +250,9 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
                     "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
     if (variant >= 5 && (!is_packed(m->p.format) || m->p.C != 32))
         return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_set_spmv_variant: variants 5-8 need a PackSELL matrix with C = 32");
+                    "packsell_set_spmv_variant: variants 5-10 need a PackSELL matrix with C = 32");
+    if (variant >= 9 && !m->stage[variant - 9].part)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: stage plan unavailable");
     m->variant = variant;
     return PACKSELL_OK;
 }
@@ -262,7 +264,7 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
     cudaStream_t s = as_stream(stream);
-    const int nvar = 8;
+    const int nvar = 10;
     if (h_times)
         for (int v = 0; v < nvar; ++v) h_times[v] = 0.f;
     cudaEvent_t e0, e1;
@@ -275,6 +277,7 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
         if (var >= 2 && !is_packed(m->p.format)) continue;
         if (var >= 5 && m->p.C != 32) continue;
+        if (var >= 9 && !m->stage[var - 9].part) continue;
         if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;
         m->variant = var;
         for (int r = 0; r < 3 && st == PACKSELL_OK; ++r) st = spmv_impl(*m, x, y, s);

@@ -45,6 +45,34 @@ struct Word {
     }
 };
 
+// Masks of a matrix's word layout: delta bits (flag 1) and value bits.
+struct Decode {
+    uint32_t dmask, vmask;
+};
+
+inline Decode make_decode(const Matrix &A) {
+    Decode d;
+    d.dmask = (1u << A.p.D) - 1u;
+    d.vmask = ~((2u << A.p.D) - 1u);
+    return d;
+}
+
+// One word: add its delta to c; if it carries a value, gather x_c.
+template <int FMT>
+__device__ __forceinline__ void word_gather(uint32_t wd, Decode dc, const float *__restrict__ x,
+                                            int &c, bool &f, float &xv) {
+    f = (wd & 1u) != 0u;
+    c += (int)((wd >> 1) & (f ? dc.dmask : 0x7fffffffu));
+    if (f) xv = __ldg(x + c);
+}
+
+// The value a word carries (FP16 in the upper half, or E8MY bits).
+template <int FMT>
+__device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
+    if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
+    return __uint_as_float(wd & dc.vmask);
+}
+
 __device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) {
     uint32_t v;
     asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));

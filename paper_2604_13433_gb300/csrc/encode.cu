@@ -401,6 +401,7 @@ void free_matrix_arrays(Matrix *A) {
     cudaFree(A->rowptr);
     cudaFree(A->status);
     for (int v = 0; v < Matrix::kBulkVariants; ++v) cudaFree(A->part[v]);
+    stage_free(*A);
 }
 
 }  // namespace
@@ -564,6 +565,10 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
     }
     *out = A;
     return PACKSELL_OK;
+}
+
+packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_t s) {
+    return scan_exclusive(in, out, S, s);
 }
 
 void destroy_matrix(Matrix *A) {

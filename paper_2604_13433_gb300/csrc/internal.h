@@ -18,6 +18,14 @@ struct DevStatus {
     long long index;
 };
 
+// Stage plan of a stage-planned SpMV configuration (stage.cu).
+struct StagePlan {
+    int32_t *part = nullptr;  // warps + 1 slice boundaries
+    int64_t *sptr = nullptr;  // warps + 1 starts of each warp's boundary list
+    int32_t *sb = nullptr;    // boundary lists (relative word offsets)
+    int blocks = 0, warps = 0;
+};
+
 struct Matrix {
     int64_t n = 0, m = 0, nnz = 0;
     packsell_params p{};
@@ -41,6 +49,8 @@ struct Matrix {
     int32_t *part[kBulkVariants] = {};  // part_warps + 1 slice boundaries
     int part_warps[kBulkVariants] = {};
     int part_blocks[kBulkVariants] = {};
+    static constexpr int kStageVariants = 2;  // variants 9, 10
+    StagePlan stage[kStageVariants];
 };
 
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
@@ -58,6 +68,13 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
                             const int64_t *rowptr, const int32_t *col, const void *val,
                             int val_is_f64, cudaStream_t s, Matrix **out);
 packsell_status validate_impl(const Matrix &A, cudaStream_t s);
+packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_t s);
+
+// stage.cu
+packsell_status plan_stage(Matrix &A, cudaStream_t s);
+void stage_free(Matrix &A);
+packsell_status launch_stage(const Matrix &A, int v, const void *perm, int pb, const float *x,
+                             float *y, cudaStream_t s);
 
 // spmv.cu
 packsell_status plan_spmv(Matrix &A, cudaStream_t s);

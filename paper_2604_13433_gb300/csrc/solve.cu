@@ -316,12 +316,12 @@ Work carve(void *base, int64_t n, bool inner, bool has_m, int max_iters, int pbl
 
 // fixed grid of the vector kernels (4 blocks per SM): the reductions are
 // deterministic for a given device
-int vec_blocks() { return reduce_blocks(); }
+int vec_blocks() { return reduce_blocks() / 2; }
 
 }  // namespace
 
 size_t solve_workspace_bytes(int64_t n, int m_in, int has_m, int max_iters) {
-    const int pblocks = vec_blocks();
+    const int pblocks = reduce_blocks();
     return carve(nullptr, n, m_in > 0, has_m != 0, max_iters, pblocks).bytes + 256;
 }
 
@@ -355,7 +355,7 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
     }
     if (!b || !x) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: NULL vector");
 
-    const int pblocks = vec_blocks();
+    const int pblocks = reduce_blocks();
     const size_t need = solve_workspace_bytes(n, o.m_in, inv_diag != nullptr, o.max_iters);
     void *own = nullptr;
     cudaStream_t s = caller;

@@ -22,16 +22,9 @@ constexpr int UNROLL = 8;
 
 inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, (n + TPB - 1) / TPB); }
 
-struct Decode {
-    uint32_t dmask, vmask;
-};
-
-inline Decode make_decode(const Matrix &A) {
-    Decode d;
-    d.dmask = (1u << A.p.D) - 1u;
-    d.vmask = ~((2u << A.p.D) - 1u);
-    return d;
-}
+// Words per prefetch round for a matrix whose widest slice has w words: the
+// smallest of 8, 10, 12, 16 that holds w (16 for wider slices).
+inline int round_words(int w) { return w <= 8 ? 8 : w <= 10 ? 10 : w <= 12 ? 12 : 16; }
 
 template <int FMT>
 __global__ void __launch_bounds__(TPB)
@@ -74,67 +67,77 @@ __global__ void __launch_bounds__(TPB)
     y[orig_row(i, sigma, perm, perm_bytes)] = t;
 }
 
-// One word: add its delta to c; if it carries a value, gather x_c.
-template <int FMT>
-__device__ __forceinline__ void word_gather(uint32_t wd, Decode dc, const float *__restrict__ x,
-                                            int &c, bool &f, float &xv) {
-    f = (wd & 1u) != 0u;
-    c += (int)((wd >> 1) & (f ? dc.dmask : 0x7fffffffu));
-    if (f) xv = __ldg(x + c);
-}
-
-template <int FMT>
-__device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
-    if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
-    return __uint_as_float(wd & dc.vmask);
-}
-
 // Thread-per-row SpMV with row register prefetch: each thread first issues
 // the loads of up to PF words of its row at once (plain loads the compiler
 // can predicate on j < w), then decodes them, issues their x
 // gathers, and finally runs the fused multiply-adds in stored order. A row of
 // up to PF words costs one memory round trip for its words and one for its
 // gathers. Words past the row's slice width are taken as 0 (padding).
-template <int FMT, int PF, int C, int MINB, bool DOT = false>
+// One row of the prefetch kernels: returns the sum, sets the output index
+// (PERM: rows are written through the sigma permutation).
+template <int FMT, int PF, int C, bool PERM = true>
+__device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, long long k_left,
+                                              const int64_t *__restrict__ offset,
+                                              const uint32_t *__restrict__ pack,
+                                              const void *__restrict__ perm, int perm_bytes,
+                                              Decode dc, const float *__restrict__ x, int &io) {
+    const int k = i / C, l = i - k * C;
+    const int64_t s = offset[k];
+    const int w = (int)((offset[k + 1] - s) / C);
+    const uint32_t *__restrict__ pp = pack + s + l;
+    const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
+    int c = (k_left < blk) ? (int)(blk - k_left) : 0;
+    float t = 0.f;
+    for (int j0 = 0; j0 < w; j0 += PF) {
+        const int wr = w - j0;
+        // loads predicated on the width; a word past it acts as padding
+        uint32_t wd[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
+        bool f[PF];
+        float xv[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+    }
+    io = i;
+    if (PERM) {
+        if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
+        else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
+    }
+    return t;
+}
+
+// One row per thread; the reducing form (DOT) runs on the fixed solver grid
+// and strides over rows (warps stay on whole slices) so that its reduction
+// is deterministic.
+template <int FMT, int PF, int C, int MINB, bool DOT = false, bool PERM = true>
 __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_prefetch(int n, int sigma, int sig_shift, long long k_left,
                     const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                     const void *__restrict__ perm, int perm_bytes, Decode dc,
                     const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
-    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
-    float d1 = 0.f;  // per-thread sum in FP32; block and grid sums in FP64
-    // one row per thread; the reducing form runs on a fixed grid and strides
-    // over rows (warps stay on whole slices) so its reduction is deterministic
-    const int stride = DOT ? gridDim.x * blockDim.x : n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int k = i / C, l = i - k * C;
-        const int64_t s = offset[k];
-        const int w = (int)((offset[k + 1] - s) / C);
-        const uint32_t *__restrict__ pp = pack + s + l;
-        const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
-        int c = (k_left < blk) ? (int)(blk - k_left) : 0;
-        float t = 0.f;
-        for (int j0 = 0; j0 < w; j0 += PF) {
-            const int wr = w - j0;
-            // loads predicated on the width; a word past it acts as padding
-            uint32_t wd[PF];
-#pragma unroll
-            for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
-            bool f[PF];
-            float xv[PF];
-#pragma unroll
-            for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
-#pragma unroll
-            for (int u = 0; u < PF; ++u)
-                if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
-        }
-        int io = i;
-        if (perm_bytes == 1) io = blk + (int)((const uint8_t *)perm)[i];
-        else if (perm_bytes == 2) io = blk + (int)((const uint16_t *)perm)[i];
+    if (!DOT) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= n) return;
+        int io;
+        const float t = prefetch_row<FMT, PF, C, PERM>(i, sigma, sig_shift, k_left, offset, pack,
+                                                       perm, perm_bytes, dc, x, io);
         y[io] = t;
-        if (DOT) d1 = fmaf(x[io], t, d1);
+        return;
     }
-    if (DOT) reduce_publish(red, (double)d1, 0.0);
+    if (red.sc->done) return;  // solver converged: idle (grid-uniform)
+    float d1 = 0.f;  // per-thread sum in FP32; block and grid sums in FP64
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int io;
+        const float t = prefetch_row<FMT, PF, C, PERM>(i, sigma, sig_shift, k_left, offset, pack,
+                                                       perm, perm_bytes, dc, x, io);
+        y[io] = t;
+        d1 = fmaf(x[io], t, d1);
+    }
+    reduce_publish(red, (double)d1, 0.0);
 }
 
 // Dual-row persistent SpMV: every thread handles two rows per loop trip, row
@@ -230,8 +233,12 @@ packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const
                                 float *y, cudaStream_t s) {
     const int sg = A.p.sigma;
     const int sig_shift = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
-    k_spmv_prefetch<FMT, PF, 32, MINB><<<grid_for(A.n), TPB, 0, s>>>(
-        (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+    if (pb)  // the permuted form needs a few more registers: one block fewer per SM
+        k_spmv_prefetch<FMT, PF, 32, MINB - 1, false, true><<<grid_for(A.n), TPB, 0, s>>>(
+            (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+    else
+        k_spmv_prefetch<FMT, PF, 32, MINB, false, false><<<grid_for(A.n), TPB, 0, s>>>(
+            (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
     PS_LAUNCH_CHECK("packsell_spmv (prefetch)");
     return PACKSELL_OK;
 }
@@ -763,7 +770,7 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
         A.part_warps[v] = G;
     }
     if (A.part[0]) A.auto_variant = 2;
-    return PACKSELL_OK;
+    return plan_stage(A, s);
 }
 
 packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_t s) {
@@ -772,13 +779,23 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     int g = grid_for(A.n);
     const int var = A.variant == 0 ? A.auto_variant : A.variant;
+    if ((var == 9 || var == 10) && is_packed(A.p.format))
+        return launch_stage(A, var - 9, perm, pb, x, y, s);
     if ((var == 7 || var == 8) && is_packed(A.p.format)) {
         if (A.p.C != 32)
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the dual-row variants need C = 32");
         const bool h = A.p.format == PACKSELL_FMT_FP16;
-        if (var == 7)
+        if (var == 7) {
+            const int pf = std::min(12, round_words(A.max_width));
+            if (pf == 8)
+                return h ? launch_dual<PACKSELL_FMT_FP16, 8, 5>(A, perm, pb, x, y, s)
+                         : launch_dual<PACKSELL_FMT_E8MY, 8, 5>(A, perm, pb, x, y, s);
+            if (pf == 10)
+                return h ? launch_dual<PACKSELL_FMT_FP16, 10, 4>(A, perm, pb, x, y, s)
+                         : launch_dual<PACKSELL_FMT_E8MY, 10, 4>(A, perm, pb, x, y, s);
             return h ? launch_dual<PACKSELL_FMT_FP16, 12, 4>(A, perm, pb, x, y, s)
                      : launch_dual<PACKSELL_FMT_E8MY, 12, 4>(A, perm, pb, x, y, s);
+        }
         return h ? launch_dual<PACKSELL_FMT_FP16, 16, 3>(A, perm, pb, x, y, s)
                  : launch_dual<PACKSELL_FMT_E8MY, 16, 3>(A, perm, pb, x, y, s);
     }
@@ -786,11 +803,23 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
         if (A.p.C != 32)
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the prefetch variants need C = 32");
         const bool h = A.p.format == PACKSELL_FMT_FP16;
-        if (var == 5)
-            return h ? launch_prefetch<PACKSELL_FMT_FP16, 16, 5>(A, perm, pb, x, y, s)
-                     : launch_prefetch<PACKSELL_FMT_E8MY, 16, 5>(A, perm, pb, x, y, s);
-        return h ? launch_prefetch<PACKSELL_FMT_FP16, 32, 4>(A, perm, pb, x, y, s)
-                 : launch_prefetch<PACKSELL_FMT_E8MY, 32, 4>(A, perm, pb, x, y, s);
+        if (var == 6)
+            return h ? launch_prefetch<PACKSELL_FMT_FP16, 32, 4>(A, perm, pb, x, y, s)
+                     : launch_prefetch<PACKSELL_FMT_E8MY, 32, 4>(A, perm, pb, x, y, s);
+        // round size fitted to the widest slice: decoded slots past a row's
+        // width are wasted work, which dominates on short rows
+        const int pf = round_words(A.max_width);
+        if (pf == 8)
+            return h ? launch_prefetch<PACKSELL_FMT_FP16, 8, 6>(A, perm, pb, x, y, s)
+                     : launch_prefetch<PACKSELL_FMT_E8MY, 8, 6>(A, perm, pb, x, y, s);
+        if (pf == 10)
+            return h ? launch_prefetch<PACKSELL_FMT_FP16, 10, 6>(A, perm, pb, x, y, s)
+                     : launch_prefetch<PACKSELL_FMT_E8MY, 10, 6>(A, perm, pb, x, y, s);
+        if (pf == 12)
+            return h ? launch_prefetch<PACKSELL_FMT_FP16, 12, 5>(A, perm, pb, x, y, s)
+                     : launch_prefetch<PACKSELL_FMT_E8MY, 12, 5>(A, perm, pb, x, y, s);
+        return h ? launch_prefetch<PACKSELL_FMT_FP16, 16, 5>(A, perm, pb, x, y, s)
+                 : launch_prefetch<PACKSELL_FMT_E8MY, 16, 5>(A, perm, pb, x, y, s);
     }
     if (var >= 2 && var <= 4 && is_packed(A.p.format)) {
         const int v = var - 2;
@@ -922,22 +951,52 @@ packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u,
 }
 
 // ---- fused SpMV + dot launchers for the solvers (square, original order) ----
-// The reducing kernels run on a fixed grid of 4 blocks per SM.
-int reduce_blocks() {
+// Reducing kernels run on fixed grids of at most 8 blocks per SM (the size of
+// the partial-sum buffers); each kernel's grid depends only on the device.
+int device_sms() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         sms = 160;  // no device yet: size for a large part
     }
-    return std::max(1, sms * 4);
+    return std::max(1, sms);
+}
+
+int reduce_blocks() { return device_sms() * 8; }
+
+// persistent grid of a reducing kernel: resident blocks, at most 8 per SM
+template <typename K>
+int dot_grid(K kern) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TPB, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per = 4;
+    }
+    return device_sms() * std::min(8, std::max(1, per));
+}
+
+template <int FMT, int PF, int MINB>
+void launch_prefetch_dot(const Matrix &A, const float *x, float *y, const Red &red,
+                         cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    if (A.perm_bytes) {
+        auto k = k_spmv_prefetch<FMT, PF, 32, MINB - 1, true, true>;
+        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm,
+                                      A.perm_bytes, make_decode(A), x, y, red);
+    } else {
+        auto k = k_spmv_prefetch<FMT, PF, 32, MINB, true, false>;
+        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm, 0,
+                                      make_decode(A), x, y, red);
+    }
 }
 
 int spmv_dot_blocks(const Matrix &) { return reduce_blocks(); }
 
 packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
                              cudaStream_t s) {
-    const int g = reduce_blocks();
+    const int g = device_sms() * 4;
     const void *perm = A.perm;
     const int pb = A.perm_bytes;
     if (A.p.format == PACKSELL_FMT_SELL_F32) {
@@ -945,25 +1004,21 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
                                                    (const float *)A.val, A.col, perm, pb, x, y,
                                                    nullptr, red);
     } else if (A.p.C == 32) {
-        // dual-row kernel; 12 words per round when every row fits
-        const int sg = A.p.sigma;
-        const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+        // row-prefetch kernel, rounds fitted to the widest slice
         const bool h = A.p.format == PACKSELL_FMT_FP16;
-        const Decode dc = make_decode(A);
-        if (A.max_width <= 12) {
-            if (h)
-                k_spmv_dual<PACKSELL_FMT_FP16, 12, 4, true><<<g, TPB, 0, s>>>(
-                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
-            else
-                k_spmv_dual<PACKSELL_FMT_E8MY, 12, 4, true><<<g, TPB, 0, s>>>(
-                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+        const int pf = round_words(A.max_width);
+        if (pf == 8) {
+            if (h) launch_prefetch_dot<PACKSELL_FMT_FP16, 8, 6>(A, x, y, red, s);
+            else launch_prefetch_dot<PACKSELL_FMT_E8MY, 8, 6>(A, x, y, red, s);
+        } else if (pf == 10) {
+            if (h) launch_prefetch_dot<PACKSELL_FMT_FP16, 10, 6>(A, x, y, red, s);
+            else launch_prefetch_dot<PACKSELL_FMT_E8MY, 10, 6>(A, x, y, red, s);
+        } else if (pf == 12) {
+            if (h) launch_prefetch_dot<PACKSELL_FMT_FP16, 12, 5>(A, x, y, red, s);
+            else launch_prefetch_dot<PACKSELL_FMT_E8MY, 12, 5>(A, x, y, red, s);
         } else {
-            if (h)
-                k_spmv_dual<PACKSELL_FMT_FP16, 16, 3, true><<<g, TPB, 0, s>>>(
-                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
-            else
-                k_spmv_dual<PACKSELL_FMT_E8MY, 16, 3, true><<<g, TPB, 0, s>>>(
-                    (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, x, y, red);
+            if (h) launch_prefetch_dot<PACKSELL_FMT_FP16, 16, 5>(A, x, y, red, s);
+            else launch_prefetch_dot<PACKSELL_FMT_E8MY, 16, 5>(A, x, y, red, s);
         }
     } else {
         if (A.p.format == PACKSELL_FMT_FP16)
@@ -979,7 +1034,7 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
 
 packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
                              const Red &red, cudaStream_t s) {
-    k_spmv_sell<double, true><<<reduce_blocks(), TPB, 0, s>>>(
+    k_spmv_sell<double, true><<<device_sms() * 4, TPB, 0, s>>>(
         (int)A.n, A.p.C, A.p.sigma, A.offset, (const double *)A.val, A.col, A.perm, A.perm_bytes, x,
         y, b, red);
     PS_LAUNCH_CHECK("spmv_dot_f64");

@@ -29,6 +29,7 @@ SPMV_AUTO, SPMV_ROWTHREAD, SPMV_BULK = 0, 1, 2
 SPMV_BULK_VARIANTS = (2, 3, 4)
 SPMV_PREFETCH = (5, 6)
 SPMV_DUAL = (7, 8)
+SPMV_STAGE = (9, 10)
 
 
 class PackSELLError(RuntimeError):
@@ -208,7 +209,7 @@ def packsell_encode_csr(csr, device="cuda", **kw) -> PackSELLMatrix:
 
 
 def packsell_set_spmv_variant(A: PackSELLMatrix, variant: int) -> None:
-    """0 auto, 1 thread-per-row, 2-4 bulk-staged configurations, 5-6 row prefetch, 7-8 dual-row."""
+    """0 auto, 1 thread-per-row, 2-4 bulk-staged configurations, 5-6 row prefetch, 7-8 dual-row, 9-10 stage-planned."""
     _check(lib().packsell_set_spmv_variant(A.handle, int(variant)))
 
 
@@ -218,11 +219,11 @@ def packsell_tune_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | Non
     Returns {variant: ms per launch} for the variants that ran."""
     if y is None:
         y = torch.empty(A.n, dtype=torch.float32, device=x.device)
-    times = (ctypes.c_float * 8)()
+    times = (ctypes.c_float * 10)()
     _check(lib().packsell_tune_spmv(A.handle, _dev(x, torch.float32, "x", A.m),
                                     _dev(y, torch.float32, "y", A.n), int(reps), times,
                                     _stream(stream)))
-    return {v + 1: times[v] for v in range(8) if times[v] > 0}
+    return {v + 1: times[v] for v in range(10) if times[v] > 0}
 
 
 def packsell_check_status(A: PackSELLMatrix, stream=None) -> None:

@@ -29,7 +29,7 @@ def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0, rel_tol=Non
     xd = dev(x)
     variants = [packsell.SPMV_ROWTHREAD]
     if C == 32 and fmt in ("fp16", "e8my"):
-        variants += list(packsell.SPMV_PREFETCH) + list(packsell.SPMV_DUAL)
+        variants += list(packsell.SPMV_PREFETCH) + list(packsell.SPMV_DUAL) + list(packsell.SPMV_STAGE)
     if C == 32 and csr.n > 0 and fmt in ("fp16", "e8my"):
         variants += list(packsell.SPMV_BULK_VARIANTS)
     ys = []
@@ -124,7 +124,7 @@ def test_tune_spmv_picks_a_variant():
     A = encode_gpu(csr, fmt="fp16")
     x = dev(I.uniform(csr.m, seed=1))
     times = packsell.packsell_tune_spmv(A, x, reps=5)
-    assert set(times) == set(range(1, 9)) and all(t > 0 for t in times.values())
+    assert set(times) == set(range(1, 11)) and all(t > 0 for t in times.values())
     y = packsell.packsell_spmv(A, x).cpu().numpy()  # variant 0 = tuned choice
     enc = O.encode(csr, fmt=O.FMT_FP16)
     twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), x.cpu().numpy())
