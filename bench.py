@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--variant", type=int, default=0,
                     help="SpMV variant of the headline matrix (0: autotune)")
+    ap.add_argument("--extended", action="store_true",
+                    help="also run the irregular-matrix (SpMM, batch) and batched "
+                         "differentiable-solve sections")
     ap.add_argument("--formats", default="all",
                     help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
                          "e8m15), 'all' or 'none'")
@@ -205,6 +208,153 @@ def cpu_baseline(csr, deq, x, nbytes, budget_s=12.0):
                       "algorithmic bytes"}
 
 
+def backward_error(torch, ps, A, y, y64, normA, normx):
+    """||y - A x||_inf / (||A||_inf ||x||_inf) with A x from the FP64 SELL product of
+    the unquantised matrix in the original row order (the paper's accuracy
+    metric, §5.1.2). y is in A's storage order when A has an explicit
+    permutation; each format's sort differs (dummy words count), so y is put
+    back in the original order through A's own storage rows first."""
+    if A.explicit_perm:
+        rows = ps.packsell_storage_rows(A).long()
+        yo = torch.empty_like(y)
+        yo[rows] = y
+        y = yo
+    return float((y.double() - y64).abs().max() / (normA * normx))
+
+
+def cusparse_csr_gbps(torch, rp, cl, vl, n, m, x, K, W):
+    """cuSPARSE CSR FP32 SpMV through torch.sparse (comparison only, not part of
+    the library), GB/s counted with CSR's algorithmic bytes."""
+    # both index arrays must have the same dtype (int64 here), and the tensor is
+    # checked before cuSPARSE reads it
+    A = torch.sparse_csr_tensor(rp.long(), cl.long(), vl.float(), size=(n, m),
+                                check_invariants=True)
+    xc = x.view(-1, 1)
+    ms, _ = time_launches(torch, lambda: torch.sparse.mm(A, xc), K, W)
+    nbytes = 8 * vl.numel() + 8 * (n + 1) + 4 * m + 4 * n
+    return {"GBps": nbytes / ms / 1e6, "us": ms * 1e3, "bytes": nbytes}
+
+
+def extended_section(ps, torch, dev, K, W):
+    """Irregular non-symmetric 4M-row matrix (Zipf(2) row lengths, columns
+    around the diagonal plus 5 % uniform): tuned PackSELL FP16 SpMV, FP32 SELL,
+    cuSPARSE CSR, SpMM for k in {1, 4, 16, 64}; a batch of 256 such matrices
+    (1k-100k rows) in one launch; and a batched differentiable solve (512 SPD
+    5-point systems on 32^2..256^2 grids, block-diagonal) forward + backward."""
+    out = {}
+    csr = I.zipf_irregular(4194304, seed=3)
+    rp = torch.from_numpy(csr.rowptr).to(dev)
+    cl = torch.from_numpy(csr.col).to(dev)
+    vl = torch.from_numpy(csr.val).to(dev)
+    x = torch.from_numpy(I.uniform(csr.m, seed=4)).to(dev)
+    y = torch.empty(csr.n, dtype=torch.float32, device=dev)
+    A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="fp16", D=15, explicit_perm=True)
+    tuned = ps.packsell_tune_spmv(A, x, y, reps=20)
+    ms, _ = time_launches(torch, lambda: ps.packsell_spmv(A, x, y), K, W)
+    nb = spmv_bytes(A, False)
+    sec = {"n": csr.n, "nnz": csr.nnz, "words": A.n_words, "words_per_nnz": A.n_words / csr.nnz,
+           "dummies": A.n_dummies, "fp16": {"GBps": nb / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6,
+                                            "us": ms * 1e3, "variant": min(tuned, key=tuned.get)}}
+    S = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f32", explicit_perm=True)
+    ms, _ = time_launches(torch, lambda: ps.packsell_spmv(S, x, y), K, W)
+    sec["sell_f32"] = {"GBps": spmv_bytes(S, True) / ms / 1e6, "us": ms * 1e3,
+                       "words": S.n_words}
+    del S
+    sec["cusparse_csr_f32"] = cusparse_csr_gbps(torch, rp, cl, vl, csr.n, csr.m, x, K, W)
+    spmm = {}
+    for k in (1, 4, 16, 64):
+        X = torch.rand(csr.m, k, device=dev)
+        Y = torch.empty(csr.n, k, device=dev)
+        ms, _ = time_launches(torch, lambda: ps.packsell_spmm(A, X, Y), max(K // 10, 5), 3)
+        nbk = 4 * A.n_words + 8 * (A.n_slices + 1) + 4 * k * (csr.m + csr.n)
+        spmm[str(k)] = {"GBps": nbk / ms / 1e6, "GFLOPs": 2 * k * csr.nnz / ms / 1e6,
+                        "us": ms * 1e3}
+        del X, Y
+    sec["spmm"] = spmm
+    out["irregular_4M"] = sec
+    del A, rp, cl, vl
+    # batch of 256 irregular matrices, one launch
+    mats, xs, ys = [], [], []
+    for c in I.zipf_batch(256, seed=5):
+        mats.append(ps.packsell_encode_csr(c, fmt="fp16", D=15))
+        xs.append(torch.from_numpy(I.uniform(c.m, seed=c.n)).to(dev))
+        ys.append(torch.empty(c.n, device=dev))
+    B = ps.packsell_batch_create(mats, xs, ys)
+    ms, _ = time_launches(torch, B.spmv, K, W)
+    out["batch_256"] = {"matrices": 256, "rows": int(sum(m.n for m in mats)),
+                        "words": B.words, "items": B.items, "GBps": B.bytes / ms / 1e6,
+                        "us": ms * 1e3}
+    del B, mats, xs, ys
+    out["diff_solve_512"] = diff_solve_section(ps, torch, dev)
+    return out
+
+
+def diff_solve_section(ps, torch, dev):
+    """512 SPD 5-point systems (face coefficients exp(N(0, 0.5)), grids 32^2 to
+    256^2) assembled block-diagonally; loss ||x - x_t||^2; forward solve and
+    backward (adjoint solve, dA on the pattern, chain to the faces) timed."""
+    from paper_2604_13433_gb300 import autograd as ag
+
+    rng = np.random.default_rng(6)
+    sides = rng.integers(32, 257, size=512)
+    rows, cols, faces_th, pos = [], [], [], []
+    uu, vv, uv, vu, pb = [], [], [], [], []
+    off_r = off_q = 0
+    for i, L in enumerate(sides):
+        c, f = I.poisson5_varcoef(int(L), seed=1000 + i)
+        rows.append(c.rowptr[:-1] + off_q)
+        cols.append(c.col.astype(np.int64) + off_r)
+        faces_th.append(f["theta"])
+        F = f["u"].size
+        uu.append(f["pos_uu"] + off_q)
+        vv.append(f["pos_vv"] + off_q)
+        uv.append(f["pos_uv"] + off_q)
+        vu.append(f["pos_vu"] + off_q)
+        pb.append(f["pos_b"] + off_q)
+        pos.append((F, f["theta"].size - F))
+        off_r += c.n
+        off_q += c.nnz
+    n, nnz = off_r, off_q
+    rowptr = np.append(np.concatenate(rows), nnz).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32)
+    # face and boundary coefficients of all systems, interior faces first per system
+    th_f = np.concatenate([t[:F] for t, (F, _) in zip(faces_th, pos)])
+    th_b = np.concatenate([t[F:] for t, (F, _) in zip(faces_th, pos)])
+    P = {k: torch.from_numpy(np.concatenate(v)).to(dev) for k, v in
+         (("uu", uu), ("vv", vv), ("uv", uv), ("vu", vu), ("b", pb))}
+    Ff = th_f.size
+    theta = torch.from_numpy(np.concatenate([th_f, th_b])).to(dev).requires_grad_(True)
+    b = torch.from_numpy(I.uniform(n, seed=7).astype(np.float64)).to(dev).requires_grad_(True)
+    xt = torch.from_numpy(I.normal(n, seed=8)).to(dev)
+    rp = torch.from_numpy(rowptr).to(dev)
+    cl = torch.from_numpy(col).to(dev)
+
+    def assemble(th):
+        v = torch.zeros(nnz, dtype=th.dtype, device=dev)
+        tf, tb = th[:Ff], th[Ff:]
+        v = v.index_add(0, P["uu"], tf).index_add(0, P["vv"], tf)
+        v = v.index_add(0, P["uv"], -tf).index_add(0, P["vu"], -tf)
+        return v.index_add(0, P["b"], tb)
+
+    res = {"systems": 512, "n": int(n), "nnz": int(nnz)}
+    for name, m_in, fmt, D in (("fp64_pcg", 0, "fp16", 15), ("iocg_e8m11", 20, "e8my", 11)):
+        theta.grad = None
+        b.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = ag.solve(rp, cl, assemble(theta), b, m_in=m_in, fmt=fmt, D=D, rtol=1e-10,
+                     max_iters=20000)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ((x - xt) ** 2).sum().backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res[name] = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                     "grad_norm_theta": float(theta.grad.norm()),
+                     "grad_norm_b": float(b.grad.norm())}
+    return res
+
+
 def pcg_section(ps, torch, dev, grid, m_in):
     """Time to a true relative residual of 1e-10 on the 7-point variable-
     coefficient Poisson problem (log-normal face coefficients, symmetrically
@@ -316,6 +466,12 @@ def run_ours(args):
     B16 = spmv_bytes(A16, False)
 
     formats = {}
+    A64 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f64", explicit_perm=False)
+    y64 = ps.packsell_spmv_f64(A64, x.double())
+    row_abs = torch.zeros(csr.n, dtype=torch.float64, device=dev).index_add_(
+        0, torch.repeat_interleave(torch.arange(csr.n, device=dev), torch.diff(rp)), vl.double().abs())
+    normA, normx = float(row_abs.max()), float(x.abs().max())
+    del A64, row_abs
     with Clocks(local) as clk:
         ms16, total16 = time_launches(torch, lambda: ps.packsell_spmv(A16, x, y), K, W)
         sweep = (("sell_f32", "sell_f32", 15), ("fp16_v1", "fp16", 15),
@@ -337,7 +493,8 @@ def run_ours(args):
             ms, _ = time_launches(torch, lambda: ps.packsell_spmv(A, x, y), K, W)
             formats[name] = {"GBps": nb / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6,
                              "us": ms * 1e3, "bytes": nb, "words": A.n_words,
-                             "dummies": A.n_dummies, "footprint_vs_sell": None}
+                             "dummies": A.n_dummies, "footprint_vs_sell": None,
+                             "backward_error": backward_error(torch, ps, A, y, y64, normA, normx)}
             del A
         # end to end through the public API: pinned host x in, host y out
         xp = torch.from_numpy(x_h).pin_memory()
@@ -353,11 +510,16 @@ def run_ours(args):
         if not args.no_e2e:
             ms_e2e, _ = time_launches(torch, e2e_step, max(K // 10, 10), max(W // 10, 3))
     sell = formats.get("sell_f32")
+    ps.packsell_spmv(A16, x, y)
     formats["fp16"] = {"GBps": B16 / ms16 / 1e6, "GFLOPs": 2 * csr.nnz / ms16 / 1e6,
                        "us": ms16 * 1e3, "bytes": B16, "words": A16.n_words,
-                       "dummies": A16.n_dummies, "footprint_vs_sell": None}
+                       "dummies": A16.n_dummies, "footprint_vs_sell": None,
+                       "backward_error": backward_error(torch, ps, A16, y, y64, normA, normx)}
+    if args.formats == "all":
+        formats["cusparse_csr_f32"] = cusparse_csr_gbps(torch, rp, cl, vl, csr.n, csr.m, x, K, W)
     for v in formats.values():
         v["footprint_vs_sell"] = v["bytes"] / sell["bytes"] if sell else None
+    formats.get("cusparse_csr_f32", {}).pop("footprint_vs_sell", None)
 
     # whole-job numbers: max time over ranks, units summed over ranks
     t_step_ms = total16 / K
@@ -393,6 +555,8 @@ def run_ours(args):
     }
     if not args.no_pcg:
         line["pcg"] = pcg_section(ps, torch, dev, args.pcg_grid, args.pcg_min)
+    if args.extended:
+        line["extended"] = extended_section(ps, torch, dev, K, W)
     if rank == 0 and not args.no_cpu:
         import oracle as O
 

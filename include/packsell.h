@@ -293,6 +293,13 @@ typedef struct packsell_solve_result {
  * diagonal is missing or zero get 1. */
 packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream);
 
+/* rows[i] = the original row stored at storage position i (int32 [n], device),
+ * i.e. (i / sigma) * sigma + perm[i] with the sigma-block sort of §3 / §4.3.
+ * With explicit_perm, packsell_spmv writes y[i] for that row, so
+ * y_orig[rows[i]] = y[i]; with sigma = 1 rows[i] = i. Works for every format
+ * and either perm mode. Errors: INVALID_ARG on a NULL argument. */
+packsell_status packsell_storage_rows(const packsell_matrix *A, int32_t *rows, void *stream);
+
 /* Device workspace bytes packsell_pcg needs for n unknowns (has_diag: a Jacobi
  * preconditioner is passed). */
 size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag,

@@ -366,6 +366,13 @@ packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *s
     return inv_diag_impl(*M(A), out, as_stream(stream));
 }
 
+packsell_status packsell_storage_rows(const packsell_matrix *A, int32_t *rows, void *stream) {
+    clear_error();
+    if (!A || (M(A)->n > 0 && !rows))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_storage_rows: NULL argument");
+    return storage_rows_impl(*M(A), rows, as_stream(stream));
+}
+
 packsell_status packsell_pattern_outer_f64(const packsell_matrix *A, double alpha,
                                            const double *u, const double *v, double *out,
                                            void *stream) {

@@ -663,4 +663,19 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     return PACKSELL_OK;
 }
 
+// Storage position -> original row (§3): the inverse of the sigma-block sort.
+__global__ void k_storage_rows(int n, int sigma, const void *perm, int perm_bytes,
+                               int32_t *__restrict__ rows) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rows[i] = orig_row(i, sigma, perm, perm_bytes);
+}
+
+packsell_status storage_rows_impl(const Matrix &A, int32_t *rows, cudaStream_t s) {
+    if (A.n == 0) return PACKSELL_OK;
+    const int blocks = (int)std::min<int64_t>((A.n + 255) / 256, 4096);
+    k_storage_rows<<<blocks, 256, 0, s>>>((int)A.n, A.p.sigma, A.perm, A.perm_bytes, rows);
+    PS_LAUNCH_CHECK("packsell_storage_rows");
+    return PACKSELL_OK;
+}
+
 }  // namespace packsell

@@ -86,6 +86,7 @@ packsell_status spmv_t_impl(const Matrix &A, const float *dy, float *dx, cudaStr
 packsell_status pattern_outer_impl(const Matrix &A, float alpha, const float *u, const float *v,
                                    float *out, cudaStream_t s);
 packsell_status inv_diag_impl(const Matrix &A, double *out, cudaStream_t s);
+packsell_status storage_rows_impl(const Matrix &A, int32_t *rows, cudaStream_t s);
 packsell_status pattern_outer_f64_impl(const Matrix &A, double alpha, const double *u,
                                        const double *v, double *out, cudaStream_t s);
 

@@ -284,7 +284,7 @@ def zipf_irregular(n: int, m: int | None = None, seed: int = 0, zipf_a: float = 
         return g
 
     key = row * m + draw(row)
-    for it in range(200):
+    for it in range(60):
         key.sort()
         dup = np.zeros(total, dtype=bool)
         dup[1:] = key[1:] == key[:-1]
@@ -292,9 +292,18 @@ def zipf_irregular(n: int, m: int | None = None, seed: int = 0, zipf_a: float = 
         if nd == 0:
             break
         rows = key[dup] // m
-        key[dup] = rows * m + (draw(rows) if it < 100 else rng.integers(0, m, size=nd))
+        key[dup] = rows * m + (draw(rows) if it < 40 else rng.integers(0, m, size=nd))
     else:
-        raise RuntimeError("zipf_irregular: could not make columns distinct")
+        # rows that still repeat a column (nearly full rows of small matrices)
+        # are drawn again whole, as a uniform subset without replacement
+        key.sort()
+        dup = np.zeros(total, dtype=bool)
+        dup[1:] = key[1:] == key[:-1]
+        rowptr0 = np.concatenate([[0], np.cumsum(lengths)])
+        for r in np.unique(key[dup] // m):
+            a, b = rowptr0[r], rowptr0[r + 1]
+            key[a:b] = r * m + np.sort(rng.choice(m, size=b - a, replace=False))
+        key.sort()
     col = key % m
     del key, row
     rowptr = np.zeros(n + 1, dtype=np.int64)

@@ -92,6 +92,7 @@ SIGNATURES = {
     "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "packsell_pattern_outer_f64": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
     "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
+    "packsell_storage_rows": (ctypes.c_int, [_P, _P, _P]),
     "packsell_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "packsell_batch_spmv": (ctypes.c_int, [_P, _P]),
     "packsell_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -296,6 +297,17 @@ def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
         out = torch.empty(A.n, dtype=torch.float64, device="cuda")
     _check(lib().packsell_inv_diag(A.handle, _dev(out, torch.float64, "out", A.n),
                                    _stream(stream)))
+    return out
+
+
+def packsell_storage_rows(A: PackSELLMatrix, out: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """Original row held at each storage position (int32 [n]): with an
+    explicit permutation, y_orig[rows] = y."""
+    if out is None:
+        out = torch.empty(A.n, dtype=torch.int32, device="cuda")
+    _check(lib().packsell_storage_rows(A.handle, _dev(out, torch.int32, "out", A.n),
+                                       _stream(stream)))
     return out
 
 

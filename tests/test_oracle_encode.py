@@ -227,3 +227,15 @@ def test_encoder_rejects_bad_input():
                   val=np.ones(3, np.float32))
     with pytest.raises(O.OracleError):
         O.encode(lower, sigma=1, k_left=0)
+
+
+def test_irregular_generator_small_dense_rows():
+    # small matrices whose Zipf row lengths reach m: every row must still hold
+    # distinct sorted columns in range
+    for seed in range(3):
+        c = I.zipf_irregular(300, seed=seed, sigma_col=30.0)
+        d = np.diff(c.col.astype(np.int64))
+        first = np.zeros(c.nnz, bool)
+        first[c.rowptr[:-1][c.row_lengths() > 0]] = True
+        assert np.all(d[~first[1:]] > 0) and c.col.max() < c.m and c.col.min() >= 0
+        assert O.check_csr(c) == 0
