@@ -254,7 +254,8 @@ def extended_section(ps, torch, dev, K, W):
     nb = spmv_bytes(A, False)
     sec = {"n": csr.n, "nnz": csr.nnz, "words": A.n_words, "words_per_nnz": A.n_words / csr.nnz,
            "dummies": A.n_dummies, "fp16": {"GBps": nb / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6,
-                                            "us": ms * 1e3, "variant": min(tuned, key=tuned.get)}}
+                                            "us": ms * 1e3, "variant": min(tuned, key=tuned.get),
+                                            "tuner_us": {str(v): t * 1e3 for v, t in tuned.items()}}}
     S = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f32", explicit_perm=True)
     ms, _ = time_launches(torch, lambda: ps.packsell_spmv(S, x, y), K, W)
     sec["sell_f32"] = {"GBps": spmv_bytes(S, True) / ms / 1e6, "us": ms * 1e3,
@@ -273,6 +274,20 @@ def extended_section(ps, torch, dev, K, W):
     sec["spmm"] = spmm
     out["irregular_4M"] = sec
     del A, rp, cl, vl
+    # SpMM on the 27-point 128^3 matrix (rows of equal length)
+    csr = I.stencil27(128, seed=0)
+    A = ps.packsell_encode_csr(csr, fmt="fp16", D=15, explicit_perm=True)
+    spmm = {}
+    for k in (4, 16, 64):
+        X = torch.rand(csr.m, k, device=dev)
+        Y = torch.empty(csr.n, k, device=dev)
+        ms, _ = time_launches(torch, lambda: ps.packsell_spmm(A, X, Y), max(K // 10, 5), 3)
+        nbk = 4 * A.n_words + 8 * (A.n_slices + 1) + 4 * k * (csr.m + csr.n)
+        spmm[str(k)] = {"GBps": nbk / ms / 1e6, "GFLOPs": 2 * k * csr.nnz / ms / 1e6,
+                        "us": ms * 1e3}
+        del X, Y
+    out["stencil27_128_spmm"] = spmm
+    del A
     # batch of 256 irregular matrices, one launch
     mats, xs, ys = [], [], []
     for c in I.zipf_batch(256, seed=5):

@@ -167,9 +167,16 @@ packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y
 packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
                                   void *stream);
 
-/* Y = A X for k right-hand sides. X: float, row-major [m x k] with leading
- * dimension ldx >= k; Y: float, row-major [n x k] with ldy >= k. One decode
- * of each word feeds k multiply-adds. PackSELL and SELL_F32 matrices. */
+/* Y = A X for k right-hand sides (an extension: the paper evaluates k = 1).
+ * X: float, row-major [m x k] with leading dimension ldx >= k; Y: float,
+ * row-major [n x k] with ldy >= k (rows in storage order with explicit_perm).
+ * A group of 1-16 lanes shares each row (more for wider k); the words are
+ * decoded once per lane and every real word feeds the row's k columns with
+ * fused multiply-adds in stored order, so column q of Y equals packsell_spmv
+ * with x = X[:, q] bit for bit. k = 1 with ldx = ldy = 1 runs the SpMV
+ * itself. 16-byte X/Y loads need k, ldx, ldy divisible by 4 and 16-byte
+ * aligned X and Y; other layouts take scalar loads. PackSELL and SELL_F32
+ * matrices. Errors: INVALID_ARG (k < 1, ld < k, SELL_F64). No allocation. */
 packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X,
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 

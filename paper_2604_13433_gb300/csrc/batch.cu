@@ -75,6 +75,7 @@ __device__ __forceinline__ float row_dot(const BatchMat &M, int row, int64_t s, 
                 t = fmaf(v, xv[u], t);
             }
         }
+        if (wd[BPF - 1] == 0u) break;  // padding: the row has ended
     }
     return t;
 }

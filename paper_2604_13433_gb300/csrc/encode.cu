@@ -39,29 +39,34 @@ __global__ void k_check_rows(int n, int64_t m, int64_t nnz, const int64_t *__res
         if (rowptr[0] != 0) dev_fail(st, PACKSELL_ERR_INVALID_ARG, -1);
         if (rowptr[n] != nnz) dev_fail(st, PACKSELL_ERR_INVALID_ARG, -2);
     }
-    if (i >= n) return;
-    int64_t a = rowptr[i], b = rowptr[i + 1];
-    if (a < 0 || b < a || b > nnz) {
-        dev_fail(st, PACKSELL_ERR_INVALID_ARG, i);
-        return;
-    }
-    int prev = -1;
-    for (int64_t p = a; p < b; ++p) {
-        int c = col[p];
-        if (c < 0 || (int64_t)c >= m) {
-            dev_fail(st, PACKSELL_ERR_RANGE, p);
-            return;
+    unsigned dmax = 0;  // this row's i - (first column), if positive
+    if (i < n) {
+        int64_t a = rowptr[i], b = rowptr[i + 1];
+        if (a < 0 || b < a || b > nnz) {
+            dev_fail(st, PACKSELL_ERR_INVALID_ARG, i);
+        } else {
+            int prev = -1;
+            bool ok = true;
+            for (int64_t p = a; p < b; ++p) {
+                int c = col[p];
+                if (c < 0 || (int64_t)c >= m) {
+                    dev_fail(st, PACKSELL_ERR_RANGE, p);
+                    ok = false;
+                    break;
+                }
+                if (c <= prev) {
+                    dev_fail(st, PACKSELL_ERR_UNSORTED, p);
+                    ok = false;
+                    break;
+                }
+                prev = c;
+            }
+            if (ok && b > a && i > col[a]) dmax = (unsigned)(i - col[a]);
         }
-        if (c <= prev) {
-            dev_fail(st, PACKSELL_ERR_UNSORTED, p);
-            return;
-        }
-        prev = c;
     }
-    if (b > a) {
-        long long d = (long long)i - (long long)col[a];
-        if (d > 0) atomicMax(kl, (unsigned long long)d);
-    }
+    // one atomic per warp: millions of atomics on one address serialise
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    if ((threadIdx.x & 31) == 0 && dmax) atomicMax(kl, (unsigned long long)dmax);
 }
 
 // FP16 value field: binary16 in bits 16..31, round to nearest even.

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(TPB)
     int c = left_offset(i, sigma, k_left);
     float t = 0.f;
     int j = 0;
-    for (; j + UNROLL <= w; j += UNROLL) {
+    bool live = true;  // false once a zero (padding) word ends the row
+    for (; live && j + UNROLL <= w; j += UNROLL) {
         uint32_t wd[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) wd[u] = ldg_stream(pp + (int64_t)(j + u) * C);
@@ -56,11 +57,14 @@ __global__ void __launch_bounds__(TPB)
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u)
             if (fl[u]) t = fmaf(vv[u], xv[u], t);
+        live = wd[UNROLL - 1] != 0u;
     }
-    for (; j < w; ++j) {
+    for (; live && j < w; ++j) {
         uint32_t f, d;
         float v;
-        Word<FMT>::decode(ldg_stream(pp + (int64_t)j * C), dc.dmask, dc.vmask, f, d, v);
+        const uint32_t wj = ldg_stream(pp + (int64_t)j * C);
+        if (wj == 0u) break;
+        Word<FMT>::decode(wj, dc.dmask, dc.vmask, f, d, v);
         c += (int)d;
         if (f) t = fmaf(v, __ldg(x + c), t);
     }
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(TPB)
 // gathers. Words past the row's slice width are taken as 0 (padding).
 // One row of the prefetch kernels: returns the sum, sets the output index
 // (PERM: rows are written through the sigma permutation).
-template <int FMT, int PF, int C, bool PERM = true>
+template <int FMT, int PF, int C, bool PERM = true, bool EXIT = false>
 __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, long long k_left,
                                               const int64_t *__restrict__ offset,
                                               const uint32_t *__restrict__ pack,
@@ -101,6 +105,11 @@ __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, l
 #pragma unroll
         for (int u = 0; u < PF; ++u)
             if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+        // EXIT: a zero word is padding (real words have flag 1, dummies a
+        // nonzero delta), and padding runs to the slice's end: the row is
+        // done, and the lane stops loading, so on slices of uneven rows the
+        // warp's later loads fetch only the sectors of rows still running
+        if (EXIT && wd[PF - 1] == 0u) break;
     }
     io = i;
     if (PERM) {
@@ -113,7 +122,8 @@ __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, l
 // One row per thread; the reducing form (DOT) runs on the fixed solver grid
 // and strides over rows (warps stay on whole slices) so that its reduction
 // is deterministic.
-template <int FMT, int PF, int C, int MINB, bool DOT = false, bool PERM = true>
+template <int FMT, int PF, int C, int MINB, bool DOT = false, bool PERM = true,
+          bool EXIT = false>
 __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_prefetch(int n, int sigma, int sig_shift, long long k_left,
                     const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
@@ -123,8 +133,8 @@ __global__ void __launch_bounds__(TPB, MINB)
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= n) return;
         int io;
-        const float t = prefetch_row<FMT, PF, C, PERM>(i, sigma, sig_shift, k_left, offset, pack,
-                                                       perm, perm_bytes, dc, x, io);
+        const float t = prefetch_row<FMT, PF, C, PERM, EXIT>(i, sigma, sig_shift, k_left, offset,
+                                                             pack, perm, perm_bytes, dc, x, io);
         y[io] = t;
         return;
     }
@@ -228,17 +238,29 @@ packsell_status launch_dual(const Matrix &A, const void *perm, int pb, const flo
     return PACKSELL_OK;
 }
 
-template <int FMT, int PF, int MINB>
-packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const float *x,
-                                float *y, cudaStream_t s) {
+template <int FMT, int PF, int MINB, bool EXIT>
+void launch_prefetch_e(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+                       cudaStream_t s) {
     const int sg = A.p.sigma;
     const int sig_shift = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
     if (pb)  // the permuted form needs a few more registers: one block fewer per SM
-        k_spmv_prefetch<FMT, PF, 32, MINB - 1, false, true><<<grid_for(A.n), TPB, 0, s>>>(
+        k_spmv_prefetch<FMT, PF, 32, MINB - 1, false, true, EXIT><<<grid_for(A.n), TPB, 0, s>>>(
             (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
     else
-        k_spmv_prefetch<FMT, PF, 32, MINB, false, false><<<grid_for(A.n), TPB, 0, s>>>(
+        k_spmv_prefetch<FMT, PF, 32, MINB, false, false, EXIT><<<grid_for(A.n), TPB, 0, s>>>(
             (int)A.n, sg, sig_shift, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+}
+
+template <int FMT, int PF, int MINB>
+packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const float *x,
+                                float *y, cudaStream_t s) {
+    // rows stop at their first padding word only where padding is a real
+    // share of the stored words (more than 1/8): elsewhere the test costs
+    // more than it saves
+    if (A.n_pad * 8 > A.n_words)
+        launch_prefetch_e<FMT, PF, MINB, true>(A, perm, pb, x, y, s);
+    else
+        launch_prefetch_e<FMT, PF, MINB, false>(A, perm, pb, x, y, s);
     PS_LAUNCH_CHECK("packsell_spmv (prefetch)");
     return PACKSELL_OK;
 }
@@ -582,72 +604,129 @@ __global__ void __launch_bounds__(TPB)
     reduce_publish(red, (double)d1, 0.0);
 }
 
-// SpMM, k right-hand sides in chunks of KT accumulators per thread.
-template <int FMT, int KT>
-__global__ void __launch_bounds__(TPB)
-    k_spmm_packed(int n, int C, int sigma, long long k_left, const int64_t *__restrict__ offset,
-                  const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
-                  Decode dc, int k, const float *__restrict__ X, int64_t ldx,
-                  float *__restrict__ Y, int64_t ldy) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int kb = i / C, l = i - kb * C;
-    int64_t s = offset[kb];
-    int w = (int)((offset[kb + 1] - s) / C);
-    const uint32_t *pp = pack + s + l;
-    int io = orig_row(i, sigma, perm, perm_bytes);
-    int c0 = left_offset(i, sigma, k_left);
-    for (int r0 = 0; r0 < k; r0 += KT) {
-        float acc[KT];
+// SpMM, Y = A X with X row-major [m x k] (leading dimension ldx), Y [n x k].
+// G lanes share a row (G = 1, 2, 4, 8, 16): they read the same words (one
+// broadcast load), decode them alike, and lane sub of the group owns the
+// column groups q0 + 4 sub + 4 G h (h < KV) of four consecutive columns, so
+// one gather instruction fetches 32/G rows of X, 16 G contiguous bytes each
+// (16-byte loads when VEC, four scalar loads otherwise). A pass covers 4 G KV
+// columns; wider k takes several passes. Each column is accumulated with
+// fused multiply-adds in stored order, so column q of Y equals packsell_spmv
+// with x = X[:, q] bit for bit. Rounds of SPF words per row as in the
+// prefetch SpMV; a row ends at its first zero word (padding follows).
+constexpr int SPF = 8;
+
+template <int KV, bool VEC>
+__device__ __forceinline__ void spmm_gather(const float *__restrict__ xr, int qa, int step, int k,
+                                            float v, float4 (&acc)[KV]) {
+    float4 xv[KV];
 #pragma unroll
-        for (int q = 0; q < KT; ++q) acc[q] = 0.f;
-        int c = c0;
-        for (int j = 0; j < w; ++j) {
-            uint32_t f, d;
-            float v;
-            Word<FMT>::decode(ldg_stream(pp + (int64_t)j * C), dc.dmask, dc.vmask, f, d, v);
-            c += (int)d;
-            if (f) {
-                const float *xr = X + (int64_t)c * ldx + r0;
-#pragma unroll
-                for (int q = 0; q < KT; ++q)
-                    if (r0 + q < k) acc[q] = fmaf(v, __ldg(xr + q), acc[q]);
-            }
+    for (int h = 0; h < KV; ++h) {
+        const int q = qa + step * h;
+        if (VEC) {
+            xv[h] = (q < k) ? __ldg(reinterpret_cast<const float4 *>(xr + step * h))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            xv[h].x = (q < k) ? __ldg(xr + step * h) : 0.f;
+            xv[h].y = (q + 1 < k) ? __ldg(xr + step * h + 1) : 0.f;
+            xv[h].z = (q + 2 < k) ? __ldg(xr + step * h + 2) : 0.f;
+            xv[h].w = (q + 3 < k) ? __ldg(xr + step * h + 3) : 0.f;
         }
-        float *yr = Y + (int64_t)io * ldy + r0;
+    }
 #pragma unroll
-        for (int q = 0; q < KT; ++q)
-            if (r0 + q < k) yr[q] = acc[q];
+    for (int h = 0; h < KV; ++h) {
+        acc[h].x = fmaf(v, xv[h].x, acc[h].x);
+        acc[h].y = fmaf(v, xv[h].y, acc[h].y);
+        acc[h].z = fmaf(v, xv[h].z, acc[h].z);
+        acc[h].w = fmaf(v, xv[h].w, acc[h].w);
     }
 }
 
-template <int KT>
+template <int KV, bool VEC>
+__device__ __forceinline__ void spmm_store(float *__restrict__ yr, int qa, int step, int k,
+                                           const float4 (&acc)[KV]) {
+#pragma unroll
+    for (int h = 0; h < KV; ++h) {
+        const int q = qa + step * h;
+        if (VEC) {
+            if (q < k) *reinterpret_cast<float4 *>(yr + step * h) = acc[h];
+        } else {
+            if (q < k) yr[step * h] = acc[h].x;
+            if (q + 1 < k) yr[step * h + 1] = acc[h].y;
+            if (q + 2 < k) yr[step * h + 2] = acc[h].z;
+            if (q + 3 < k) yr[step * h + 3] = acc[h].w;
+        }
+    }
+}
+
+template <int FMT, int G, int KV, bool VEC, bool C32>
+__global__ void __launch_bounds__(TPB)
+    k_spmm_packed(int n, int Cr, int sigma, long long k_left, const int64_t *__restrict__ offset,
+                  const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
+                  Decode dc, int k, const float *__restrict__ X, int64_t ldx,
+                  float *__restrict__ Y, int64_t ldy) {
+    const int C = C32 ? 32 : Cr;  // a constant word stride when C = 32
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt / G), sub = (int)(gt % G);
+    if (i >= n) return;
+    const int kb = i / C, l = i - kb * C;
+    const int64_t s = offset[kb];
+    const int w = (int)((offset[kb + 1] - s) / C);
+    const uint32_t *__restrict__ pp = pack + s + l;
+    const int c0 = left_offset(i, sigma, k_left);
+    const int io = orig_row(i, sigma, perm, perm_bytes);
+    constexpr int step = 4 * G;
+    for (int q0 = 0; q0 < k; q0 += step * KV) {
+        const int qa = q0 + 4 * sub;
+        float4 acc[KV];
+#pragma unroll
+        for (int h = 0; h < KV; ++h) acc[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int c = c0;
+        for (int j0 = 0; j0 < w; j0 += SPF) {
+            const int wr = w - j0;
+            uint32_t wd[SPF];
+#pragma unroll
+            for (int u = 0; u < SPF; ++u) wd[u] = (u < wr) ? pp[(C32 ? (j0 + u) * 32 : (int64_t)(j0 + u) * C)] : 0u;
+#pragma unroll
+            for (int u = 0; u < SPF; ++u) {
+                const bool f = (wd[u] & 1u) != 0u;
+                c += (int)((wd[u] >> 1) & (f ? dc.dmask : 0x7fffffffu));
+                if (f)
+                    spmm_gather<KV, VEC>(X + (int64_t)c * ldx + qa, qa, step, k,
+                                         word_value<FMT>(wd[u], dc), acc);
+            }
+            if (wd[SPF - 1] == 0u) break;  // the row has ended
+        }
+        spmm_store<KV, VEC>(Y + (int64_t)io * ldy + qa, qa, step, k, acc);
+    }
+}
+
+// The same lane-group SpMM for FP32 SELL: every stored slot multiplies
+// (padding holds value 0), as in the SELL SpMV.
+template <int G, int KV, bool VEC>
 __global__ void __launch_bounds__(TPB)
     k_spmm_sell(int n, int C, int sigma, const int64_t *__restrict__ offset,
                 const float *__restrict__ val, const int32_t *__restrict__ col,
                 const void *__restrict__ perm, int perm_bytes, int k, const float *__restrict__ X,
                 int64_t ldx, float *__restrict__ Y, int64_t ldy) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt / G), sub = (int)(gt % G);
     if (i >= n) return;
-    int kb = i / C, l = i - kb * C;
-    int64_t s = offset[kb];
-    int w = (int)((offset[kb + 1] - s) / C);
-    int io = orig_row(i, sigma, perm, perm_bytes);
-    for (int r0 = 0; r0 < k; r0 += KT) {
-        float acc[KT];
+    const int kb = i / C, l = i - kb * C;
+    const int64_t s = offset[kb];
+    const int w = (int)((offset[kb + 1] - s) / C);
+    const int io = orig_row(i, sigma, perm, perm_bytes);
+    constexpr int step = 4 * G;
+    for (int q0 = 0; q0 < k; q0 += step * KV) {
+        const int qa = q0 + 4 * sub;
+        float4 acc[KV];
 #pragma unroll
-        for (int q = 0; q < KT; ++q) acc[q] = 0.f;
+        for (int h = 0; h < KV; ++h) acc[h] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int j = 0; j < w; ++j) {
-            float v = val[s + (int64_t)j * C + l];
-            const float *xr = X + (int64_t)col[s + (int64_t)j * C + l] * ldx + r0;
-#pragma unroll
-            for (int q = 0; q < KT; ++q)
-                if (r0 + q < k) acc[q] = fmaf(v, __ldg(xr + q), acc[q]);
+            const int64_t p = s + (int64_t)j * C + l;
+            spmm_gather<KV, VEC>(X + (int64_t)col[p] * ldx + qa, qa, step, k, val[p], acc);
         }
-        float *yr = Y + (int64_t)io * ldy + r0;
-#pragma unroll
-        for (int q = 0; q < KT; ++q)
-            if (r0 + q < k) yr[q] = acc[q];
+        spmm_store<KV, VEC>(Y + (int64_t)io * ldy + qa, qa, step, k, acc);
     }
 }
 
@@ -860,34 +939,57 @@ packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaS
     return PACKSELL_OK;
 }
 
-packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, float *Y,
-                          int64_t ldy, cudaStream_t s) {
-    if (k < 1 || ldx < k || ldy < k)
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: need k >= 1, ldx >= k, ldy >= k");
-    if (A.n == 0) return PACKSELL_OK;
-    const void *perm = A.p.explicit_perm ? nullptr : A.perm;
-    int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
-    int g = grid_for(A.n);
-    constexpr int KT = 16;
+template <int G, int KV, bool VEC>
+void launch_spmm(const Matrix &A, const void *perm, int pb, int k, const float *X, int64_t ldx,
+                 float *Y, int64_t ldy, cudaStream_t s) {
+    const int64_t threads = A.n * G;
+    const unsigned g = (unsigned)((threads + TPB - 1) / TPB);
     switch (A.p.format) {
         case PACKSELL_FMT_FP16:
-            k_spmm_packed<PACKSELL_FMT_FP16, KT><<<g, TPB, 0, s>>>(
+            (A.p.C == 32 ? k_spmm_packed<PACKSELL_FMT_FP16, G, KV, VEC, true>
+                         : k_spmm_packed<PACKSELL_FMT_FP16, G, KV, VEC, false>)<<<g, TPB, 0, s>>>(
                 (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A),
                 k, X, ldx, Y, ldy);
             break;
         case PACKSELL_FMT_E8MY:
-            k_spmm_packed<PACKSELL_FMT_E8MY, KT><<<g, TPB, 0, s>>>(
+            (A.p.C == 32 ? k_spmm_packed<PACKSELL_FMT_E8MY, G, KV, VEC, true>
+                         : k_spmm_packed<PACKSELL_FMT_E8MY, G, KV, VEC, false>)<<<g, TPB, 0, s>>>(
                 (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A),
                 k, X, ldx, Y, ldy);
             break;
-        case PACKSELL_FMT_SELL_F32:
-            k_spmm_sell<KT><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
-                                              (const float *)A.val, A.col, perm, pb, k, X, ldx, Y,
-                                              ldy);
-            break;
         default:
-            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: SELL_F64 not supported");
+            k_spmm_sell<G, KV, VEC><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
+                                                     (const float *)A.val, A.col, perm, pb, k, X,
+                                                     ldx, Y, ldy);
     }
+}
+
+template <int G, int KV>
+void launch_spmm_v(bool vec, const Matrix &A, const void *perm, int pb, int k, const float *X,
+                   int64_t ldx, float *Y, int64_t ldy, cudaStream_t s) {
+    if (vec) launch_spmm<G, KV, true>(A, perm, pb, k, X, ldx, Y, ldy, s);
+    else launch_spmm<G, KV, false>(A, perm, pb, k, X, ldx, Y, ldy, s);
+}
+
+packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, float *Y,
+                          int64_t ldy, cudaStream_t s) {
+    if (k < 1 || ldx < k || ldy < k)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: need k >= 1, ldx >= k, ldy >= k");
+    if (A.p.format == PACKSELL_FMT_SELL_F64)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: SELL_F64 not supported");
+    if (A.n == 0) return PACKSELL_OK;
+    if (k == 1 && ldx == 1 && ldy == 1) return spmv_impl(A, X, Y, s);  // the tuned SpMV
+    const void *perm = A.p.explicit_perm ? nullptr : A.perm;
+    int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
+    const bool vec = k % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 &&
+                     ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+    // lanes per row and column groups per lane: one pass for k <= 128
+    if (k <= 4) launch_spmm_v<1, 1>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
+    else if (k <= 8) launch_spmm_v<1, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
+    else if (k <= 16) launch_spmm_v<2, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
+    else if (k <= 32) launch_spmm_v<4, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
+    else if (k <= 64) launch_spmm_v<8, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
+    else launch_spmm_v<16, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
     PS_LAUNCH_CHECK("packsell_spmm");
     return PACKSELL_OK;
 }

@@ -192,8 +192,12 @@ def test_sell_f32_and_f64():
 
 
 @pytest.mark.parametrize("fmt,D,k", [("fp16", 15, 1), ("e8my", 11, 4), ("e8my", 2, 16),
-                                     ("fp16", 15, 64), ("sell_f32", 0, 5)])
+                                     ("fp16", 15, 64), ("sell_f32", 0, 5), ("fp16", 15, 3),
+                                     ("e8my", 7, 32), ("fp16", 15, 100), ("sell_f32", 0, 130),
+                                     ("e8my", 15, 136), ("fp16", 15, 8)])
 def test_spmm(fmt, D, k):
+    """Lane-group SpMM: k = 1 routes through the SpMV; k % 4 != 0 takes the
+    scalar loads; k > 128 takes two passes. Every column equals the twin."""
     need_gpu()
     packsell = P()
     csr = I.random_csr(1500, 1200, 0.005, seed=k, empty_rows=0.05, long_gaps=True)
@@ -207,6 +211,35 @@ def test_spmm(fmt, D, k):
         twin = O.csr_spmv_fma_f32(csr, deq.astype(np.float32), np.ascontiguousarray(X[:, r]))
         assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32))
     assert np.abs(Y - ref).max() <= REL_TOL * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("fmt,C,sigma,explicit,k", [("fp16", 32, 256, True, 16),
+                                                     ("e8my", 8, 1, False, 12),
+                                                     ("sell_f32", 16, 64, False, 24),
+                                                     ("fp16", 32, 100, False, 64)])
+def test_spmm_strided_layouts(fmt, C, sigma, explicit, k):
+    """X and Y as column slices of wider arrays (ld = k + 3: scalar loads),
+    other slice heights, no sorting, a non-power-of-two sigma, both orders."""
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(900, 700, 0.01, seed=C + k, empty_rows=0.05, long_gaps=True)
+    enc = None if fmt == "sell_f32" else O.encode(csr, C=C, sigma=sigma, D=11 if fmt == "e8my" else 15,
+                                                  fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, C=C, sigma=sigma, D=11 if fmt == "e8my" else 15,
+                   explicit_perm=explicit)
+    deq = csr.val.astype(np.float64) if enc is None else enc.deq
+    Xw = np.random.default_rng(k).uniform(-1, 1, (700, k + 3)).astype(np.float32)
+    Xd = dev(Xw)[:, 1:k + 1]
+    Yd = torch.full((900, k + 3), float("nan"), device="cuda")
+    packsell.packsell_spmm(A, Xd, Yd[:, 2:k + 2])
+    Y = Yd.cpu().numpy()
+    assert np.isnan(Y[:, :2]).all() and np.isnan(Y[:, k + 2:]).all()  # nothing written outside
+    Y = Y[:, 2:k + 2]
+    if explicit:
+        Y = Y[np.argsort(O.storage_rows(O.encode(csr, C=C, sigma=sigma, D=15, fmt=O.FMT_FP16)))]
+    for r in range(k):
+        twin = O.csr_spmv_fma_f32(csr, deq.astype(np.float32), np.ascontiguousarray(Xw[:, r + 1]))
+        assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32)), f"column {r}"
 
 
 @pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 3), ("sell_f32", 15)])
