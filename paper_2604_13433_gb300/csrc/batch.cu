@@ -57,7 +57,7 @@ __device__ __forceinline__ float row_dot(const BatchMat &M, int row, int64_t s, 
         const int wr = w - j0;
         uint32_t wd[BPF];
 #pragma unroll
-        for (int u = 0; u < BPF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * 32] : 0u;
+        for (int u = 0; u < BPF; ++u) wd[u] = (u < wr) ? ldg_stream(pp + (j0 + u) * 32) : 0u;
         bool f[BPF];
         float xv[BPF];
 #pragma unroll

@@ -73,11 +73,10 @@ __device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
     return __uint_as_float(wd & dc.vmask);
 }
 
-__device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) {
-    uint32_t v;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
+// A word of the packed stream is read once: a cache-streaming load (evict
+// first) keeps the words from taking L1 and L2 lines from the x gathers
+// (with plain loads the words evict x and the gathers fall through to L2).
+__device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) { return __ldcs(p); }
 
 // ---- mbarrier and bulk-copy (TMA engine) primitives, inline PTX ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {

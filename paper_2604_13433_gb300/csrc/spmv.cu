@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(TPB)
 }
 
 // Thread-per-row SpMV with row register prefetch: each thread first issues
-// the loads of up to PF words of its row at once (plain loads the compiler
-// can predicate on j < w), then decodes them, issues their x
+// the loads of up to PF words of its row at once (L1-bypassing loads
+// predicated on j < w), then decodes them, issues their x
 // gathers, and finally runs the fused multiply-adds in stored order. A row of
 // up to PF words costs one memory round trip for its words and one for its
 // gathers. Words past the row's slice width are taken as 0 (padding).
@@ -97,7 +97,7 @@ __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, l
         // loads predicated on the width; a word past it acts as padding
         uint32_t wd[PF];
 #pragma unroll
-        for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? pp[(j0 + u) * C] : 0u;
+        for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? ldg_stream(pp + (j0 + u) * C) : 0u;
         bool f[PF];
         float xv[PF];
 #pragma unroll
@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(TPB, MINB)
             const int r0 = w0 - j0, r1 = w1 - j0;
             uint32_t a[PF], b[PF];
 #pragma unroll
-            for (int u = 0; u < PF; ++u) a[u] = (u < r0) ? p0[(j0 + u) * 32] : 0u;
+            for (int u = 0; u < PF; ++u) a[u] = (u < r0) ? ldg_stream(p0 + (j0 + u) * 32) : 0u;
 #pragma unroll
-            for (int u = 0; u < PF; ++u) b[u] = (u < r1) ? p1[(j0 + u) * 32] : 0u;
+            for (int u = 0; u < PF; ++u) b[u] = (u < r1) ? ldg_stream(p1 + (j0 + u) * 32) : 0u;
             bool fa[PF], fb[PF];
             float xa[PF], xb[PF];
 #pragma unroll
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(TPB)
         for (int j = 0; j < w; ++j) {
             bool f;
             float xv;
-            const uint32_t wd = pack[s + (int64_t)j * C + l];
+            const uint32_t wd = ldg_stream(pack + s + (int64_t)j * C + l);
             word_gather<FMT>(wd, dc, x, c, f, xv);
             if (f) t = fmaf(word_value<FMT>(wd, dc), xv, t);
         }
@@ -686,7 +686,8 @@ __global__ void __launch_bounds__(TPB)
             const int wr = w - j0;
             uint32_t wd[SPF];
 #pragma unroll
-            for (int u = 0; u < SPF; ++u) wd[u] = (u < wr) ? pp[(C32 ? (j0 + u) * 32 : (int64_t)(j0 + u) * C)] : 0u;
+            for (int u = 0; u < SPF; ++u)
+                wd[u] = (u < wr) ? ldg_stream(pp + (C32 ? (j0 + u) * 32 : (int64_t)(j0 + u) * C)) : 0u;
 #pragma unroll
             for (int u = 0; u < SPF; ++u) {
                 const bool f = (wd[u] & 1u) != 0u;
