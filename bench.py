@@ -308,6 +308,27 @@ def extended_section(ps, torch, dev, K, W):
                        "words": S.n_words}
     del S
     sec["cusparse_csr_f32"] = cusparse_csr_gbps(torch, rp, cl, vl, csr.n, csr.m, x, K, W)
+    # the same matrix packed in CSR order (C = 1, sigma = 1: no padding), SpMV
+    # variant 11 and SpMM
+    Acsr = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="fp16", D=15, C=1, sigma=1)
+    tuned_c = ps.packsell_tune_spmv(Acsr, x, y, reps=20)
+    ms, _ = time_launches(torch, lambda: ps.packsell_spmv(Acsr, x, y), K, W)
+    nbc = spmv_bytes(Acsr, False)
+    spmm_c = {}
+    for k in (4, 16, 64):
+        X = torch.rand(csr.m, k, device=dev)
+        Y = torch.empty(csr.n, k, device=dev)
+        msk, _ = time_launches(torch, lambda: ps.packsell_spmm(Acsr, X, Y), max(K // 10, 5), 3)
+        nbk = 4 * Acsr.n_words + 8 * (Acsr.n_slices + 1) + 4 * k * (csr.m + csr.n)
+        spmm_c[str(k)] = {"GBps": nbk / msk / 1e6, "us": msk * 1e3}
+        del X, Y
+    sec["packcsr_fp16"] = {"GBps": nbc / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6,
+                           "us": ms * 1e3, "bytes": nbc, "words": Acsr.n_words,
+                           "words_per_nnz": Acsr.n_words / csr.nnz,
+                           "variant": min(tuned_c, key=tuned_c.get),
+                           "tuner_us": {str(v): t * 1e3 for v, t in tuned_c.items()},
+                           "spmm": spmm_c}
+    del Acsr
     spmm = {}
     for k in (1, 4, 16, 64):
         X = torch.rand(csr.m, k, device=dev)

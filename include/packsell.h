@@ -180,6 +180,9 @@ packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, dou
 packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X,
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 
+/* Number of SpMV kernel variants (1..PACKSELL_SPMV_VARIANTS). */
+#define PACKSELL_SPMV_VARIANTS 11
+
 /* SpMV kernel variants (all compute the same bits):
  *   0 auto (the plan's or the tuner's choice),
  *   1 thread-per-row with direct loads (the paper's mapping, §5.1.1),
@@ -197,14 +200,25 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *   9, 10 stage-planned TMA: at encode time each warp's slices are cut into
  *     stages of whole slices (at most 4 KB (9) or 2 KB (10)); one
  *     cp.async.bulk per stage into a double-buffered shared-memory slot with
- *     an mbarrier; the consumer waits once per stage (PackSELL, C = 32). */
+ *     an mbarrier; the consumer waits once per stage (PackSELL, C = 32). *
+ *  11 CSR order (PackSELL with C = 1: each slice is one row, the words of the
+ *     rows lie one after another with no padding, the delta-value packing in
+ *     CSR order that §7 leaves as future work for matrices too irregular for
+ *     SELL). At encode time the rows are cut into tiles of at most 256 words
+ *     and 64 rows, and rows of more than 256 words become items of their own.
+ *     A warp copies a tile's words to shared memory with coalesced loads and
+ *     its lanes sum one row each; a long row is walked 256 words at a time
+ *     with a warp prefix sum of the deltas for the columns, parallel gathers
+ *     and one in-order chain of fused multiply-adds. Same bits as variant 1.
+ *     The plan's default for C = 1 PackSELL matrices. */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant for this matrix: time every available variant
  * (`reps` launches each after a warm-up, CUDA events on `stream`) on the
  * caller's x [m] and y [n], and make variant 0 run the fastest. Writes y.
  * Synchronises `stream`. If h_times is not NULL it receives the average
- * milliseconds per launch of variants 1..10 (0 where unavailable). */
+ * milliseconds per launch of variants 1..PACKSELL_SPMV_VARIANTS (0 where
+ * unavailable). */
 packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
                                    float *h_times, void *stream);
 

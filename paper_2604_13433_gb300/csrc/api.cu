@@ -242,9 +242,16 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     clear_error();
-    if (!A || variant < 0 || variant > 10)
+    if (!A || variant < 0 || variant > PACKSELL_SPMV_VARIANTS)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
+    if (variant == 11) {
+        if (!m->csr_items)
+            return fail(PACKSELL_ERR_INVALID_ARG,
+                        "packsell_set_spmv_variant: variant 11 needs a PackSELL matrix with C = 1");
+        m->variant = variant;
+        return PACKSELL_OK;
+    }
     if (variant >= 2 && variant <= 4 && !m->part[variant - 2])
         return fail(PACKSELL_ERR_INVALID_ARG,
                     "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
@@ -264,7 +271,7 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
     cudaStream_t s = as_stream(stream);
-    const int nvar = 10;
+    const int nvar = PACKSELL_SPMV_VARIANTS;
     if (h_times)
         for (int v = 0; v < nvar; ++v) h_times[v] = 0.f;
     cudaEvent_t e0, e1;
@@ -276,7 +283,8 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     packsell_status st = PACKSELL_OK;
     for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
         if (var >= 2 && !is_packed(m->p.format)) continue;
-        if (var >= 5 && m->p.C != 32) continue;
+        if (var == 11 && !m->csr_items) continue;
+        if (var >= 5 && var <= 10 && m->p.C != 32) continue;
         if (var >= 9 && !m->stage[var - 9].part) continue;
         if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;
         m->variant = var;

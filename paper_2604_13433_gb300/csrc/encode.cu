@@ -407,6 +407,7 @@ void free_matrix_arrays(Matrix *A) {
     cudaFree(A->status);
     for (int v = 0; v < Matrix::kBulkVariants; ++v) cudaFree(A->part[v]);
     stage_free(*A);
+    csr_plan_free(*A);
 }
 
 }  // namespace

@@ -51,6 +51,10 @@ struct Matrix {
     int part_blocks[kBulkVariants] = {};
     static constexpr int kStageVariants = 2;  // variants 9, 10
     StagePlan stage[kStageVariants];
+    // variant 11 (C = 1): work items (first row, last row + 1) of the
+    // CSR-order kernel, as int2 pairs
+    void *csr_items = nullptr;
+    int csr_nitems = 0;
 };
 
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
@@ -73,6 +77,12 @@ packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_
 // stage.cu
 packsell_status plan_stage(Matrix &A, cudaStream_t s);
 void stage_free(Matrix &A);
+
+// csr.cu
+packsell_status plan_csr(Matrix &A, cudaStream_t s);
+void csr_plan_free(Matrix &A);
+packsell_status launch_csr(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+                           cudaStream_t s);
 packsell_status launch_stage(const Matrix &A, int v, const void *perm, int pb, const float *x,
                              float *y, cudaStream_t s);
 

@@ -826,6 +826,12 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
         PS_CUDA(cudaMemsetAsync(A.status, 0, sizeof(DevStatus), s));
     }
     A.auto_variant = 1;
+    if (is_packed(A.p.format) && A.p.C == 1 && A.n > 0 && A.n < INT32_MAX) {
+        const packsell_status st = plan_csr(A, s);
+        if (st != PACKSELL_OK) return st;
+        if (A.csr_items) A.auto_variant = 11;
+        return PACKSELL_OK;
+    }
     // the bulk kernel indexes a warp's words with 32-bit integers
     if (!is_packed(A.p.format) || A.p.C != 32 || A.n == 0 || A.n_words >= (1ll << 31) - 4096)
         return PACKSELL_OK;
@@ -859,6 +865,7 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     int g = grid_for(A.n);
     const int var = A.variant == 0 ? A.auto_variant : A.variant;
+    if (var == 11 && is_packed(A.p.format)) return launch_csr(A, perm, pb, x, y, s);
     if ((var == 9 || var == 10) && is_packed(A.p.format))
         return launch_stage(A, var - 9, perm, pb, x, y, s);
     if ((var == 7 || var == 8) && is_packed(A.p.format)) {

@@ -30,6 +30,8 @@ SPMV_BULK_VARIANTS = (2, 3, 4)
 SPMV_PREFETCH = (5, 6)
 SPMV_DUAL = (7, 8)
 SPMV_STAGE = (9, 10)
+SPMV_CSR = 11  # C = 1 PackSELL matrices (rows stored one after another)
+SPMV_VARIANTS = 11
 
 
 class PackSELLError(RuntimeError):
@@ -220,11 +222,11 @@ def packsell_tune_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | Non
     Returns {variant: ms per launch} for the variants that ran."""
     if y is None:
         y = torch.empty(A.n, dtype=torch.float32, device=x.device)
-    times = (ctypes.c_float * 10)()
+    times = (ctypes.c_float * SPMV_VARIANTS)()
     _check(lib().packsell_tune_spmv(A.handle, _dev(x, torch.float32, "x", A.m),
                                     _dev(y, torch.float32, "y", A.n), int(reps), times,
                                     _stream(stream)))
-    return {v + 1: times[v] for v in range(10) if times[v] > 0}
+    return {v + 1: times[v] for v in range(SPMV_VARIANTS) if times[v] > 0}
 
 
 def packsell_check_status(A: PackSELLMatrix, stream=None) -> None:

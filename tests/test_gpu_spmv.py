@@ -32,6 +32,8 @@ def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0, rel_tol=Non
         variants += list(packsell.SPMV_PREFETCH) + list(packsell.SPMV_DUAL) + list(packsell.SPMV_STAGE)
     if C == 32 and csr.n > 0 and fmt in ("fp16", "e8my"):
         variants += list(packsell.SPMV_BULK_VARIANTS)
+    if C == 1 and csr.n > 0 and fmt in ("fp16", "e8my"):
+        variants.append(packsell.SPMV_CSR)
     ys = []
     for v in variants:
         packsell.packsell_set_spmv_variant(A, v)
@@ -144,6 +146,42 @@ def test_storage_rows_maps_explicit_to_original(fmt, D, sigma):
     yo[rows.long()] = ye
     yi = packsell.packsell_spmv(Ai, x)
     assert torch.equal(yo.view(torch.int32), yi.view(torch.int32))
+
+
+def _lengths_csr(lengths, m, seed):
+    """A CSR with the given row lengths (distinct random columns per row)."""
+    rng = np.random.default_rng(seed)
+    cols = [np.sort(rng.choice(m, size=L, replace=False)) for L in lengths]
+    rowptr = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32) if sum(lengths) else np.zeros(0, np.int32)
+    val = rng.uniform(-1, 1, int(rowptr[-1])).astype(np.float32)
+    return I.CSR(n=len(lengths), m=m, rowptr=rowptr, col=col, val=val)
+
+
+@pytest.mark.parametrize("fmt,D,sigma,explicit", [("fp16", 15, 1, False), ("e8my", 11, 1, True),
+                                                  ("fp16", 15, 256, False), ("e8my", 3, 1, False),
+                                                  ("e8my", 7, 100, True)])
+def test_spmv_csr_order_zipf(fmt, D, sigma, explicit):
+    """CSR-order packing (C = 1, variant 11) on power-law rows up to 4,096
+    words: tiles of short rows and the long-row path, bitwise the twin."""
+    need_gpu()
+    csr = I.zipf_irregular(30000, seed=5)
+    A, enc, x, y = check_spmv(csr, fmt, D, C=1, sigma=sigma, explicit=explicit)
+    assert A.n_pad == 0
+
+
+def test_spmv_csr_order_tile_edges():
+    """Row lengths around the 256-word tile limit and the 64-row tile cap,
+    empty rows, and rows with many dummies (D = 2)."""
+    need_gpu()
+    lengths = [0, 1, 255, 256, 257, 0, 511, 512, 513, 3] + [4] * 70 + [0] * 40 + [256, 1, 1000, 2]
+    csr = _lengths_csr(lengths, 5000, seed=1)
+    for fmt, D in (("fp16", 15), ("e8my", 2)):
+        check_spmv(csr, fmt, D, C=1, sigma=1)
+    packsell = P()
+    A = encode_gpu(csr, fmt="fp16", C=1, sigma=1)
+    times = packsell.packsell_tune_spmv(A, dev(I.uniform(csr.m, seed=2)), reps=3)
+    assert packsell.SPMV_CSR in times and 5 not in times  # C = 32 variants are skipped
 
 
 def test_tune_spmv_picks_a_variant():

@@ -181,6 +181,29 @@ def test_encode_layout_and_roundtrip(case):
     _roundtrip(csr, e)
 
 
+@pytest.mark.parametrize("D,fmt", [(15, O.FMT_FP16), (5, O.FMT_E8MY)])
+def test_csr_order_layout(D, fmt):
+    """C = 1, sigma = 1 is delta-value packing in CSR order: each slice is one
+    row, so the pack is the rows' word sequences one after another (no
+    padding) and the offsets are their running sums. The expected words are
+    built here from numpy deltas (Eq. 2, Eq. 4) and the dummy rule (§4.3)."""
+    csr = I.random_csr(120, 300, 0.05, seed=D, empty_rows=0.1, long_gaps=True)
+    e = O.encode(csr, C=1, sigma=1, D=D, fmt=fmt)
+    d, row = _deltas(csr, 1, e.k_left)
+    want, counts = [], np.zeros(csr.n, np.int64)
+    for p in range(csr.nnz):
+        if d[p] >= (1 << D):
+            want.append(O.word_dummy(int(d[p])))
+            want.append(int(e.field[p]) | 1)
+            counts[row[p]] += 2
+        else:
+            want.append(int(e.field[p]) | (int(d[p]) << 1) | 1)
+            counts[row[p]] += 1
+    assert e.n_pad == 0 and e.n_words == len(want)
+    assert [int(w) for w in e.pack] == want
+    assert np.array_equal(e.offset, np.concatenate([[0], np.cumsum(counts)]))
+
+
 def test_empty_matrix_and_all_empty_rows():
     csr = I.CSR(n=5, m=7, rowptr=np.zeros(6, np.int64), col=np.zeros(0, np.int32),
                 val=np.zeros(0, np.float32))
