@@ -387,39 +387,16 @@ def diff_solve_section(ps, torch, dev):
     backward (adjoint solve, dA on the pattern, chain to the faces) timed."""
     from paper_2604_13433_gb300 import autograd as ag
 
-    rng = np.random.default_rng(6)
-    sides = rng.integers(32, 257, size=512)
-    rows, cols, faces_th, pos = [], [], [], []
-    uu, vv, uv, vu, pb = [], [], [], [], []
-    off_r = off_q = 0
-    for i, L in enumerate(sides):
-        c, f = I.poisson5_varcoef(int(L), seed=1000 + i)
-        rows.append(c.rowptr[:-1] + off_q)
-        cols.append(c.col.astype(np.int64) + off_r)
-        faces_th.append(f["theta"])
-        F = f["u"].size
-        uu.append(f["pos_uu"] + off_q)
-        vv.append(f["pos_vv"] + off_q)
-        uv.append(f["pos_uv"] + off_q)
-        vu.append(f["pos_vu"] + off_q)
-        pb.append(f["pos_b"] + off_q)
-        pos.append((F, f["theta"].size - F))
-        off_r += c.n
-        off_q += c.nnz
-    n, nnz = off_r, off_q
-    rowptr = np.append(np.concatenate(rows), nnz).astype(np.int64)
-    col = np.concatenate(cols).astype(np.int32)
-    # face and boundary coefficients of all systems, interior faces first per system
-    th_f = np.concatenate([t[:F] for t, (F, _) in zip(faces_th, pos)])
-    th_b = np.concatenate([t[F:] for t, (F, _) in zip(faces_th, pos)])
-    P = {k: torch.from_numpy(np.concatenate(v)).to(dev) for k, v in
-         (("uu", uu), ("vv", vv), ("uv", uv), ("vu", vu), ("b", pb))}
-    Ff = th_f.size
-    theta = torch.from_numpy(np.concatenate([th_f, th_b])).to(dev).requires_grad_(True)
+    csr, parts = I.poisson5_varcoef_batch(512, seed=6)
+    n, nnz = csr.n, csr.nnz
+    P = {k: torch.from_numpy(parts["pos_" + k]).to(dev) for k in ("uu", "vv", "uv", "vu", "b")}
+    Ff = parts["theta_f"].size
+    theta = torch.from_numpy(np.concatenate([parts["theta_f"], parts["theta_b"]])).to(dev)
+    theta.requires_grad_(True)
     b = torch.from_numpy(I.uniform(n, seed=7).astype(np.float64)).to(dev).requires_grad_(True)
     xt = torch.from_numpy(I.normal(n, seed=8)).to(dev)
-    rp = torch.from_numpy(rowptr).to(dev)
-    cl = torch.from_numpy(col).to(dev)
+    rp = torch.from_numpy(csr.rowptr).to(dev)
+    cl = torch.from_numpy(csr.col).to(dev)
 
     def assemble(th):
         v = torch.zeros(nnz, dtype=th.dtype, device=dev)

@@ -324,6 +324,43 @@ def zipf_batch(count: int = 256, seed: int = 0, nmin: int = 1000, nmax: int = 10
             for s, sd in zip(sizes, seeds)]
 
 
+def poisson5_varcoef_batch(count: int = 512, seed: int = 6, lmin: int = 32, lmax: int = 256,
+                           sigma: float = 0.5):
+    """``count`` SPD 5-point variable-coefficient systems on L x L grids, L
+    uniform on [lmin, lmax], assembled block-diagonally. Returns (csr, parts):
+    csr has the block-diagonal pattern and values; parts holds, per system,
+    its row offset ``row0``, side ``L``, nonzero offset ``nz0``, face dict
+    (positions local to the system) and the seed it was drawn with, plus the
+    concatenated global position arrays ``pos_uu/vv/uv/vu`` (interior faces of
+    every system, in system order), ``pos_b`` (boundary terms) and
+    ``theta_f``/``theta_b`` (their coefficients)."""
+    rng = _rng(seed)
+    sides = rng.integers(lmin, lmax + 1, size=count)
+    rows, cols, vals, systems = [], [], [], []
+    glob = {k: [] for k in ("pos_uu", "pos_vv", "pos_uv", "pos_vu", "pos_b")}
+    th_f, th_b = [], []
+    r0 = z0 = 0
+    for i, L in enumerate(sides):
+        c, f = poisson5_varcoef(int(L), seed=1000 + i, sigma=sigma)
+        rows.append(c.rowptr[:-1] + z0)
+        cols.append(c.col.astype(np.int64) + r0)
+        vals.append(c.val)
+        for k in glob:
+            glob[k].append(f[k] + z0)
+        F = f["u"].size
+        th_f.append(f["theta"][:F])
+        th_b.append(f["theta"][F:])
+        systems.append({"row0": r0, "L": int(L), "nz0": z0, "faces": f, "csr": c})
+        r0 += c.n
+        z0 += c.nnz
+    rowptr = np.append(np.concatenate(rows), z0).astype(np.int64)
+    csr = CSR(n=r0, m=r0, rowptr=rowptr, col=np.concatenate(cols).astype(np.int32),
+              val=np.concatenate(vals), meta={"kind": "poisson5_varcoef_batch", "count": count})
+    parts = {k: np.concatenate(v) for k, v in glob.items()}
+    parts.update(theta_f=np.concatenate(th_f), theta_b=np.concatenate(th_b), systems=systems)
+    return csr, parts
+
+
 # --------------------------------------------------------------------------
 # vectors and small random matrices
 # --------------------------------------------------------------------------

@@ -262,3 +262,24 @@ def test_irregular_generator_small_dense_rows():
         first[c.rowptr[:-1][c.row_lengths() > 0]] = True
         assert np.all(d[~first[1:]] > 0) and c.col.max() < c.m and c.col.min() >= 0
         assert O.check_csr(c) == 0
+
+
+def test_poisson5_batch_generator_blocks_and_face_model():
+    """The block-diagonal batch: each block equals its own system, and the
+    values are the face model sum_f theta_f (e_u - e_v)(e_u - e_v)^T plus
+    boundary terms, assembled here from the position arrays with numpy."""
+    csr, parts = I.poisson5_varcoef_batch(6, seed=2, lmin=3, lmax=9)
+    v = np.zeros(csr.nnz)
+    np.add.at(v, parts["pos_uu"], parts["theta_f"])
+    np.add.at(v, parts["pos_vv"], parts["theta_f"])
+    np.add.at(v, parts["pos_uv"], -parts["theta_f"])
+    np.add.at(v, parts["pos_vu"], -parts["theta_f"])
+    np.add.at(v, parts["pos_b"], parts["theta_b"])
+    assert np.allclose(v, csr.val, rtol=1e-15, atol=0)
+    for sy in parts["systems"]:
+        c = sy["csr"]
+        r0, z0 = sy["row0"], sy["nz0"]
+        assert c.n == sy["L"] ** 2
+        assert np.array_equal(csr.rowptr[r0:r0 + c.n + 1] - z0, c.rowptr)
+        assert np.array_equal(csr.col[z0:z0 + c.nnz] - r0, c.col)
+
