@@ -60,7 +60,8 @@ def parse():
                     help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
                          "e8m15), 'all' or 'none'")
     ap.add_argument("--pcg-grid", type=int, default=256, help="7-point Poisson grid side")
-    ap.add_argument("--pcg-min", type=int, default=20, help="inner iterations of IO-CG")
+    ap.add_argument("--pcg-min", default="20,80",
+                    help="inner iterations of IO-CG, comma-separated (the paper sweeps 20, 50, 80)")
     return ap.parse_args()
 
 
@@ -439,7 +440,7 @@ def pcg_section(ps, torch, dev, grid, m_in):
     vl = torch.from_numpy(csr.val).to(dev)
     b = torch.from_numpy(b_h).to(dev)
     out = {"workload": f"poisson7_varcoef_{grid}^3", "n": csr.n, "nnz": csr.nnz,
-           "rtol": 1e-10, "m_in": m_in}
+           "rtol": 1e-10, "m_in": list(m_in)}
     x = torch.zeros(csr.n, dtype=torch.float64, device=dev)
     for sigma in (256, 1):
         sec = out if sigma == 256 else out.setdefault("sigma1", {})
@@ -452,13 +453,17 @@ def pcg_section(ps, torch, dev, grid, m_in):
         for name, fmt, D in (("iocg_fp16", "fp16", 15), ("iocg_e8m11", "e8my", 11),
                              ("iocg_sell_f32", "sell_f32", 15)):
             Ain = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D, sigma=sigma)
-            x.zero_()
-            _, info = ps.packsell_pcg(A64, b, x, A_inner=Ain, m_in=m_in, rtol=1e-10,
-                                      max_iters=5000, check=False)
-            sec[name] = {k: info[k] for k in ("seconds", "iters", "inner_iters", "relres_true",
-                                              "status")}
-            sec[name]["speedup_vs_fp64_pcg"] = base / info["seconds"] if info["seconds"] else None
-            sec[name]["inner_words"] = Ain.n_words
+            for mi in m_in:
+                key = name if mi == m_in[0] else f"{name}_m{mi}"
+                x.zero_()
+                _, info = ps.packsell_pcg(A64, b, x, A_inner=Ain, m_in=mi, rtol=1e-10,
+                                          max_iters=5000, check=False)
+                sec[key] = {k: info[k] for k in ("seconds", "iters", "inner_iters",
+                                                 "relres_true", "status")}
+                sec[key]["m_in"] = mi
+                sec[key]["speedup_vs_fp64_pcg"] = (base / info["seconds"] if info["seconds"]
+                                                   else None)
+                sec[key]["inner_words"] = Ain.n_words
             del Ain
         del A64
     return out
@@ -635,7 +640,8 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if not args.no_pcg:
-        line["pcg"] = pcg_section(ps, torch, dev, args.pcg_grid, args.pcg_min)
+        line["pcg"] = pcg_section(ps, torch, dev, args.pcg_grid,
+                                  [int(v) for v in str(args.pcg_min).split(",")])
     if args.extended:
         line["extended"] = extended_section(ps, torch, dev, K, W)
     if rank == 0 and not args.no_cpu:

@@ -181,7 +181,7 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 
 /* Number of SpMV kernel variants (1..PACKSELL_SPMV_VARIANTS). */
-#define PACKSELL_SPMV_VARIANTS 11
+#define PACKSELL_SPMV_VARIANTS 12
 
 /* SpMV kernel variants (all compute the same bits):
  *   0 auto (the plan's or the tuner's choice),
@@ -200,7 +200,7 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *   9, 10 stage-planned TMA: at encode time each warp's slices are cut into
  *     stages of whole slices (at most 4 KB (9) or 2 KB (10)); one
  *     cp.async.bulk per stage into a double-buffered shared-memory slot with
- *     an mbarrier; the consumer waits once per stage (PackSELL, C = 32). *
+ *     an mbarrier; the consumer waits once per stage (PackSELL, C = 32).
  *  11 CSR order (PackSELL with C = 1: each slice is one row, the words of the
  *     rows lie one after another with no padding, the delta-value packing in
  *     CSR order that §7 leaves as future work for matrices too irregular for
@@ -210,7 +210,14 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     its lanes sum one row each; a long row is walked 256 words at a time
  *     with a warp prefix sum of the deltas for the columns, parallel gathers
  *     and one in-order chain of fused multiply-adds. Same bits as variant 1.
- *     The plan's default for C = 1 PackSELL matrices. */
+ *     The plan's default for C = 1 PackSELL matrices.
+ *  12 pipelined persistent (PackSELL, C = 32): each thread walks rows i,
+ *     i + stride, ... and loads the next row's words (and the slice offsets
+ *     of the row after it) before it decodes and gathers the current row, so
+ *     the word loads of one row overlap the gathers of the previous one; one
+ *     round per row, fitted to the widest slice as in 5, so every slice must
+ *     hold at most 16 words. For short rows (the solver's 7-point matrices);
+ *     the solver's fused SpMV + dot uses it for such matrices. */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant for this matrix: time every available variant

@@ -150,6 +150,80 @@ __global__ void __launch_bounds__(TPB, MINB)
     reduce_publish(red, (double)d1, 0.0);
 }
 
+// Pipelined persistent SpMV for short rows (variant 12, and the solver's
+// fused SpMV + dot when every row fits one round): each thread walks rows
+// i, i + stride, ... (stride a multiple of 32, so a warp stays on whole
+// slices) and loads the next row's words, and the slice offsets of the row
+// after it, before it decodes and gathers the current row: the word loads
+// of one row overlap the gathers of the previous one. Every slice must fit
+// one round (width <= PF <= 16). Same bits as the thread-per-row kernels.
+template <int FMT, int PF>
+__device__ __forceinline__ void pipe_round(const uint32_t (&wd)[PF], Decode dc,
+                                           const float *__restrict__ x, int &c, float &t) {
+    bool f[PF];
+    float xv[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) word_gather<FMT>(wd[u], dc, x, c, f[u], xv[u]);
+#pragma unroll
+    for (int u = 0; u < PF; ++u)
+        if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
+}
+
+template <int FMT, int PF, int MINB, bool DOT, bool PERM>
+__global__ void __launch_bounds__(TPB, MINB)
+    k_spmv_pipe(int n, int sigma, int sig_shift, long long k_left,
+                const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                const void *__restrict__ perm, int perm_bytes, Decode dc,
+                const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
+    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
+    float d1 = 0.f;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int64_t s = offset[i >> 5];
+        const int w = (int)((offset[(i >> 5) + 1] - s) >> 5);
+        uint32_t cur[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) cur[u] = (u < w) ? ldg_stream(pack + s + (i & 31) + u * 32) : 0u;
+        int in = i + stride;
+        int64_t sn = 0, en = 0;
+        if (in < n) {
+            sn = offset[in >> 5];
+            en = offset[(in >> 5) + 1];
+        }
+        while (true) {
+            const int wn = (int)((en - sn) >> 5);
+            uint32_t nxt[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+                nxt[u] = (in < n && u < wn) ? ldg_stream(pack + sn + (in & 31) + u * 32) : 0u;
+            const int in2 = in + stride;
+            int64_t sn2 = 0, en2 = 0;
+            if (in2 < n) {
+                sn2 = offset[in2 >> 5];
+                en2 = offset[(in2 >> 5) + 1];
+            }
+            const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
+            int c = (k_left < blk) ? (int)(blk - k_left) : 0;
+            float t = 0.f;
+            pipe_round<FMT, PF>(cur, dc, x, c, t);
+            int io = i;
+            if (PERM) io = blk + (perm_bytes == 1 ? (int)((const uint8_t *)perm)[i]
+                                                  : (int)((const uint16_t *)perm)[i]);
+            y[io] = t;
+            if (DOT) d1 = fmaf(x[io], t, d1);
+            if (in >= n) break;
+            i = in;
+#pragma unroll
+            for (int u = 0; u < PF; ++u) cur[u] = nxt[u];
+            in = in2;
+            sn = sn2;
+            en = en2;
+        }
+    }
+    if (DOT) reduce_publish(red, (double)d1, 0.0);
+}
+
 // Dual-row persistent SpMV: every thread handles two rows per loop trip, row
 // i (slice k) and row i + stride (another slice), in lockstep: the word loads
 // of both rows are issued before either is decoded, then both rows' gathers,
@@ -262,6 +336,38 @@ packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const
     else
         launch_prefetch_e<FMT, PF, MINB, false>(A, perm, pb, x, y, s);
     PS_LAUNCH_CHECK("packsell_spmv (prefetch)");
+    return PACKSELL_OK;
+}
+
+template <int FMT, int PF, int MINB, bool PERM>
+int pipe_blocks() {
+    static int blocks = 0;  // persistent grid: every block resident at once
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per, k_spmv_pipe<FMT, PF, MINB, false, PERM>, TPB, 0) != cudaSuccess)
+            return 0;
+        blocks = sms * std::max(per, 1);
+    }
+    return blocks;
+}
+
+template <int FMT, int PF, int MINB>
+packsell_status launch_pipe(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+                            cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    const int blocks = pb ? pipe_blocks<FMT, PF, MINB, true>() : pipe_blocks<FMT, PF, MINB, false>();
+    if (!blocks) return fail(PACKSELL_ERR_CUDA, "packsell_spmv (pipelined): device query failed");
+    if (pb)
+        k_spmv_pipe<FMT, PF, MINB, false, true><<<blocks, TPB, 0, s>>>(
+            (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+    else
+        k_spmv_pipe<FMT, PF, MINB, false, false><<<blocks, TPB, 0, s>>>(
+            (int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+    PS_LAUNCH_CHECK("packsell_spmv (pipelined)");
     return PACKSELL_OK;
 }
 
@@ -866,6 +972,24 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
     int g = grid_for(A.n);
     const int var = A.variant == 0 ? A.auto_variant : A.variant;
     if (var == 11 && is_packed(A.p.format)) return launch_csr(A, perm, pb, x, y, s);
+    if (var == 12 && is_packed(A.p.format)) {
+        if (A.p.C != 32 || A.max_width > 16)
+            return fail(PACKSELL_ERR_INVALID_ARG,
+                        "packsell_spmv: variant 12 needs C = 32 and slices of at most 16 words");
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        const int pf = round_words(A.max_width);
+        if (pf == 8)
+            return h ? launch_pipe<PACKSELL_FMT_FP16, 8, 5>(A, perm, pb, x, y, s)
+                     : launch_pipe<PACKSELL_FMT_E8MY, 8, 5>(A, perm, pb, x, y, s);
+        if (pf == 10)
+            return h ? launch_pipe<PACKSELL_FMT_FP16, 10, 4>(A, perm, pb, x, y, s)
+                     : launch_pipe<PACKSELL_FMT_E8MY, 10, 4>(A, perm, pb, x, y, s);
+        if (pf == 12)
+            return h ? launch_pipe<PACKSELL_FMT_FP16, 12, 4>(A, perm, pb, x, y, s)
+                     : launch_pipe<PACKSELL_FMT_E8MY, 12, 4>(A, perm, pb, x, y, s);
+        return h ? launch_pipe<PACKSELL_FMT_FP16, 16, 3>(A, perm, pb, x, y, s)
+                 : launch_pipe<PACKSELL_FMT_E8MY, 16, 3>(A, perm, pb, x, y, s);
+    }
     if ((var == 9 || var == 10) && is_packed(A.p.format))
         return launch_stage(A, var - 9, perm, pb, x, y, s);
     if ((var == 7 || var == 8) && is_packed(A.p.format)) {
@@ -1102,6 +1226,21 @@ void launch_prefetch_dot(const Matrix &A, const float *x, float *y, const Red &r
     }
 }
 
+template <int FMT, int PF, int MINB>
+void launch_pipe_dot(const Matrix &A, const float *x, float *y, const Red &red, cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    if (A.perm_bytes) {
+        auto k = k_spmv_pipe<FMT, PF, MINB, true, true>;
+        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm,
+                                      A.perm_bytes, make_decode(A), x, y, red);
+    } else {
+        auto k = k_spmv_pipe<FMT, PF, MINB, true, false>;
+        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm, 0,
+                                      make_decode(A), x, y, red);
+    }
+}
+
 int spmv_dot_blocks(const Matrix &) { return reduce_blocks(); }
 
 packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
@@ -1113,6 +1252,24 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
         k_spmv_sell<float, true><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
                                                    (const float *)A.val, A.col, perm, pb, x, y,
                                                    nullptr, red);
+    } else if (A.p.C == 32 && A.max_width <= 16) {
+        // every row fits one round: the pipelined kernel loads the next
+        // row's words while the current row is gathered
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        const int pf = round_words(A.max_width);
+        if (pf == 8) {
+            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 8, 5>(A, x, y, red, s);
+            else launch_pipe_dot<PACKSELL_FMT_E8MY, 8, 5>(A, x, y, red, s);
+        } else if (pf == 10) {
+            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 10, 4>(A, x, y, red, s);
+            else launch_pipe_dot<PACKSELL_FMT_E8MY, 10, 4>(A, x, y, red, s);
+        } else if (pf == 12) {
+            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 12, 4>(A, x, y, red, s);
+            else launch_pipe_dot<PACKSELL_FMT_E8MY, 12, 4>(A, x, y, red, s);
+        } else {
+            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 16, 3>(A, x, y, red, s);
+            else launch_pipe_dot<PACKSELL_FMT_E8MY, 16, 3>(A, x, y, red, s);
+        }
     } else if (A.p.C == 32) {
         // row-prefetch kernel, rounds fitted to the widest slice
         const bool h = A.p.format == PACKSELL_FMT_FP16;

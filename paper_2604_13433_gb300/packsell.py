@@ -31,7 +31,8 @@ SPMV_PREFETCH = (5, 6)
 SPMV_DUAL = (7, 8)
 SPMV_STAGE = (9, 10)
 SPMV_CSR = 11  # C = 1 PackSELL matrices (rows stored one after another)
-SPMV_VARIANTS = 11
+SPMV_PIPE = 12  # C = 32, next row's words loaded while the current one is gathered
+SPMV_VARIANTS = 12
 
 
 class PackSELLError(RuntimeError):

@@ -34,6 +34,8 @@ def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0, rel_tol=Non
         variants += list(packsell.SPMV_BULK_VARIANTS)
     if C == 1 and csr.n > 0 and fmt in ("fp16", "e8my"):
         variants.append(packsell.SPMV_CSR)
+    if C == 32 and csr.n > 0 and fmt in ("fp16", "e8my") and A.max_width <= 16:
+        variants.append(packsell.SPMV_PIPE)
     ys = []
     for v in variants:
         packsell.packsell_set_spmv_variant(A, v)
@@ -182,6 +184,24 @@ def test_spmv_csr_order_tile_edges():
     A = encode_gpu(csr, fmt="fp16", C=1, sigma=1)
     times = packsell.packsell_tune_spmv(A, dev(I.uniform(csr.m, seed=2)), reps=3)
     assert packsell.SPMV_CSR in times and 5 not in times  # C = 32 variants are skipped
+
+
+def test_pipelined_variant_short_rows_only():
+    """Variant 12 runs one round per row: offered for slices of at most 16
+    words (7-point rows with their dummies), refused and skipped otherwise."""
+    need_gpu()
+    packsell = P()
+    csr = I.poisson7_varcoef(24, seed=3)
+    A, enc, x, y = check_spmv(csr, "fp16", 15, sigma=1)
+    assert A.max_width <= 16
+    times = packsell.packsell_tune_spmv(A, dev(x), reps=3)
+    assert packsell.SPMV_PIPE in times
+    B = encode_gpu(I.stencil27(16, seed=1), fmt="fp16")
+    assert B.max_width > 16
+    with pytest.raises(packsell.PackSELLError):
+        packsell.packsell_set_spmv_variant(B, packsell.SPMV_PIPE)
+    assert packsell.SPMV_PIPE not in packsell.packsell_tune_spmv(
+        B, dev(I.uniform(B.m, seed=2)), reps=2)
 
 
 def test_tune_spmv_picks_a_variant():
