@@ -273,6 +273,7 @@ def test_spmm(fmt, D, k):
 
 @pytest.mark.parametrize("fmt,C,sigma,explicit,k", [("fp16", 32, 256, True, 16),
                                                      ("e8my", 8, 1, False, 12),
+                                                     ("fp16", 1, 1, False, 32),
                                                      ("sell_f32", 16, 64, False, 24),
                                                      ("fp16", 32, 100, False, 64)])
 def test_spmm_strided_layouts(fmt, C, sigma, explicit, k):
