@@ -26,6 +26,12 @@
  *    No C++ exception crosses this boundary.
  *  - Index types: row and column counts below 2^31, nonzero and word counts
  *    in int64.
+ *  - Inputs and outputs of one call must not overlap (x and y of a product,
+ *    X and Y of packsell_spmm, the solver's b and x).
+ *  - A matrix is read-only to the products, which may run on several
+ *    streams at once. packsell_set_spmv_variant and packsell_tune_spmv change
+ *    it and must not overlap other calls on the same matrix; kernels that
+ *    report through the matrix's device status word share that word.
  */
 #ifndef PACKSELL_H
 #define PACKSELL_H
