@@ -204,6 +204,51 @@ def test_pipelined_variant_short_rows_only():
         B, dev(I.uniform(B.m, seed=2)), reps=2)
 
 
+def test_spmv_column_range_limit():
+    """m = 2^31 - 1 columns (the format's limit): deltas above 2^30 need the
+    31-bit dummy, one row ends at column m - 1. x (8 GB) lives only on the
+    device, filled from a formula; the oracle twin runs on the same matrix
+    with its used columns renumbered 0.., which keeps every value, order and
+    x value, so each row's fused multiply-add chain is the same."""
+    need_gpu()
+    packsell = P()
+    m = 2 ** 31 - 1
+    rng = np.random.default_rng(31)
+    rows = []
+    for i in range(64):
+        L = int(rng.integers(0, 9))
+        cols = np.sort(rng.choice(m - 1, size=L, replace=False)) if L else np.zeros(0, np.int64)
+        if i % 7 == 0:
+            cols = np.unique(np.append(cols, m - 1))
+        if i % 5 == 0:
+            cols = np.unique(np.append(cols, [0, 2 ** 30 + i]))
+        rows.append(cols.astype(np.int64))
+    rowptr = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int64)
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.uniform(-1, 1, col.size).astype(np.float32)
+    csr = I.CSR(n=64, m=m, rowptr=rowptr, col=col, val=val)
+    # x_c = ((c mod 1000) - 500) * 2^-9: exact in float32 on both sides (a
+    # division by 500 is not: torch divides by a scalar through its reciprocal)
+    xf = lambda c: ((c % 1000) - 500).astype(np.float32) * np.float32(2.0 ** -9)
+    for fmt, D in (("fp16", 15), ("e8my", 11)):
+        A = encode_gpu(csr, fmt=fmt, D=D)
+        assert A.n_dummies > 0
+        xd = torch.empty(m, dtype=torch.float32, device="cuda")
+        step = 1 << 28
+        for a in range(0, m, step):
+            c = torch.arange(a, min(m, a + step), dtype=torch.int64, device="cuda")
+            xd[a:a + c.numel()] = ((c % 1000) - 500).to(torch.float32) * (2.0 ** -9)
+        used, inv = np.unique(col, return_inverse=True)
+        xu = xd[torch.from_numpy(used).cuda()].cpu().numpy()
+        assert np.array_equal(xu.view(np.uint32), xf(used.astype(np.int64)).view(np.uint32))
+        y = packsell.packsell_spmv(A, xd).cpu().numpy()
+        del xd
+        small = I.CSR(n=64, m=used.size, rowptr=rowptr, col=inv.astype(np.int32), val=val)
+        _, deq = O.quantize(val, FMT[fmt], D)
+        twin = O.csr_spmv_fma_f32(small, deq.astype(np.float32), xf(used.astype(np.int64)))
+        assert np.array_equal(y.view(np.uint32), twin.view(np.uint32))
+
+
 def test_tune_spmv_picks_a_variant():
     need_gpu()
     packsell = P()
