@@ -6,7 +6,8 @@
 //
 // SpMV variant 11. At encode time the rows are cut into work items: tiles of
 // consecutive rows of at most CL words each, holding at most CT words and CR
-// rows, and single rows of more than CL words. A warp takes items in turn:
+// rows, and single rows of more than CL words, listed first, longest first.
+// Warp w takes items w, w + W, ... (W warps in the grid):
 //  * tile: the warp copies the tile's words (one contiguous run) into shared
 //    memory with coalesced loads; then lane l sums rows l, l + 32 of the
 //    tile from shared memory, each in stored order with fused multiply-adds,
@@ -63,6 +64,8 @@ __global__ void __launch_bounds__(CW * 32)
     __shared__ __align__(16) float s_x[CW][CT];  // long rows: gathered x
     __shared__ int s_ro[CW][CR + 1];  // tile row offsets (relative)
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    // warp w takes items w, w + W, ...: the plan lists the long rows first,
+    // longest first, so they are dealt one per warp before the short tiles
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int it = gw; it < nitems; it += nwarps) {
@@ -223,6 +226,14 @@ packsell_status plan_csr(Matrix &A, cudaStream_t s) {
         }
     }
     if ((int)A.n > r0) items.push_back(make_int2(r0, (int)A.n));
+    // long rows first, longest first: they set the kernel's critical path,
+    // and taken early from the queue they overlap the many short tiles
+    auto is_long = [&](const int2 &a) { return a.y - a.x == 1 && off[a.y] - off[a.x] > CL; };
+    std::stable_partition(items.begin(), items.end(), is_long);
+    const size_t nlong = (size_t)std::count_if(items.begin(), items.end(), is_long);
+    std::stable_sort(items.begin(), items.begin() + nlong, [&](const int2 &a, const int2 &b) {
+        return off[a.y] - off[a.x] > off[b.y] - off[b.x];
+    });
     if (items.size() >= (size_t)INT32_MAX) return fail(PACKSELL_ERR_RANGE, "plan_csr: too many items");
     PS_CUDA(cudaMalloc(&A.csr_items, sizeof(int2) * items.size()));
     PS_CUDA(cudaMemcpyAsync(A.csr_items, items.data(), sizeof(int2) * items.size(),
