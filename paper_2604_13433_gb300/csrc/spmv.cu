@@ -723,9 +723,8 @@ __global__ void __launch_bounds__(TPB)
 constexpr int SPF = 8;
 
 template <int KV, bool VEC>
-__device__ __forceinline__ void spmm_gather(const float *__restrict__ xr, int qa, int step, int k,
-                                            float v, float4 (&acc)[KV]) {
-    float4 xv[KV];
+__device__ __forceinline__ void spmm_load(const float *__restrict__ xr, int qa, int step, int k,
+                                          float4 (&xv)[KV]) {
 #pragma unroll
     for (int h = 0; h < KV; ++h) {
         const int q = qa + step * h;
@@ -739,6 +738,10 @@ __device__ __forceinline__ void spmm_gather(const float *__restrict__ xr, int qa
             xv[h].w = (q + 3 < k) ? __ldg(xr + step * h + 3) : 0.f;
         }
     }
+}
+
+template <int KV>
+__device__ __forceinline__ void spmm_fma(float v, const float4 (&xv)[KV], float4 (&acc)[KV]) {
 #pragma unroll
     for (int h = 0; h < KV; ++h) {
         acc[h].x = fmaf(v, xv[h].x, acc[h].x);
@@ -746,6 +749,14 @@ __device__ __forceinline__ void spmm_gather(const float *__restrict__ xr, int qa
         acc[h].z = fmaf(v, xv[h].z, acc[h].z);
         acc[h].w = fmaf(v, xv[h].w, acc[h].w);
     }
+}
+
+template <int KV, bool VEC>
+__device__ __forceinline__ void spmm_gather(const float *__restrict__ xr, int qa, int step, int k,
+                                            float v, float4 (&acc)[KV]) {
+    float4 xv[KV];
+    spmm_load<KV, VEC>(xr, qa, step, k, xv);
+    spmm_fma<KV>(v, xv, acc);
 }
 
 template <int KV, bool VEC>
@@ -765,7 +776,7 @@ __device__ __forceinline__ void spmm_store(float *__restrict__ yr, int qa, int s
     }
 }
 
-template <int FMT, int G, int KV, bool VEC, bool C32>
+template <int FMT, int G, int KV, bool VEC, bool C32, int GB = 1>
 __global__ void __launch_bounds__(TPB)
     k_spmm_packed(int n, int Cr, int sigma, long long k_left, const int64_t *__restrict__ offset,
                   const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
@@ -794,13 +805,38 @@ __global__ void __launch_bounds__(TPB)
 #pragma unroll
             for (int u = 0; u < SPF; ++u)
                 wd[u] = (u < wr) ? ldg_stream(pp + (C32 ? (j0 + u) * 32 : (int64_t)(j0 + u) * C)) : 0u;
+            if (GB == 1) {
 #pragma unroll
-            for (int u = 0; u < SPF; ++u) {
-                const bool f = (wd[u] & 1u) != 0u;
-                c += (int)((wd[u] >> 1) & (f ? dc.dmask : 0x7fffffffu));
-                if (f)
-                    spmm_gather<KV, VEC>(X + (int64_t)c * ldx + qa, qa, step, k,
-                                         word_value<FMT>(wd[u], dc), acc);
+                for (int u = 0; u < SPF; ++u) {
+                    const bool f = (wd[u] & 1u) != 0u;
+                    c += (int)((wd[u] >> 1) & (f ? dc.dmask : 0x7fffffffu));
+                    if (f)
+                        spmm_gather<KV, VEC>(X + (int64_t)c * ldx + qa, qa, step, k,
+                                             word_value<FMT>(wd[u], dc), acc);
+                }
+            } else {
+                // two phases: the columns of the round first, then the X
+                // gathers of GB words at a time before their multiply-adds
+                // (long rows: one gather latency per GB words, not per word)
+                int cc[SPF];
+#pragma unroll
+                for (int u = 0; u < SPF; ++u) {
+                    const bool f = (wd[u] & 1u) != 0u;
+                    c += (int)((wd[u] >> 1) & (f ? dc.dmask : 0x7fffffffu));
+                    cc[u] = c;
+                }
+#pragma unroll
+                for (int g0 = 0; g0 < SPF; g0 += GB) {
+                    float4 xv[GB][KV];
+#pragma unroll
+                    for (int u = 0; u < GB; ++u) {
+                        if (wd[g0 + u] & 1u)
+                            spmm_load<KV, VEC>(X + (int64_t)cc[g0 + u] * ldx + qa, qa, step, k, xv[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < GB; ++u)
+                        if (wd[g0 + u] & 1u) spmm_fma<KV>(word_value<FMT>(wd[g0 + u], dc), xv[u], acc);
+                }
             }
             if (wd[SPF - 1] == 0u) break;  // the row has ended
         }
@@ -1071,6 +1107,17 @@ packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaS
     return PACKSELL_OK;
 }
 
+template <int FMT, int G, int KV, bool VEC>
+void launch_spmm_packed(const Matrix &A, const void *perm, int pb, int k, const float *X,
+                        int64_t ldx, float *Y, int64_t ldy, unsigned g, cudaStream_t s) {
+    constexpr int GB = KV == 1 ? 8 : 4;  // gathers in flight per lane in the two-phase form
+    auto kern = A.p.C != 32 ? k_spmm_packed<FMT, G, KV, VEC, false>
+                : A.max_width > 32 ? k_spmm_packed<FMT, G, KV, VEC, true, GB>  // long rows
+                                   : k_spmm_packed<FMT, G, KV, VEC, true>;
+    kern<<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb,
+                           make_decode(A), k, X, ldx, Y, ldy);
+}
+
 template <int G, int KV, bool VEC>
 void launch_spmm(const Matrix &A, const void *perm, int pb, int k, const float *X, int64_t ldx,
                  float *Y, int64_t ldy, cudaStream_t s) {
@@ -1078,16 +1125,10 @@ void launch_spmm(const Matrix &A, const void *perm, int pb, int k, const float *
     const unsigned g = (unsigned)((threads + TPB - 1) / TPB);
     switch (A.p.format) {
         case PACKSELL_FMT_FP16:
-            (A.p.C == 32 ? k_spmm_packed<PACKSELL_FMT_FP16, G, KV, VEC, true>
-                         : k_spmm_packed<PACKSELL_FMT_FP16, G, KV, VEC, false>)<<<g, TPB, 0, s>>>(
-                (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A),
-                k, X, ldx, Y, ldy);
+            launch_spmm_packed<PACKSELL_FMT_FP16, G, KV, VEC>(A, perm, pb, k, X, ldx, Y, ldy, g, s);
             break;
         case PACKSELL_FMT_E8MY:
-            (A.p.C == 32 ? k_spmm_packed<PACKSELL_FMT_E8MY, G, KV, VEC, true>
-                         : k_spmm_packed<PACKSELL_FMT_E8MY, G, KV, VEC, false>)<<<g, TPB, 0, s>>>(
-                (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A),
-                k, X, ldx, Y, ldy);
+            launch_spmm_packed<PACKSELL_FMT_E8MY, G, KV, VEC>(A, perm, pb, k, X, ldx, Y, ldy, g, s);
             break;
         default:
             k_spmm_sell<G, KV, VEC><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,

@@ -23,6 +23,7 @@ CASES = [
     (2000, 3000, 0.005, 64, 512, "fp16", 15, 0.1, True),
     (5000, 5000, 0.002, 32, 4096, "e8my", 9, 0.02, True),
     (3000, 300, 0.02, 1024, 3000, "e8my", 5, 0.0, True),
+    (70000, 70000, 0.0002, 32, 65536, "fp16", 15, 0.05, True),  # the largest sigma
 ]
 
 

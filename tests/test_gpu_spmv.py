@@ -316,6 +316,24 @@ def test_spmm(fmt, D, k):
     assert np.abs(Y - ref).max() <= REL_TOL * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("fmt,D,k", [("fp16", 15, 3), ("e8my", 11, 8), ("fp16", 15, 64),
+                                     ("fp16", 15, 100), ("e8my", 7, 4)])
+def test_spmm_long_rows(fmt, D, k):
+    """Rows of up to 4,096 words (slices wider than 32 words take the
+    two-phase SpMM: columns of a round first, then gathers in batches)."""
+    need_gpu()
+    packsell = P()
+    csr = I.zipf_irregular(20000, seed=k)
+    A = encode_gpu(csr, fmt=fmt, D=D)
+    assert A.max_width > 32
+    X = np.random.default_rng(k).uniform(-1, 1, (csr.m, k)).astype(np.float32)
+    Y = packsell.packsell_spmm(A, dev(X)).cpu().numpy()
+    deq = O.encode(csr, D=D, fmt=FMT[fmt]).deq.astype(np.float32)
+    for r in sorted({0, k // 2, k - 1}):
+        twin = O.csr_spmv_fma_f32(csr, deq, np.ascontiguousarray(X[:, r]))
+        assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32)), f"column {r}"
+
+
 @pytest.mark.parametrize("fmt,C,sigma,explicit,k", [("fp16", 32, 256, True, 16),
                                                      ("e8my", 8, 1, False, 12),
                                                      ("fp16", 1, 1, False, 32),
