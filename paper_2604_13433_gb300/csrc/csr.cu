@@ -54,7 +54,7 @@ __device__ __forceinline__ int csr_left(int row, int sigma, int sig_shift, long 
 }
 
 template <int FMT, bool PERM>
-__global__ void __launch_bounds__(CW * 32)
+__global__ void __launch_bounds__(CW * 32, 4)
     k_spmv_csr(int sigma, int sig_shift, long long k_left, const int64_t *__restrict__ offset,
                const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
                Decode dc, const int2 *__restrict__ items, int nitems,
@@ -77,16 +77,22 @@ __global__ void __launch_bounds__(CW * 32)
             // ---- one long row, CT words per chunk ----
             uint32_t carry = (uint32_t)csr_left(r0, sigma, sig_shift, k_left);
             float t = 0.f;
+            // the chunk's words are loaded one chunk ahead: the loads of
+            // chunk k + 1 are in flight while chunk k is scanned, gathered
+            // and summed (a warp issues in order: loads placed right before
+            // their use would wait out each round trip)
+            uint32_t wd[CT / 32];
+#pragma unroll
+            for (int u = 0; u < CT / 32; ++u)
+                wd[u] = 32 * u + lane < min(CT, nwd) ? ldg_stream(pack + base + 32 * u + lane) : 0u;
             for (int k0 = 0; k0 < nwd; k0 += CT) {
                 const int cnt = min(CT, nwd - k0);
-                // all loads of the chunk first, then the scan, then all
-                // gathers, then the stores (a warp issues in order: a store
-                // right after its load would wait out each round trip)
-                uint32_t wd[CT / 32], c[CT / 32];
+                const int cn = min(CT, nwd - k0 - CT);  // next chunk (<= 0: none)
+                uint32_t nx[CT / 32], c[CT / 32];
 #pragma unroll
                 for (int u = 0; u < CT / 32; ++u) {
                     const int k = 32 * u + lane;
-                    wd[u] = k < cnt ? ldg_stream(pack + base + k0 + k) : 0u;
+                    nx[u] = k < cn ? ldg_stream(pack + base + k0 + CT + k) : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < CT / 32; ++u) {
@@ -130,6 +136,8 @@ __global__ void __launch_bounds__(CW * 32)
                     }
                 }
                 __syncwarp();
+#pragma unroll
+                for (int u = 0; u < CT / 32; ++u) wd[u] = nx[u];
             }
             if (lane == 0) csr_store<FMT, PERM>(r0, sigma, sig_shift, perm, perm_bytes, t, y);
             continue;
