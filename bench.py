@@ -598,6 +598,22 @@ def run_ours(args):
                              "dummies": A.n_dummies, "footprint_vs_sell": None,
                              "backward_error": backward_error(torch, ps, A, y, y64, normA, normx)}
             del A
+        # the paper's FP16 SpMV configuration: x and y in binary16
+        if args.formats == "all":
+            xh = x.half()
+            yh = torch.empty(csr.n, dtype=torch.float16, device=dev)
+            ms, _ = time_launches(torch, lambda: ps.packsell_spmv_x16(A16, xh, yh), K, W)
+            nbh = 4 * A16.n_words + 8 * (A16.n_slices + 1) + 2 * csr.m + 2 * csr.n
+            A64h = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f64",
+                                      explicit_perm=False)
+            y64h = ps.packsell_spmv_f64(A64h, xh.double())
+            del A64h
+            formats["fp16_x16y16"] = {
+                "GBps": nbh / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6, "us": ms * 1e3,
+                "bytes": nbh, "words": A16.n_words, "dummies": A16.n_dummies,
+                "footprint_vs_sell": None,
+                "backward_error": backward_error(torch, ps, A16, yh.float(), y64h, normA,
+                                                 float(xh.abs().max()))}
         # end to end through the public API: pinned host x in, host y out
         xp = torch.from_numpy(x_h).pin_memory()
         yp = torch.empty(csr.n, dtype=torch.float32).pin_memory()

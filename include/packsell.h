@@ -169,6 +169,16 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
                               void *stream);
 
+/* y = A x with binary16 vectors: the paper's FP16 SpMV configuration (§5.1.1,
+ * x and y in FP16). x: uint16 [m], binary16 bit patterns, widened exactly to
+ * FP32; each row is summed with FP32 fused multiply-adds in stored order (the
+ * chain of packsell_spmv with x widened); y: uint16 [n], the sums rounded to
+ * binary16 (nearest, ties to even), in the original row order (storage order
+ * with explicit_perm). PackSELL matrices with C = 32. Errors: INVALID_ARG.
+ * No allocation. */
+packsell_status packsell_spmv_x16(const packsell_matrix *A, const uint16_t *x, uint16_t *y,
+                                  void *stream);
+
 /* y = A x in double for a SELL_F64 matrix (the FP64 outer operator). */
 packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
                                   void *stream);

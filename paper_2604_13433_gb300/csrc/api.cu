@@ -378,6 +378,14 @@ packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *s
     return inv_diag_impl(*M(A), out, as_stream(stream));
 }
 
+packsell_status packsell_spmv_x16(const packsell_matrix *A, const uint16_t *x, uint16_t *y,
+                                  void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_x16: NULL argument");
+    return spmv_x16_impl(*M(A), x, y, as_stream(stream));
+}
+
 packsell_status packsell_storage_rows(const packsell_matrix *A, int32_t *rows, void *stream) {
     clear_error();
     if (!A || (M(A)->n > 0 && !rows))

@@ -78,6 +78,9 @@ packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_
 packsell_status plan_stage(Matrix &A, cudaStream_t s);
 void stage_free(Matrix &A);
 
+// half_io.cu
+packsell_status spmv_x16_impl(const Matrix &A, const uint16_t *x, uint16_t *y, cudaStream_t s);
+
 // csr.cu
 packsell_status plan_csr(Matrix &A, cudaStream_t s);
 void csr_plan_free(Matrix &A);

@@ -96,6 +96,7 @@ SIGNATURES = {
     "packsell_pattern_outer_f64": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
     "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
     "packsell_storage_rows": (ctypes.c_int, [_P, _P, _P]),
+    "packsell_spmv_x16": (ctypes.c_int, [_P, _P, _P, _P]),
     "packsell_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "packsell_batch_spmv": (ctypes.c_int, [_P, _P]),
     "packsell_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -301,6 +302,17 @@ def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
     _check(lib().packsell_inv_diag(A.handle, _dev(out, torch.float64, "out", A.n),
                                    _stream(stream)))
     return out
+
+
+def packsell_spmv_x16(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """y = A x with float16 x and y (FP32 accumulation in stored order, y
+    rounded to binary16)."""
+    if y is None:
+        y = torch.empty(A.n, dtype=torch.float16, device="cuda")
+    _check(lib().packsell_spmv_x16(A.handle, _dev(x, torch.float16, "x", A.m),
+                                   _dev(y, torch.float16, "y", A.n), _stream(stream)))
+    return y
 
 
 def packsell_storage_rows(A: PackSELLMatrix, out: torch.Tensor | None = None,

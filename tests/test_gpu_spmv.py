@@ -249,6 +249,26 @@ def test_spmv_column_range_limit():
         assert np.array_equal(y.view(np.uint32), twin.view(np.uint32))
 
 
+@pytest.mark.parametrize("fmt,D,explicit", [("fp16", 15, False), ("fp16", 15, True),
+                                             ("e8my", 11, False), ("e8my", 5, True)])
+def test_spmv_x16_paper_configuration(fmt, D, explicit):
+    """x and y in binary16 (the paper's FP16 SpMV, §5.1.1): y equals the FP32
+    twin on the widened x, rounded to binary16 (nearest even), bit for bit."""
+    need_gpu()
+    packsell = P()
+    for csr in (I.stencil27(20, seed=6), I.random_csr(900, 700, 0.01, seed=3, empty_rows=0.1,
+                                                     long_gaps=True)):
+        enc = O.encode(csr, D=D, fmt=FMT[fmt])
+        A = encode_gpu(csr, fmt=fmt, D=D, explicit_perm=explicit)
+        xh = np.random.default_rng(7).uniform(-2, 2, csr.m).astype(np.float16)
+        y = packsell.packsell_spmv_x16(A, dev(xh)).cpu().numpy()
+        twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), xh.astype(np.float32))
+        want = twin.astype(np.float16)
+        if explicit:
+            want = want[O.storage_rows(enc)]
+        assert np.array_equal(y.view(np.uint16), want.view(np.uint16))
+
+
 def test_tune_spmv_picks_a_variant():
     need_gpu()
     packsell = P()
