@@ -169,6 +169,17 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
                               void *stream);
 
+/* y = A x from and to host memory: enqueues on `stream` the copy of h_x
+ * (float [m], host; pinned memory lets the copy run asynchronously) into the
+ * caller's device buffer d_x, packsell_spmv(A, d_x, d_y), and the copy of
+ * d_y (float [n], device) into h_y (host). The caller owns all four buffers
+ * and must keep them until the stream reaches the end of the call; h_y is
+ * valid after the stream is synchronised. One cudaMemcpyAsync per copy; no
+ * allocation. Errors: INVALID_ARG on a NULL buffer, CUDA if a copy cannot be
+ * enqueued. */
+packsell_status packsell_spmv_host(const packsell_matrix *A, const float *h_x, float *h_y,
+                                   float *d_x, float *d_y, void *stream);
+
 /* y = A x with binary16 vectors: the paper's FP16 SpMV configuration (§5.1.1,
  * x and y in FP16). x: uint16 [m], binary16 bit patterns, widened exactly to
  * FP32; each row is summed with FP32 fused multiply-adds in stored order (the

@@ -378,6 +378,23 @@ packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *s
     return inv_diag_impl(*M(A), out, as_stream(stream));
 }
 
+packsell_status packsell_spmv_host(const packsell_matrix *A, const float *h_x, float *h_y,
+                                   float *d_x, float *d_y, void *stream) {
+    clear_error();
+    if (!A) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_host: NULL matrix");
+    const Matrix &m = *M(A);
+    if ((m.m > 0 && (!h_x || !d_x)) || (m.n > 0 && (!h_y || !d_y)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_host: NULL buffer");
+    cudaStream_t s = as_stream(stream);
+    if (m.m > 0)
+        PS_CUDA(cudaMemcpyAsync(d_x, h_x, sizeof(float) * (size_t)m.m, cudaMemcpyHostToDevice, s));
+    const packsell_status st = spmv_impl(m, d_x, d_y, s);
+    if (st != PACKSELL_OK) return st;
+    if (m.n > 0)
+        PS_CUDA(cudaMemcpyAsync(h_y, d_y, sizeof(float) * (size_t)m.n, cudaMemcpyDeviceToHost, s));
+    return PACKSELL_OK;
+}
+
 packsell_status packsell_spmv_x16(const packsell_matrix *A, const uint16_t *x, uint16_t *y,
                                   void *stream) {
     clear_error();

@@ -97,6 +97,7 @@ SIGNATURES = {
     "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
     "packsell_storage_rows": (ctypes.c_int, [_P, _P, _P]),
     "packsell_spmv_x16": (ctypes.c_int, [_P, _P, _P, _P]),
+    "packsell_spmv_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "packsell_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "packsell_batch_spmv": (ctypes.c_int, [_P, _P]),
     "packsell_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -302,6 +303,21 @@ def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
     _check(lib().packsell_inv_diag(A.handle, _dev(out, torch.float64, "out", A.n),
                                    _stream(stream)))
     return out
+
+
+def packsell_spmv_host(A: PackSELLMatrix, x_host: torch.Tensor, y_host: torch.Tensor,
+                       x_dev: torch.Tensor, y_dev: torch.Tensor, stream=None) -> torch.Tensor:
+    """y_host = A x_host through the device staging buffers x_dev, y_dev
+    (copy in, SpMV, copy out, all on `stream`; pinned host tensors make the
+    copies asynchronous). Returns y_host; valid once the stream is synced."""
+    for name, t, numel in (("x_host", x_host, A.m), ("y_host", y_host, A.n)):
+        if (not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32
+                or not t.is_contiguous() or t.numel() != numel):
+            raise TypeError(f"{name} must be a contiguous float32 host tensor of {numel}")
+    _check(lib().packsell_spmv_host(A.handle, x_host.data_ptr(), y_host.data_ptr(),
+                                    _dev(x_dev, torch.float32, "x_dev", A.m),
+                                    _dev(y_dev, torch.float32, "y_dev", A.n), _stream(stream)))
+    return y_host
 
 
 def packsell_spmv_x16(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,

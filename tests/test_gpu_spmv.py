@@ -269,6 +269,26 @@ def test_spmv_x16_paper_configuration(fmt, D, explicit):
         assert np.array_equal(y.view(np.uint16), want.view(np.uint16))
 
 
+def test_spmv_host_buffers():
+    """packsell_spmv_host: host x in, host y out through caller-owned device
+    buffers; equals packsell_spmv bit for bit; NULL buffers are refused."""
+    need_gpu()
+    packsell = P()
+    csr = I.stencil27(16, seed=9)
+    A = encode_gpu(csr, fmt="fp16")
+    xh = torch.from_numpy(I.uniform(csr.m, seed=10)).pin_memory()
+    yh = torch.empty(csr.n, dtype=torch.float32).pin_memory()
+    xd = torch.empty(csr.m, device="cuda")
+    yd = torch.empty(csr.n, device="cuda")
+    packsell.packsell_spmv_host(A, xh, yh, xd, yd)
+    torch.cuda.synchronize()
+    ref = packsell.packsell_spmv(A, xh.cuda()).cpu()
+    assert torch.equal(yh.view(torch.int32), ref.view(torch.int32))
+    with pytest.raises(packsell.PackSELLError):
+        packsell._check(packsell.lib().packsell_spmv_host(A.handle, None, yh.data_ptr(),
+                                                          xd.data_ptr(), yd.data_ptr(), None))
+
+
 def test_tune_spmv_picks_a_variant():
     need_gpu()
     packsell = P()
