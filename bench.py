@@ -377,18 +377,22 @@ def extended_section(ps, torch, dev, K, W):
         del X, Y
     out["stencil27_128_spmm"] = spmm
     del A
-    # batch of 256 irregular matrices, one launch
-    mats, xs, ys = [], [], []
-    for c in I.zipf_batch(256, seed=5):
-        mats.append(ps.packsell_encode_csr(c, fmt="fp16", D=15))
-        xs.append(torch.from_numpy(I.uniform(c.m, seed=c.n)).to(dev))
-        ys.append(torch.empty(c.n, device=dev))
-    B = ps.packsell_batch_create(mats, xs, ys)
-    ms, _ = time_launches(torch, B.spmv, K, W)
-    out["batch_256"] = {"matrices": 256, "rows": int(sum(m.n for m in mats)),
-                        "words": B.words, "items": B.items, "GBps": B.bytes / ms / 1e6,
-                        "us": ms * 1e3}
-    del B, mats, xs, ys
+    # batch of 256 irregular matrices, one launch; sigma = 256 (the paper's
+    # setting) and sigma = 65536, whose sort puts the power-law rows' long
+    # rows together in their own slices (far less padding)
+    batch = I.zipf_batch(256, seed=5)
+    for key, sigma in (("batch_256", 256), ("batch_256_sigma65536", 65536)):
+        mats, xs, ys = [], [], []
+        for c in batch:
+            mats.append(ps.packsell_encode_csr(c, fmt="fp16", D=15, sigma=sigma))
+            xs.append(torch.from_numpy(I.uniform(c.m, seed=c.n)).to(dev))
+            ys.append(torch.empty(c.n, device=dev))
+        B = ps.packsell_batch_create(mats, xs, ys)
+        ms, _ = time_launches(torch, B.spmv, K, W)
+        out[key] = {"matrices": 256, "sigma": sigma, "rows": int(sum(m.n for m in mats)),
+                    "words": B.words, "items": B.items, "GBps": B.bytes / ms / 1e6,
+                    "us": ms * 1e3}
+        del B, mats, xs, ys
     out["diff_solve_512"] = diff_solve_section(ps, torch, dev)
     return out
 
@@ -418,7 +422,13 @@ def diff_solve_section(ps, torch, dev):
         return v.index_add(0, P["b"], tb)
 
     res = {"systems": 512, "n": int(n), "nnz": int(nnz)}
-    for name, m_in, fmt, D in (("fp64_pcg", 0, "fp16", 15), ("iocg_e8m11", 20, "e8my", 11)):
+    configs = (("fp64_pcg", 0, "fp16", 15), ("iocg_e8m11", 20, "e8my", 11))
+    for _, m_in, fmt, D in configs:  # untimed: first use of every kernel and allocation
+        x = ag.solve(rp, cl, assemble(theta), b, m_in=m_in, fmt=fmt, D=D, rtol=1e-10,
+                     max_iters=20000)
+        ((x - xt) ** 2).sum().backward()
+    torch.cuda.synchronize()
+    for name, m_in, fmt, D in configs:
         theta.grad = None
         b.grad = None
         torch.cuda.synchronize()
