@@ -80,6 +80,12 @@ def lib():
         L.orc_encode_plan.argtypes = [i64, i64, P, P, i32, i32, i32, i64, P, P, P, P]
         L.orc_encode_fill.argtypes = [i64, P, P, P, i32, i32, i32, i64, P, P, P]
         L.orc_decode.argtypes = [i64, i32, i32, i32, i64, P, P, P, P, P, P, P]
+        L.orc_e4m3_bits.argtypes = [ctypes.c_double, P]
+        L.orc_e4m3_value.argtypes = [ctypes.c_uint8]
+        L.orc_e4m3_value.restype = ctypes.c_double
+        L.orc_encode_plan_w.argtypes = [i64, i64, P, P, i32, i32, i32, i32, i64, P, P, P, P]
+        L.orc_encode16_fill.argtypes = [i64, P, P, P, i32, i32, i64, P, P, P]
+        L.orc_decode16.argtypes = [i64, i32, i32, i64, P, P, P, P, P, P, P]
         L.orc_csr_spmv_f64.argtypes = [i64, P, P, P, P, P]
         L.orc_csr_spmv_fma_f32.argtypes = [i64, P, P, P, P, P]
         L.orc_csr_spmv_t_f64.argtypes = [i64, i64, P, P, P, P, P]
@@ -225,6 +231,90 @@ def encode(csr, C: int = 32, sigma: int = 256, D: int = 15, fmt: int = FMT_FP16,
     return Encoded(n=n, m=m, C=C, sigma=sigma, D=D, fmt=fmt, k_left=int(stats[0]),
                    words=words, perm=perm, offset=offset, pack=pack, field=field, deq=deq,
                    n_words=int(stats[1]), n_dummies=int(stats[2]), n_pad=int(stats[3]))
+
+
+def e4m3_bits(v: float) -> int:
+    """FP8 E4M3 code of v (round to nearest even); OracleError on NaN/inf or
+    a value that rounds past 448."""
+    out = ctypes.c_uint8()
+    st = lib().orc_e4m3_bits(float(v), ctypes.byref(out))
+    if st:
+        raise OracleError(st, "e4m3_bits")
+    return int(out.value)
+
+
+def e4m3_value(code: int) -> float:
+    return float(lib().orc_e4m3_value(code))
+
+
+def quantize_e4m3(val: np.ndarray):
+    """E4M3 codes (uint8) and their values (float64) of every entry."""
+    v = np.asarray(val, np.float64).ravel()
+    codes = np.array([e4m3_bits(t) for t in v], np.uint8) if v.size else np.zeros(0, np.uint8)
+    table = np.array([e4m3_value(c) for c in range(256)], np.float64)
+    return codes, table[codes]
+
+
+@dataclass
+class Encoded16:
+    """16-bit PackSELL words (W = 16, D = 7, E4M3 values)."""
+    n: int
+    m: int
+    C: int
+    sigma: int
+    k_left: int
+    words: np.ndarray  # int64 [n]
+    perm: np.ndarray  # int32 [n]
+    offset: np.ndarray  # int64 [S + 1]
+    pack: np.ndarray  # uint16 [N_w]
+    codes: np.ndarray  # uint8 [nnz], E4M3 codes in CSR order
+    deq: np.ndarray  # float64 [nnz]
+    n_words: int
+    n_dummies: int
+    n_pad: int
+
+    @property
+    def D(self) -> int:
+        return 7
+
+
+def encode16(csr, C: int = 32, sigma: int = 256, k_left: int = -1) -> Encoded16:
+    """PackSELL with 16-bit words: D = 7 delta bits, E4M3 values in the upper
+    byte, 15-bit dummy deltas (several dummies for a gap of 2^15 or more)."""
+    L = lib()
+    rowptr, col = _c(csr.rowptr, np.int64), _c(csr.col, np.int32)
+    codes, deq = quantize_e4m3(csr.val)
+    n, m = csr.n, csr.m
+    S = (n + C - 1) // C
+    words = np.empty(n, np.int64)
+    perm = np.empty(n, np.int32)
+    offset = np.empty(S + 1, np.int64)
+    stats = np.empty(4, np.int64)
+    st = L.orc_encode_plan_w(n, m, _p(rowptr), _p(col), C, sigma, 7, 16, k_left, _p(words),
+                             _p(perm), _p(offset), _p(stats))
+    if st:
+        raise OracleError(st, "encode_plan_w")
+    pack = np.empty(int(stats[1]), np.uint16)
+    codes_c = _c(codes, np.uint8)
+    st = L.orc_encode16_fill(n, _p(rowptr), _p(col), _p(codes_c), C, sigma, int(stats[0]),
+                             _p(perm), _p(offset), _p(pack))
+    if st:
+        raise OracleError(st, "encode16_fill")
+    return Encoded16(n=n, m=m, C=C, sigma=sigma, k_left=int(stats[0]), words=words, perm=perm,
+                     offset=offset, pack=pack, codes=codes, deq=deq, n_words=int(stats[1]),
+                     n_dummies=int(stats[2]), n_pad=int(stats[3]))
+
+
+def decode16(enc: Encoded16, rowptr: np.ndarray):
+    """(col, codes, counts) of the 16-bit words, as decode()."""
+    rowptr = _c(rowptr, np.int64)
+    nnz = int(rowptr[-1])
+    col = np.full(nnz, -1, np.int32)
+    codes = np.zeros(nnz, np.uint8)
+    counts = np.zeros(enc.n, np.int64)
+    lib().orc_decode16(enc.n, enc.C, enc.sigma, enc.k_left, _p(enc.perm), _p(enc.offset),
+                       _p(enc.pack), _p(rowptr), _p(col), _p(codes), _p(counts))
+    return col, codes, counts
 
 
 def check_csr(csr) -> int:

@@ -138,6 +138,48 @@ double orc_field_value(uint32_t field, int fmt)
 /*   flag 1: bits 1..D hold the delta, bits D+1..31 the value.                */
 /*   flag 0: bits 1..31 hold the delta; there is no value.                    */
 /* ------------------------------------------------------------------------ */
+/* FP8 E4M3 (the OCP 8-bit floating-point format): 1 sign bit, 4 exponent bits
+ * (bias 7), 3 fraction bits; subnormals have spacing 2^-9; the code S.1111.111
+ * is NaN and there are no infinities, so the largest finite value is
+ * 1.75 * 2^8 = 448. Round to nearest, ties to even, from the definition:
+ * scale the magnitude to an integer grid of the binade (exact in double) and
+ * round it with nearbyint (the default rounding mode is to nearest even).
+ * Returns ORC_OK, ORC_ERR_NONFINITE (input inf/nan) or ORC_ERR_RANGE (rounds
+ * past 448). This is the value format of the 16-bit words (W = 16, D = 7,
+ * V = 8), one of the other word sizes the paper names (§4.2.1). */
+int orc_e4m3_bits(double v, uint8_t *out)
+{
+    if (!isfinite(v)) return ORC_ERR_NONFINITE;
+    uint8_t s = signbit(v) ? 0x80 : 0x00;
+    double a = fabs(v);
+    if (a == 0.0) { *out = s; return ORC_OK; }
+    if (a < ldexp(1.0, -6)) {                  /* subnormal range: unit 2^-9 */
+        double q = nearbyint(a / ldexp(1.0, -9));  /* 0 .. 8 */
+        *out = (uint8_t)(s | (uint8_t)q);       /* q = 8 is the smallest normal, 0x08 */
+        return ORC_OK;
+    }
+    int e;
+    frexp(a, &e);                               /* a = f * 2^e, f in [0.5, 1) */
+    e -= 1;                                     /* a in [2^e, 2^(e+1)) */
+    double q = nearbyint(a / ldexp(1.0, e - 3)); /* 8 .. 16 */
+    if (q == 16.0) { q = 8.0; e += 1; }
+    int E = e + 7;
+    int M = (int)q - 8;
+    if (E > 15 || (E == 15 && M == 7)) return ORC_ERR_RANGE;
+    *out = (uint8_t)(s | (uint8_t)(E << 3) | (uint8_t)M);
+    return ORC_OK;
+}
+
+/* The value of an E4M3 code (NaN for S.1111.111). */
+double orc_e4m3_value(uint8_t c)
+{
+    int E = (c >> 3) & 15, M = c & 7;
+    double sgn = (c & 0x80) ? -1.0 : 1.0;
+    if (E == 15 && M == 7) return NAN;
+    if (E == 0) return sgn * ldexp((double)M, -9);
+    return sgn * ldexp(1.0 + M / 8.0, E - 7);
+}
+
 uint32_t orc_word_value(uint32_t field, uint32_t delta) { return field | (delta << 1) | 1u; }
 uint32_t orc_word_dummy(uint32_t delta) { return delta << 1; }
 
@@ -190,22 +232,37 @@ int orc_check_csr(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *co
     return ORC_OK;
 }
 
-/* Stored words of original row i: its nonzeros plus one dummy before every
- * nonzero whose delta (Eq. 2, first delta taken from the left offset) does not
- * fit in D bits. Returns -1 if a delta would be negative. */
-int64_t orc_row_words(int64_t i, const int64_t *rowptr, const int32_t *col, int64_t sigma,
-                      int64_t k_left, int D, int64_t *dummies)
+/* Stored words of original row i with W-bit words: its nonzeros plus the
+ * dummies before every nonzero whose delta (Eq. 2, first delta taken from the
+ * left offset) does not fit in D bits. A dummy's delta field has W - 1 bits
+ * (§4.2.1): while the remaining delta is 2^D or more, a dummy takes
+ * min(delta, 2^(W-1) - 1) of it. With W = 32 (columns below 2^31) that is one
+ * dummy carrying the whole delta, the real word then carrying 0 (§4.3).
+ * Returns -1 if a delta would be negative. */
+int64_t orc_row_words_w(int64_t i, const int64_t *rowptr, const int32_t *col, int64_t sigma,
+                        int64_t k_left, int D, int W, int64_t *dummies)
 {
     int64_t prev = orc_left_offset(i, sigma, k_left), words = 0;
+    const int64_t dmax = ((int64_t)1 << (W - 1)) - 1;
     *dummies = 0;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
         int64_t d = (int64_t)col[p] - prev;
         if (d < 0) return -1;
-        if (d >= ((int64_t)1 << D)) { ++words; ++*dummies; }
+        while (d >= ((int64_t)1 << D)) {
+            d -= (d < dmax ? d : dmax);
+            ++words;
+            ++*dummies;
+        }
         ++words;
         prev = col[p];
     }
     return words;
+}
+
+int64_t orc_row_words(int64_t i, const int64_t *rowptr, const int32_t *col, int64_t sigma,
+                      int64_t k_left, int D, int64_t *dummies)
+{
+    return orc_row_words_w(i, rowptr, col, sigma, k_left, D, 32, dummies);
 }
 
 typedef struct { int64_t key; int64_t idx; } orc_kv;
@@ -223,11 +280,12 @@ static int orc_kv_cmp(const void *a, const void *b)
  *   offset[S+1]      S = ceil(n / C) slices, offset[k+1] - offset[k] = C * w_k
  *   stats[4]         k_left used, total words, dummies, padding words
  * k_left_in < 0 computes the lower bandwidth. */
-int orc_encode_plan(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col,
-                    int32_t C, int32_t sigma, int32_t D, int64_t k_left_in,
-                    int64_t *words, int32_t *perm, int64_t *offset, int64_t *stats)
+int orc_encode_plan_w(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col,
+                      int32_t C, int32_t sigma, int32_t D, int32_t W, int64_t k_left_in,
+                      int64_t *words, int32_t *perm, int64_t *offset, int64_t *stats)
 {
-    if (n < 0 || m < 0 || m >= ((int64_t)1 << 31) || C < 1 || sigma < 1 || D < 1 || D > 22)
+    if (n < 0 || m < 0 || m >= ((int64_t)1 << 31) || C < 1 || sigma < 1 || D < 1 ||
+        D > W - 2 || (W != 16 && W != 32))
         return ORC_ERR_ARG;
     int st = orc_check_csr(n, m, rowptr, col);
     if (st) return st;
@@ -235,7 +293,7 @@ int orc_encode_plan(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *
     int64_t dummies = 0, nnz = rowptr[n];
     for (int64_t i = 0; i < n; ++i) {
         int64_t dm;
-        words[i] = orc_row_words(i, rowptr, col, sigma, k_left, D, &dm);
+        words[i] = orc_row_words_w(i, rowptr, col, sigma, k_left, D, W, &dm);
         if (words[i] < 0) return ORC_ERR_ARG; /* k_left smaller than the bandwidth */
         dummies += dm;
     }
@@ -263,6 +321,15 @@ int orc_encode_plan(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *
     stats[2] = dummies;
     stats[3] = offset[S] - nnz - dummies; /* padding, phantom rows included */
     return ORC_OK;
+}
+
+int orc_encode_plan(int64_t n, int64_t m, const int64_t *rowptr, const int32_t *col,
+                    int32_t C, int32_t sigma, int32_t D, int64_t k_left_in,
+                    int64_t *words, int32_t *perm, int64_t *offset, int64_t *stats)
+{
+    if (D > 22) return ORC_ERR_ARG;
+    return orc_encode_plan_w(n, m, rowptr, col, C, sigma, D, 32, k_left_in, words, perm, offset,
+                             stats);
 }
 
 /* Fill pack[offset[S]] given the plan. field[nnz] holds each nonzero's value
@@ -312,6 +379,64 @@ int orc_decode(int64_t n, int32_t C, int32_t sigma, int32_t D, int64_t k_left,
                 if (q < rowptr[orig + 1]) { col_out[q] = (int32_t)c; field_out[q] = fld; }
                 ++q;
                 ++cnt;
+            }
+        }
+        counts[orig] = cnt;
+    }
+    return ORC_OK;
+}
+
+/* 16-bit words (W = 16, D = 7): a word with a value is (code << 8) | (d << 1)
+ * | 1 with the E4M3 code in bits 8..15; a dummy is (q << 1), q < 2^15; padding
+ * is 0. Same slice layout and plan as the 32-bit words (orc_encode_plan_w with
+ * W = 16). codes[nnz]: each nonzero's E4M3 code in CSR order. */
+int orc_encode16_fill(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *codes,
+                      int32_t C, int32_t sigma, int64_t k_left, const int32_t *perm,
+                      const int64_t *offset, uint16_t *pack)
+{
+    const int D = 7;
+    const int64_t dmax = 32767;
+    int64_t S = (n + C - 1) / C;
+    memset(pack, 0, sizeof(uint16_t) * (size_t)offset[S]);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t prev = orc_left_offset(i, sigma, k_left), j = 0;
+        for (int64_t p = rowptr[orig]; p < rowptr[orig + 1]; ++p) {
+            int64_t d = (int64_t)col[p] - prev;
+            if (d < 0) return ORC_ERR_ARG;
+            while (d >= ((int64_t)1 << D)) {
+                int64_t q = d < dmax ? d : dmax;
+                pack[offset[k] + j * C + l] = (uint16_t)(q << 1);
+                ++j;
+                d -= q;
+            }
+            pack[offset[k] + j * C + l] = (uint16_t)(((uint32_t)codes[p] << 8) | ((uint32_t)d << 1) | 1u);
+            ++j;
+            prev = col[p];
+        }
+        if (offset[k] + j * C > offset[k + 1]) return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
+
+/* Decode 16-bit words back to CSR in original row order (as orc_decode). */
+int orc_decode16(int64_t n, int32_t C, int32_t sigma, int64_t k_left, const int32_t *perm,
+                 const int64_t *offset, const uint16_t *pack, const int64_t *rowptr,
+                 int32_t *col_out, uint8_t *code_out, int64_t *counts)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t w = (offset[k + 1] - offset[k]) / C;
+        int64_t c = orc_left_offset(i, sigma, k_left), q = rowptr[orig], cnt = 0;
+        for (int64_t j = 0; j < w; ++j) {
+            uint16_t word = pack[offset[k] + j * C + l];
+            if (word & 1u) {
+                c += (word >> 1) & 0x7Fu;
+                if (q < rowptr[orig + 1]) { col_out[q] = (int32_t)c; code_out[q] = (uint8_t)(word >> 8); }
+                ++q;
+                ++cnt;
+            } else {
+                c += (word >> 1) & 0x7FFFu;
             }
         }
         counts[orig] = cnt;
