@@ -169,7 +169,7 @@ class Clocks:
 
 
 def spmv_bytes(A, fmt_is_sell: bool):
-    per = 8 if fmt_is_sell else 4
+    per = 8 if fmt_is_sell else (2 if A.format == 5 else 4)  # 5: 16-bit words
     perm = 0 if A.explicit_perm else A.n * A.perm_bytes
     return per * A.n_words + 8 * (A.n_slices + 1) + perm + 4 * A.m + 4 * A.n
 
@@ -582,7 +582,7 @@ def run_ours(args):
                  ("fp16_v5", "fp16", 15), ("fp16_v6", "fp16", 15), ("fp16_v7", "fp16", 15),
                  ("fp16_v8", "fp16", 15), ("fp16_v9", "fp16", 15), ("fp16_v10", "fp16", 15),
                  ("e8m7", "e8my", 15),
-                 ("e8m11", "e8my", 11), ("e8m15", "e8my", 7))
+                 ("e8m11", "e8my", 11), ("e8m15", "e8my", 7), ("w16_e4m3", "w16_e4m3", 7))
         if args.formats != "all":
             keep = set(args.formats.split(",")) if args.formats != "none" else set()
             sweep = tuple(f for f in sweep if f[0] in keep)

@@ -69,12 +69,25 @@ typedef enum packsell_status {
  *         grid (§4.2.2); D in [1, 22].
  * SELL_F32 / SELL_F64 : plain SELL-C-sigma (§3) with separate FP32 / FP64
  *         value and int32 column arrays: the baseline format and the FP64
- *         outer operator of the mixed-precision solver. D is ignored. */
+ *         outer operator of the mixed-precision solver. D is ignored.  * W16_E4M3: 16-bit words (W = 16, one of the other word sizes of §4.2.1):
+ *         bit 0 flag, bits 1..7 delta (D = 7, needs D = 7), bits 8..15 an
+ *         FP8 E4M3 value (OCP: 4 exponent bits, bias 7, 3 fraction bits,
+ *         largest finite 448, round to nearest even; a value that rounds
+ *         past 448 is PACKSELL_ERR_RANGE). A dummy holds a 15-bit delta, so a
+ *         gap of 2^15 or more takes several dummies (each takes
+ *         min(remaining delta, 2^15 - 1)). n_words counts 16-bit words.
+ *         Supported by packsell_encode, packsell_spmv (one thread-per-row
+ *         kernel; packsell_set_spmv_variant/tune_spmv see variant 1 only),
+ *         packsell_spmv_host, packsell_get_info, packsell_storage_rows and
+ *         packsell_export (2-byte words; packsell_import rejects the blob);
+ *         the other calls return PACKSELL_ERR_INVALID_ARG for it.
+ */
 typedef enum packsell_format {
     PACKSELL_FMT_FP16 = 1,
     PACKSELL_FMT_E8MY = 2,
     PACKSELL_FMT_SELL_F32 = 3,
-    PACKSELL_FMT_SELL_F64 = 4
+    PACKSELL_FMT_SELL_F64 = 4,
+    PACKSELL_FMT_W16_E4M3 = 5
 } packsell_format;
 
 typedef struct packsell_params {

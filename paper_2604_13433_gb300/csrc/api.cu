@@ -25,13 +25,25 @@ void clear_error() { g_last_error.clear(); }
 
 int64_t matrix_bytes(const Matrix &A) {
     int64_t b = 8 * (A.n_slices + 1) + (int64_t)A.perm_bytes * A.n;
-    if (is_packed(A.p.format)) b += 4 * A.n_words;
+    if (is_w16(A.p.format)) b += 2 * A.n_words;
+    else if (is_packed(A.p.format)) b += 4 * A.n_words;
     else b += (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8) * A.n_words;
     if (A.rowptr) b += 8 * (A.n + 1);
     return b;
 }
 
 void destroy_matrix(Matrix *A);
+
+// The SpMV of a matrix: 16-bit words have their own kernel.
+packsell_status spmv_route(const Matrix &A, const float *x, float *y, cudaStream_t s) {
+    return is_w16(A.p.format) ? spmv_w16_impl(A, x, y, s) : spmv_impl(A, x, y, s);
+}
+
+// Calls that do not take 16-bit words.
+packsell_status no_w16(const Matrix &A, const char *what) {
+    if (!is_w16(A.p.format)) return PACKSELL_OK;
+    return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for 16-bit words");
+}
 
 }  // namespace packsell
 
@@ -119,7 +131,8 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     clear_error();
     if (!Ah || !bytes) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: NULL argument");
     const Matrix &A = *M(Ah);
-    size_t vb = is_packed(A.p.format) ? 4 : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
+    size_t vb = is_w16(A.p.format) ? 2 : is_packed(A.p.format) ? 4
+                : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
     size_t need = sizeof(BlobHeader) + 8 * (A.n_slices + 1) + (size_t)A.perm_bytes * A.n +
                   vb * (size_t)A.n_words;
     if (!h_blob) {
@@ -150,7 +163,9 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
         PS_CUDA(cudaMemcpyAsync(dst, A.perm, (size_t)A.perm_bytes * A.n, cudaMemcpyDeviceToHost, s));
         dst += (size_t)A.perm_bytes * A.n;
     }
-    if (is_packed(A.p.format)) {
+    if (is_w16(A.p.format)) {
+        PS_CUDA(cudaMemcpyAsync(dst, A.pack16, 2 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
+    } else if (is_packed(A.p.format)) {
         PS_CUDA(cudaMemcpyAsync(dst, A.pack, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
     } else {
         size_t eb = A.p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
@@ -292,9 +307,9 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
         if (var >= 9 && var <= 10 && !m->stage[var - 9].part) continue;
         if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;
         m->variant = var;
-        for (int r = 0; r < 3 && st == PACKSELL_OK; ++r) st = spmv_impl(*m, x, y, s);
+        for (int r = 0; r < 3 && st == PACKSELL_OK; ++r) st = spmv_route(*m, x, y, s);
         cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == PACKSELL_OK; ++r) st = spmv_impl(*m, x, y, s);
+        for (int r = 0; r < reps && st == PACKSELL_OK; ++r) st = spmv_route(*m, x, y, s);
         cudaEventRecord(e1, s);
         if (st != PACKSELL_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -337,7 +352,7 @@ packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y
     clear_error();
     if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: NULL argument");
-    return spmv_impl(*M(A), x, y, as_stream(stream));
+    return spmv_route(*M(A), x, y, as_stream(stream));
 }
 
 packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
@@ -353,6 +368,7 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
     clear_error();
     if (!A || (M(A)->m > 0 && !X) || (M(A)->n > 0 && !Y))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmm: NULL argument");
+    if (no_w16(*M(A), "packsell_spmm") != PACKSELL_OK) return PACKSELL_ERR_INVALID_ARG;
     return spmm_impl(*M(A), k, X, ldx, Y, ldy, as_stream(stream));
 }
 
@@ -361,6 +377,7 @@ packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *d
     clear_error();
     if (!A || (M(A)->n > 0 && !dy) || (M(A)->m > 0 && !dx))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_transpose: NULL argument");
+    if (no_w16(*M(A), "packsell_spmv_transpose") != PACKSELL_OK) return PACKSELL_ERR_INVALID_ARG;
     return spmv_t_impl(*M(A), dy, dx, as_stream(stream));
 }
 
@@ -369,6 +386,7 @@ packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, co
     clear_error();
     if (!A || (M(A)->nnz > 0 && (!u || !v || !out)))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pattern_outer: NULL argument");
+    if (no_w16(*M(A), "packsell_pattern_outer") != PACKSELL_OK) return PACKSELL_ERR_INVALID_ARG;
     return pattern_outer_impl(*M(A), alpha, u, v, out, as_stream(stream));
 }
 
@@ -388,7 +406,7 @@ packsell_status packsell_spmv_host(const packsell_matrix *A, const float *h_x, f
     cudaStream_t s = as_stream(stream);
     if (m.m > 0)
         PS_CUDA(cudaMemcpyAsync(d_x, h_x, sizeof(float) * (size_t)m.m, cudaMemcpyHostToDevice, s));
-    const packsell_status st = spmv_impl(m, d_x, d_y, s);
+    const packsell_status st = spmv_route(m, d_x, d_y, s);
     if (st != PACKSELL_OK) return st;
     if (m.n > 0)
         PS_CUDA(cudaMemcpyAsync(h_y, d_y, sizeof(float) * (size_t)m.n, cudaMemcpyDeviceToHost, s));

@@ -13,6 +13,7 @@
 //   6. (host reads the word total once) scatter words column-major per slice,
 //      zero words as padding.
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include <algorithm>
@@ -112,13 +113,28 @@ __device__ __forceinline__ int field_e8my(double v, int D, uint32_t &field) {
     return 0;
 }
 
+// FP8 E4M3 code (16-bit words) with the hardware conversion, round to
+// nearest even from the input precision. Saturation is only a fallback: a
+// magnitude above 464 (halfway from 448, the largest finite value, to the
+// next step) would round past 448 and is reported as out of range.
+template <typename T>
+__device__ __forceinline__ int field_e4m3(T v, uint32_t &field) {
+    if (!isfinite(v)) return PACKSELL_ERR_NONFINITE;
+    if (fabs((double)v) > 464.0) return PACKSELL_ERR_RANGE;
+    field = (sizeof(T) == 4) ? (uint32_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3)
+                             : (uint32_t)__nv_cvt_double_to_fp8((double)v, __NV_SATFINITE, __NV_E4M3);
+    return 0;
+}
+
 template <typename T>
 __global__ void k_quantize(int64_t nnz, const T *__restrict__ val, int fmt, int D,
                            uint32_t *__restrict__ field, DevStatus *st) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
         uint32_t f = 0;
-        int err = (fmt == PACKSELL_FMT_FP16) ? field_fp16(val[p], f) : field_e8my(val[p], D, f);
+        int err = (fmt == PACKSELL_FMT_FP16) ? field_fp16(val[p], f)
+                  : (fmt == PACKSELL_FMT_W16_E4M3) ? field_e4m3(val[p], f)
+                                                   : field_e8my(val[p], D, f);
         if (err) dev_fail(st, err, p);
         field[p] = f;
     }
@@ -131,7 +147,7 @@ __device__ __forceinline__ long long resolve_k_left(long long user, const unsign
 // Stored words per original row; for SELL (packed = 0) just the row length.
 __global__ void k_count_words(int n, const int64_t *__restrict__ rowptr,
                               const int32_t *__restrict__ col, int sigma, long long k_left_user,
-                              const unsigned long long *kl, int D, int packed,
+                              const unsigned long long *kl, int D, int packed, int W,
                               int32_t *__restrict__ words, unsigned long long *total,
                               DevStatus *st) {
     // a malformed row pointer (found by k_check_rows) must not be walked
@@ -144,13 +160,19 @@ __global__ void k_count_words(int n, const int64_t *__restrict__ rowptr,
         if (packed) {
             long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
             long long lim = 1ll << D;
+            const long long dmax = (1ll << (W - 1)) - 1;  // a dummy's delta field
             for (int64_t p = a; p < b; ++p) {
                 long long d = (long long)col[p] - prev;
                 if (d < 0) {
                     dev_fail(st, PACKSELL_ERR_INVALID_ARG, p);
                     break;
                 }
-                cnt += (d >= lim);
+                // dummies while the delta does not fit in D bits, each taking
+                // at most dmax of it (one dummy with 32-bit words)
+                while (d >= lim) {
+                    d -= d < dmax ? d : dmax;
+                    ++cnt;
+                }
                 prev = col[p];
             }
         }
@@ -342,6 +364,41 @@ __global__ void k_scatter_packed(int n, int64_t rows_total, int C, int sigma, lo
     for (; j < w; ++j) dst[j * C] = 0u;
 }
 
+// 16-bit words: (code << 8) | (d << 1) | 1 with a value, (q << 1) for a
+// dummy of q < 2^15, 0 for padding; dummies while the delta is 2^7 or more.
+__global__ void k_scatter_w16(int n, int64_t rows_total, int C, int sigma, long long k_left_user,
+                              const unsigned long long *kl, const int64_t *__restrict__ rowptr,
+                              const int32_t *__restrict__ col, const uint32_t *__restrict__ code,
+                              const void *perm, int perm_bytes, const int64_t *__restrict__ offset,
+                              uint16_t *__restrict__ pack) {
+    int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ii >= rows_total) return;
+    int i = (int)ii;
+    int64_t k = ii / C;
+    int l = (int)(ii - k * C);
+    int64_t s = offset[k];
+    int64_t w = (offset[k + 1] - s) / C;
+    uint16_t *dst = pack + s + l;
+    int64_t j = 0;
+    if (i < n) {
+        int r = orig_row(i, sigma, perm, perm_bytes);
+        long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+            long long d = (long long)col[p] - prev;
+            while (d >= 128) {
+                const long long q = d < 32767 ? d : 32767;
+                dst[j * C] = (uint16_t)(q << 1);
+                ++j;
+                d -= q;
+            }
+            dst[j * C] = (uint16_t)((code[p] << 8) | ((uint32_t)d << 1) | 1u);
+            ++j;
+            prev = col[p];
+        }
+    }
+    for (; j < w; ++j) dst[j * C] = 0;
+}
+
 template <typename TO, typename TI>
 __global__ void k_scatter_sell(int n, int64_t rows_total, int C, int sigma,
                                const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -399,6 +456,7 @@ struct Temps {
 
 void free_matrix_arrays(Matrix *A) {
     cudaFree(A->pack);
+    cudaFree(A->pack16);
     cudaFree(A->val);
     cudaFree(A->col);
     cudaFree(A->offset);
@@ -418,7 +476,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
     const int fmt = p.format;
     if (!out) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: out is NULL");
     *out = nullptr;
-    if (!is_packed(fmt) && !is_sell(fmt))
+    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: unknown format");
     if (p.C < 1 || p.C > 1024) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: C must be in [1, 1024]");
     if (p.sigma < 1 || p.sigma > 65536)
@@ -427,14 +485,17 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: FP16 needs D = 15");
     if (fmt == PACKSELL_FMT_E8MY && (p.D < 1 || p.D > 22))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: E8MY needs D in [1, 22]");
+    if (is_w16(fmt) && p.D != 7)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: W16_E4M3 needs D = 7");
     if (n < 0 || m < 0 || nnz < 0 || n >= (1ll << 31) || m >= (1ll << 31))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: n and m must be in [0, 2^31)");
     if (!rowptr || (nnz > 0 && (!col || !val)))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: NULL array");
     if (p.k_left < -1) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: k_left < -1");
 
-    const bool packed = is_packed(fmt);
+    const bool packed = is_packed(fmt) || is_w16(fmt);  // delta-value words
     const int D = packed ? p.D : 31;
+    const int W = is_w16(fmt) ? 16 : 32;
     const int64_t S = (n + p.C - 1) / p.C;
     const int perm_bytes = (p.sigma == 1) ? 0 : (p.sigma <= 256 ? 1 : 2);
 
@@ -488,7 +549,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         }
         if (n > 0) {
             k_count_words<<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, col, p.sigma, p.k_left, kl,
-                                                       D, packed ? 1 : 0, words, total, st);
+                                                       D, packed ? 1 : 0, W, words, total, st);
             if (p.sigma > 1) {
                 int64_t nb = (n + p.sigma - 1) / p.sigma;
                 int tpb = std::min(1024, ((std::min(p.sigma, 1024) + 31) / 32) * 32);
@@ -527,7 +588,15 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         A->n_pad = nw - (int64_t)htotal;
         A->max_width = hmaxw;
 
-        if (packed) {
+        if (is_w16(fmt)) {
+            if (cudaMalloc(&A->pack16, sizeof(uint16_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
+                return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
+            int64_t rows_total = S * p.C;
+            if (rows_total > 0)
+                k_scatter_w16<<<blocks_for(rows_total), TPB, 0, s>>>(
+                    (int)n, rows_total, p.C, p.sigma, A->p.k_left, kl, rowptr, col, field,
+                    A->perm, perm_bytes, A->offset, A->pack16);
+        } else if (packed) {
             if (cudaMalloc(&A->pack, sizeof(uint32_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
                 return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
             int64_t rows_total = S * p.C;

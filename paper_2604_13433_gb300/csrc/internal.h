@@ -35,6 +35,7 @@ struct Matrix {
     int device = 0;
     // device arrays
     uint32_t *pack = nullptr;  // PackSELL words
+    uint16_t *pack16 = nullptr;  // 16-bit words (PACKSELL_FMT_W16_E4M3)
     void *val = nullptr;       // SELL values (float / double)
     int32_t *col = nullptr;    // SELL columns
     int64_t *offset = nullptr; // n_slices + 1
@@ -59,6 +60,7 @@ struct Matrix {
 
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
 inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PACKSELL_FMT_SELL_F64; }
+inline bool is_w16(int fmt) { return fmt == PACKSELL_FMT_W16_E4M3; }
 
 // thread-local error message
 packsell_status fail(packsell_status st, const std::string &msg);
@@ -77,6 +79,9 @@ packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_
 // stage.cu
 packsell_status plan_stage(Matrix &A, cudaStream_t s);
 void stage_free(Matrix &A);
+
+// w16.cu
+packsell_status spmv_w16_impl(const Matrix &A, const float *x, float *y, cudaStream_t s);
 
 // half_io.cu
 packsell_status spmv_x16_impl(const Matrix &A, const uint16_t *x, uint16_t *y, cudaStream_t s);

@@ -19,9 +19,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpacksell.so")
 
-FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64 = 1, 2, 3, 4
+FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3 = 1, 2, 3, 4, 5
 _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
-            "sell_f64": FMT_SELL_F64}
+            "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
           6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
@@ -387,7 +387,9 @@ def packsell_arrays(A: PackSELLMatrix):
         pos += A.perm_bytes * A.n
     else:
         out["perm"] = np.zeros(A.n, np.int32)
-    if A.format in (FMT_FP16, FMT_E8MY):
+    if A.format == FMT_W16_E4M3:
+        out["pack"] = np.frombuffer(blob, np.uint16, A.n_words, pos)
+    elif A.format in (FMT_FP16, FMT_E8MY):
         out["pack"] = np.frombuffer(blob, np.uint32, A.n_words, pos)
     else:
         dt = np.float64 if A.format == FMT_SELL_F64 else np.float32
