@@ -38,7 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ("spmv.cu", "device.cuh", "reduce.cuh")
 KERNEL_NAMES = {1: "k_spmv_packed", 2: "k_spmv_bulk", 3: "k_spmv_bulk", 4: "k_spmv_bulk",
                 5: "k_spmv_prefetch", 6: "k_spmv_prefetch", 7: "k_spmv_dual", 8: "k_spmv_dual",
-                9: "k_spmv_stage", 10: "k_spmv_stage"}
+                9: "k_spmv_stage", 10: "k_spmv_stage", 11: "k_spmv_csr", 12: "k_spmv_pipe",
+                13: "k_spmv_prefetch"}
 
 
 def parse():
@@ -135,6 +136,8 @@ class Clocks:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        if self.p is not None:
+            time.sleep(1.0)  # nvidia-smi starts up (NVML init) before the timed region
         return self
 
     def __exit__(self, *a):
@@ -581,6 +584,7 @@ def run_ours(args):
                  ("fp16_v2", "fp16", 15), ("fp16_v3", "fp16", 15), ("fp16_v4", "fp16", 15),
                  ("fp16_v5", "fp16", 15), ("fp16_v6", "fp16", 15), ("fp16_v7", "fp16", 15),
                  ("fp16_v8", "fp16", 15), ("fp16_v9", "fp16", 15), ("fp16_v10", "fp16", 15),
+                 ("fp16_v13", "fp16", 15),
                  ("e8m7", "e8my", 15),
                  ("e8m11", "e8my", 11), ("e8m15", "e8my", 7), ("w16_e4m3", "w16_e4m3", 7))
         if args.formats != "all":
@@ -626,8 +630,8 @@ def run_ours(args):
 
         ms_e2e = ms_e2e_serial = None
         if not args.no_e2e:
-            ms_e2e_serial, _ = time_launches(torch, e2e_step, max(K // 10, 10), max(W // 10, 3))
-            ms_e2e = e2e_pipelined(torch, ps, A16, xp, max(K // 10, 10), max(W // 10, 3))
+            ms_e2e_serial, _ = time_launches(torch, e2e_step, max(K // 10, 100), max(W // 10, 5))
+            ms_e2e = e2e_pipelined(torch, ps, A16, xp, max(K // 10, 100), max(W // 10, 5))
     sell = formats.get("sell_f32")
     ps.packsell_spmv(A16, x, y)
     ms_cold = time_cold(torch, lambda: ps.packsell_spmv(A16, x, y))

@@ -32,6 +32,12 @@
  *    streams at once. packsell_set_spmv_variant and packsell_tune_spmv change
  *    it and must not overlap other calls on the same matrix; kernels that
  *    report through the matrix's device status word share that word.
+ *  - Some products (SpMV variant 13, FP32 SELL, 16-bit words, binary16
+ *    vectors) are launched with programmatic dependent launch: they start
+ *    while the previous kernel of the stream drains and read the matrix
+ *    before they wait for it; x, y and every other buffer are touched only
+ *    after it has completed. A matrix is complete when packsell_encode or
+ *    packsell_import returns, and the caller must not write its arrays.
  */
 #ifndef PACKSELL_H
 #define PACKSELL_H
@@ -142,7 +148,8 @@ const char *packsell_last_error(void);
  * Every step runs in CUDA kernels on `stream`: validation, lower bandwidth,
  * quantisation, word counts with dummies, the stable sigma sort (descending
  * stored words), slice widths, offsets, scatter. The call SYNCHRONISES the
- * stream once (to size the word array). Temporaries are stream-ordered
+ * stream (to size the word array, and at the end: the matrix is complete
+ * when the call returns). Temporaries are stream-ordered
  * allocations freed before return. On success *out owns new device buffers.
  * Errors: INVALID_ARG (parameters, k_left below the bandwidth), UNSORTED,
  * RANGE (column out of range, value overflows the format), NONFINITE,
@@ -221,7 +228,7 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 
 /* Number of SpMV kernel variants (1..PACKSELL_SPMV_VARIANTS). */
-#define PACKSELL_SPMV_VARIANTS 12
+#define PACKSELL_SPMV_VARIANTS 13
 
 /* SpMV kernel variants (all compute the same bits):
  *   0 auto (the plan's or the tuner's choice),
@@ -257,7 +264,13 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     the word loads of one row overlap the gathers of the previous one; one
  *     round per row, fitted to the widest slice as in 5, so every slice must
  *     hold at most 16 words. For short rows (the solver's 7-point matrices);
- *     the solver's fused SpMV + dot uses it for such matrices. */
+ *     the solver's fused SpMV + dot uses it for such matrices.
+ *  13 variant 5 (rows run to the slice width) launched with programmatic
+ *     dependent launch: its blocks are scheduled while the previous kernel
+ *     of the stream drains, load the offsets and their first round of words,
+ *     and only then wait for that kernel to complete before they read x or
+ *     write y. Safe because a matrix is complete when packsell_encode or
+ *     packsell_import returns and no product writes it (PackSELL, C = 32). */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant for this matrix: time every available variant

@@ -272,7 +272,7 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
                     "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
     if (variant >= 5 && (!is_packed(m->p.format) || m->p.C != 32))
         return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_set_spmv_variant: variants 5-10 and 12 need a PackSELL matrix with C = 32");
+                    "packsell_set_spmv_variant: variants 5-10, 12 and 13 need a PackSELL matrix with C = 32");
     if (variant == 12 && m->max_width > 16)
         return fail(PACKSELL_ERR_INVALID_ARG,
                     "packsell_set_spmv_variant: variant 12 needs slices of at most 16 words");
@@ -302,7 +302,7 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
         if (var >= 2 && !is_packed(m->p.format)) continue;
         if (var == 11 && !m->csr_items) continue;
-        if (((var >= 5 && var <= 10) || var == 12) && m->p.C != 32) continue;
+        if (((var >= 5 && var <= 10) || var >= 12) && m->p.C != 32) continue;
         if (var == 12 && m->max_width > 16) continue;
         if (var >= 9 && var <= 10 && !m->stage[var - 9].part) continue;
         if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;

@@ -4,6 +4,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "internal.h"
 
 namespace packsell {
@@ -77,6 +79,45 @@ __device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
 // first) keeps the words from taking L1 and L2 lines from the x gathers
 // (with plain loads the words evict x and the gathers fall through to L2).
 __device__ __forceinline__ uint32_t ldg_stream(const uint32_t *p) { return __ldcs(p); }
+
+// ---- programmatic dependent launch (sm_90 and later) ----
+// A kernel launched by launch_pdl may be scheduled while the previous kernel
+// of its stream drains. grid_dep_sync first waits until that kernel has
+// completed and its memory is visible (at once when there is none), then
+// lets the next kernel of the stream be scheduled once every block of this
+// grid has passed the same point (or exited). Signalling only after the
+// wait keeps at most one kernel waiting ahead: signalled at block start, a
+// chain of persistent-grid solver kernels queued up on the SMs and slowed the
+// one running. The product kernels read only the matrix (complete when
+// encode or import returns, never written by a product) before the call,
+// and x, y and solver state after it.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_sync() {
+    grid_dep_wait();
+    grid_dep_launch();
+}
+// A grid that covers the rows once (more blocks than fit at a time) may
+// signal at block start instead: its dependents can then only be scheduled
+// once its last wave has started.
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---- mbarrier and bulk-copy (TMA engine) primitives, inline PTX ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {

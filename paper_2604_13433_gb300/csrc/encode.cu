@@ -636,6 +636,10 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         PS_LAUNCH_CHECK("packsell_encode: scatter");
         packsell_status pst = plan_spmv(*A, s);
         if (pst != PACKSELL_OK) return bail(pst);
+        // the matrix is complete on return: products may read its words
+        // before they wait on the previous kernel of their stream
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "packsell_encode: synchronize"));
         // Temps are released (stream-ordered) here; they outlive the scatter.
     }
     *out = A;

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(TPB)
                const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                const void *__restrict__ perm, int perm_bytes, Decode dc,
                const __half *__restrict__ x, __half *__restrict__ y) {
+    grid_dep_launch();  // one pass over the rows: signal at block start
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = i >> 5;
@@ -31,11 +32,14 @@ __global__ void __launch_bounds__(TPB)
     const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
     int c = (k_left < blk) ? (int)(blk - k_left) : 0;
     float t = 0.f;
+    if (w <= 0) grid_dep_wait();
     for (int j0 = 0; j0 < w; j0 += PF) {
         const int wr = w - j0;
         uint32_t wd[PF];
 #pragma unroll
         for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? ldg_stream(pp + (j0 + u) * 32) : 0u;
+        // the first round's words load before the wait; x and y after it
+        if (j0 == 0) grid_dep_wait();
         bool f[PF];
         float xv[PF];
 #pragma unroll
@@ -55,26 +59,23 @@ __global__ void __launch_bounds__(TPB)
 }
 
 template <int FMT, int PF>
-void launch_x16(const Matrix &A, const void *perm, int pb, const __half *x, __half *y,
-                cudaStream_t s) {
+cudaError_t launch_x16(const Matrix &A, const void *perm, int pb, const __half *x, __half *y,
+                       cudaStream_t s) {
     const int sg = A.p.sigma;
     const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
     const unsigned g = (unsigned)((A.n + TPB - 1) / TPB);
-    if (pb)
-        k_spmv_x16<FMT, PF, true><<<g, TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack,
-                                                     perm, pb, make_decode(A), x, y);
-    else
-        k_spmv_x16<FMT, PF, false><<<g, TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset,
-                                                      A.pack, perm, pb, make_decode(A), x, y);
+    return launch_pdl(pb ? k_spmv_x16<FMT, PF, true> : k_spmv_x16<FMT, PF, false>, g, TPB, s,
+                      (int)A.n, sg, sh, A.p.k_left, (const int64_t *)A.offset,
+                      (const uint32_t *)A.pack, perm, pb, make_decode(A), x, y);
 }
 
 template <int FMT>
-void launch_x16_pf(const Matrix &A, const void *perm, int pb, const __half *x, __half *y,
-                   cudaStream_t s) {
+cudaError_t launch_x16_pf(const Matrix &A, const void *perm, int pb, const __half *x, __half *y,
+                          cudaStream_t s) {
     const int w = A.max_width;
-    if (w <= 8) launch_x16<FMT, 8>(A, perm, pb, x, y, s);
-    else if (w <= 12) launch_x16<FMT, 12>(A, perm, pb, x, y, s);
-    else launch_x16<FMT, 16>(A, perm, pb, x, y, s);
+    if (w <= 8) return launch_x16<FMT, 8>(A, perm, pb, x, y, s);
+    if (w <= 12) return launch_x16<FMT, 12>(A, perm, pb, x, y, s);
+    return launch_x16<FMT, 16>(A, perm, pb, x, y, s);
 }
 
 }  // namespace
@@ -88,8 +89,10 @@ packsell_status spmv_x16_impl(const Matrix &A, const uint16_t *x, uint16_t *y, c
     const int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     const __half *xh = reinterpret_cast<const __half *>(x);
     __half *yh = reinterpret_cast<__half *>(y);
-    if (A.p.format == PACKSELL_FMT_FP16) launch_x16_pf<PACKSELL_FMT_FP16>(A, perm, pb, xh, yh, s);
-    else launch_x16_pf<PACKSELL_FMT_E8MY>(A, perm, pb, xh, yh, s);
+    const cudaError_t e = A.p.format == PACKSELL_FMT_FP16
+                              ? launch_x16_pf<PACKSELL_FMT_FP16>(A, perm, pb, xh, yh, s)
+                              : launch_x16_pf<PACKSELL_FMT_E8MY>(A, perm, pb, xh, yh, s);
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv_x16");
     PS_LAUNCH_CHECK("packsell_spmv_x16");
     return PACKSELL_OK;
 }

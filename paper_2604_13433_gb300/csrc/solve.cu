@@ -25,6 +25,7 @@
 #include <mutex>
 #include <string>
 
+#include "device.cuh"
 #include "internal.h"
 #include "reduce.cuh"
 
@@ -117,6 +118,7 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(VTPB)
     k_update(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
              const T *__restrict__ q, const T *__restrict__ M, Red red) {
+    grid_dep_sync();  // launched by launch_pdl: everything it reads comes from earlier kernels
     if (red.sc->done) return;
     const T a = (T)red.sc->alpha;
     T rz = 0, rr = 0;
@@ -174,6 +176,7 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(VTPB)
     k_pupdate(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
               const SolveScalars *sc) {
+    grid_dep_sync();  // launched by launch_pdl, as k_update
     if (sc->done) return;
     const T b = (T)sc->beta;
     if (VEC) {
@@ -213,22 +216,24 @@ __global__ void __launch_bounds__(VTPB)
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// The per-iteration kernels (SpMV + dot, update, direction) run with
+// programmatic dependent launch: each is scheduled while the one before it
+// drains.
 template <typename T>
-void launch_update(int G, cudaStream_t q, int64_t n, T *x, T *r, const T *p, const T *qv,
-                   const T *M, const Red &red) {
-    if (aligned16(x) && aligned16(r) && aligned16(p) && aligned16(qv) && (!M || aligned16(M)))
-        k_update<T, true><<<G, VTPB, 0, q>>>(n, x, r, p, qv, M, red);
-    else
-        k_update<T, false><<<G, VTPB, 0, q>>>(n, x, r, p, qv, M, red);
+cudaError_t launch_update(int G, cudaStream_t q, int64_t n, T *x, T *r, const T *p, const T *qv,
+                          const T *M, const Red &red) {
+    const bool vec =
+        aligned16(x) && aligned16(r) && aligned16(p) && aligned16(qv) && (!M || aligned16(M));
+    return launch_pdl(vec ? k_update<T, true> : k_update<T, false>, (unsigned)G, VTPB, q, n, x, r,
+                      p, qv, M, red);
 }
 
 template <typename T>
-void launch_pupdate(int G, cudaStream_t q, int64_t n, const T *r, const T *M, T *p,
-                    const SolveScalars *sc) {
-    if (aligned16(r) && aligned16(p) && (!M || aligned16(M)))
-        k_pupdate<T, true><<<G, VTPB, 0, q>>>(n, r, M, p, sc);
-    else
-        k_pupdate<T, false><<<G, VTPB, 0, q>>>(n, r, M, p, sc);
+cudaError_t launch_pupdate(int G, cudaStream_t q, int64_t n, const T *r, const T *M, T *p,
+                           const SolveScalars *sc) {
+    const bool vec = aligned16(r) && aligned16(p) && (!M || aligned16(M));
+    return launch_pdl(vec ? k_pupdate<T, true> : k_pupdate<T, false>, (unsigned)G, VTPB, q, n, r,
+                      M, p, sc);
 }
 
 // Outer: z = ||r|| x_in (FP64), s1 = z.q (q = A p of the previous direction)
@@ -438,9 +443,11 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                     for (int k = 0; k < o.m_in; ++k) {
                         packsell_status e = spmv_dot_f32(*Ain, w.pi, w.qi, red(FIN_PQ_ALPHA), q);
                         if (e != PACKSELL_OK) return e;
-                        launch_update<float>(G, q, n, w.xi, w.ri, w.pi, w.qi, w.M32, red(FIN_RZ_BETA));
-                        if (k + 1 < o.m_in)
-                            launch_pupdate<float>(G, q, n, w.ri, w.M32, w.pi, w.sc);
+                        cudaError_t ce = launch_update<float>(G, q, n, w.xi, w.ri, w.pi, w.qi,
+                                                              w.M32, red(FIN_RZ_BETA));
+                        if (ce == cudaSuccess && k + 1 < o.m_in)
+                            ce = launch_pupdate<float>(G, q, n, w.ri, w.M32, w.pi, w.sc);
+                        if (ce != cudaSuccess) return cuda_fail(ce, "packsell_pcg: inner update");
                     }
                     k_outer_z<<<G, VTPB, 0, q>>>(n, w.xi, w.z, w.q, red(FIN_ZQ_BETA));
                     k_outer_p<<<G, VTPB, 0, q>>>(n, w.z, w.p, w.sc);
@@ -450,8 +457,10 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 } else {
                     packsell_status e = spmv_dot_f64(*A64, w.p, w.q, nullptr, red(FIN_PQ_ALPHA_64), q);
                     if (e != PACKSELL_OK) return e;
-                    launch_update<double>(G, q, n, x, w.r, w.p, w.q, inv_diag, red(FIN_RZ_BETA_RR));
-                    launch_pupdate<double>(G, q, n, w.r, inv_diag, w.p, w.sc);
+                    cudaError_t ce = launch_update<double>(G, q, n, x, w.r, w.p, w.q, inv_diag,
+                                                           red(FIN_RZ_BETA_RR));
+                    if (ce == cudaSuccess) ce = launch_pupdate<double>(G, q, n, w.r, inv_diag, w.p, w.sc);
+                    if (ce != cudaSuccess) return cuda_fail(ce, "packsell_pcg: update");
                 }
             }
             PS_LAUNCH_CHECK("packsell_pcg: iteration");

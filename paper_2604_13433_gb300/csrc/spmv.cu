@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TPB)
 // gathers. Words past the row's slice width are taken as 0 (padding).
 // One row of the prefetch kernels: returns the sum, sets the output index
 // (PERM: rows are written through the sigma permutation).
-template <int FMT, int PF, int C, bool PERM = true, bool EXIT = false>
+template <int FMT, int PF, int C, bool PERM = true, bool EXIT = false, bool PDL = false>
 __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, long long k_left,
                                               const int64_t *__restrict__ offset,
                                               const uint32_t *__restrict__ pack,
@@ -92,12 +92,17 @@ __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, l
     const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
     int c = (k_left < blk) ? (int)(blk - k_left) : 0;
     float t = 0.f;
+    if (PDL && w <= 0) grid_dep_wait();
     for (int j0 = 0; j0 < w; j0 += PF) {
         const int wr = w - j0;
         // loads predicated on the width; a word past it acts as padding
         uint32_t wd[PF];
 #pragma unroll
         for (int u = 0; u < PF; ++u) wd[u] = (u < wr) ? ldg_stream(pp + (j0 + u) * C) : 0u;
+        // PDL: the matrix is complete before any product runs, so the first
+        // round's words (and the offsets) load while the previous kernel of
+        // the stream finishes; x and y are touched only after the wait
+        if (PDL && j0 == 0) grid_dep_wait();
         bool f[PF];
         float xv[PF];
 #pragma unroll
@@ -123,18 +128,19 @@ __device__ __forceinline__ float prefetch_row(int i, int sigma, int sig_shift, l
 // and strides over rows (warps stay on whole slices) so that its reduction
 // is deterministic.
 template <int FMT, int PF, int C, int MINB, bool DOT = false, bool PERM = true,
-          bool EXIT = false>
+          bool EXIT = false, bool PDL = false>
 __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_prefetch(int n, int sigma, int sig_shift, long long k_left,
                     const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                     const void *__restrict__ perm, int perm_bytes, Decode dc,
                     const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
     if (!DOT) {
+        if (PDL) grid_dep_launch();  // one pass over the rows: signal at block start
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= n) return;
         int io;
-        const float t = prefetch_row<FMT, PF, C, PERM, EXIT>(i, sigma, sig_shift, k_left, offset,
-                                                             pack, perm, perm_bytes, dc, x, io);
+        const float t = prefetch_row<FMT, PF, C, PERM, EXIT, PDL>(
+            i, sigma, sig_shift, k_left, offset, pack, perm, perm_bytes, dc, x, io);
         y[io] = t;
         return;
     }
@@ -169,28 +175,36 @@ __device__ __forceinline__ void pipe_round(const uint32_t (&wd)[PF], Decode dc,
         if (f[u]) t = fmaf(word_value<FMT>(wd[u], dc), xv[u], t);
 }
 
-template <int FMT, int PF, int MINB, bool DOT, bool PERM>
+// PDL (launched by launch_pdl): the first row's words and the next row's
+// offsets load before the wait; the solver state, x and y after it.
+template <int FMT, int PF, int MINB, bool DOT, bool PERM, bool PDL = false>
 __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_pipe(int n, int sigma, int sig_shift, long long k_left,
                 const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                 const void *__restrict__ perm, int perm_bytes, Decode dc,
                 const float *__restrict__ x, float *__restrict__ y, Red red = Red{}) {
-    if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
+    if (!PDL && DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
     float d1 = 0.f;
     const int stride = gridDim.x * blockDim.x;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t cur[PF];
+    int in = i + stride;
+    int64_t sn = 0, en = 0;
     if (i < n) {
         const int64_t s = offset[i >> 5];
         const int w = (int)((offset[(i >> 5) + 1] - s) >> 5);
-        uint32_t cur[PF];
 #pragma unroll
         for (int u = 0; u < PF; ++u) cur[u] = (u < w) ? ldg_stream(pack + s + (i & 31) + u * 32) : 0u;
-        int in = i + stride;
-        int64_t sn = 0, en = 0;
         if (in < n) {
             sn = offset[in >> 5];
             en = offset[(in >> 5) + 1];
         }
+    }
+    if (PDL) {
+        grid_dep_sync();
+        if (DOT && red.sc->done) return;  // every thread, as above
+    }
+    if (i < n) {
         while (true) {
             const int wn = (int)((en - sn) >> 5);
             uint32_t nxt[PF];
@@ -336,6 +350,31 @@ packsell_status launch_prefetch(const Matrix &A, const void *perm, int pb, const
     else
         launch_prefetch_e<FMT, PF, MINB, false>(A, perm, pb, x, y, s);
     PS_LAUNCH_CHECK("packsell_spmv (prefetch)");
+    return PACKSELL_OK;
+}
+
+// Variant 13: the kernel of variant 5 (rows run to the slice width) launched
+// with programmatic stream serialisation, so that its blocks are scheduled
+// while the previous kernel of the stream drains and load their first words
+// before they wait for it.
+template <int FMT, int PF, int MINB>
+packsell_status launch_prefetch_pdl(const Matrix &A, const void *perm, int pb, const float *x,
+                                    float *y, cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    const unsigned g = (unsigned)grid_for(A.n);
+    const int n = (int)A.n;
+    const long long kl = A.p.k_left;
+    const int64_t *offset = A.offset;
+    const uint32_t *pack = A.pack;
+    const Decode dc = make_decode(A);
+    const cudaError_t e =
+        pb ? launch_pdl(k_spmv_prefetch<FMT, PF, 32, MINB - 1, false, true, false, true>, g, TPB, s, n,
+                        sg, sh, kl, offset, pack, perm, pb, dc, x, y, Red{})
+           : launch_pdl(k_spmv_prefetch<FMT, PF, 32, MINB, false, false, false, true>, g, TPB, s, n, sg,
+                        sh, kl, offset, pack, perm, pb, dc, x, y, Red{});
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (variant 13)");
+    PS_LAUNCH_CHECK("packsell_spmv (variant 13)");
     return PACKSELL_OK;
 }
 
@@ -638,12 +677,19 @@ packsell_status launch_bulk(const Matrix &A, int v, const void *perm, int pb, co
 // Plain SELL-C-sigma (§3): value and column streams, padding multiplies 0.
 // With DOT the kernel also reduces sum_i x_i y_i and sum_i x_i b_i over the
 // output rows (square matrices, original order).
-template <typename T, bool DOT = false>
-__global__ void __launch_bounds__(TPB)
-    k_spmv_sell(int n, int C, int sigma, const int64_t *__restrict__ offset,
-                const T *__restrict__ val, const int32_t *__restrict__ col,
-                const void *__restrict__ perm, int perm_bytes, const T *__restrict__ x,
-                T *__restrict__ y, const T *__restrict__ b = nullptr, Red red = Red{}) {
+// PDL (launched by launch_pdl): in the single pass the first round of values
+// and columns loads before the grid waits for the previous kernel of the
+// stream; the reducing form waits first.
+template <typename T, bool DOT, bool PDL>
+__device__ __forceinline__ void sell_rows(int n, int C, int sigma,
+                                          const int64_t *__restrict__ offset,
+                                          const T *__restrict__ val,
+                                          const int32_t *__restrict__ col,
+                                          const void *__restrict__ perm, int perm_bytes,
+                                          const T *__restrict__ x, T *__restrict__ y,
+                                          const T *__restrict__ b, Red red) {
+    if (DOT && PDL) grid_dep_sync();  // the reducing form waits before it starts
+    if (!DOT && PDL) grid_dep_launch();  // one pass over the rows: signal at block start
     if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
     T d1 = 0, d2 = 0;  // per-thread sums in T; block and grid sums in FP64
     const int stride = DOT ? gridDim.x * blockDim.x : n;
@@ -655,6 +701,7 @@ __global__ void __launch_bounds__(TPB)
         const int32_t *cp = col + s + l;
         T t = 0;
         int j = 0;
+        if (PDL && !DOT && w < UNROLL) grid_dep_wait();
         for (; j + UNROLL <= w; j += UNROLL) {
             T v[UNROLL];
             int cc[UNROLL];
@@ -663,6 +710,9 @@ __global__ void __launch_bounds__(TPB)
                 v[u] = __ldcs(vp + (int64_t)(j + u) * C);
                 cc[u] = __ldcs(cp + (int64_t)(j + u) * C);
             }
+            // every round (returns at once after the first): a wait in the
+            // first round alone makes the compiler peel it (34 -> 62 registers)
+            if (PDL && !DOT) grid_dep_wait();
             T xv[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) xv[u] = __ldg(x + cc[u]);
@@ -678,6 +728,26 @@ __global__ void __launch_bounds__(TPB)
         }
     }
     if (DOT) reduce_publish(red, (double)d1, (double)d2);
+}
+
+template <typename T, bool DOT = false, bool PDL = false>
+__global__ void __launch_bounds__(TPB)
+    k_spmv_sell(int n, int C, int sigma, const int64_t *__restrict__ offset,
+                const T *__restrict__ val, const int32_t *__restrict__ col,
+                const void *__restrict__ perm, int perm_bytes, const T *__restrict__ x,
+                T *__restrict__ y, const T *__restrict__ b = nullptr, Red red = Red{}) {
+    sell_rows<T, DOT, PDL>(n, C, sigma, offset, val, col, perm, perm_bytes, x, y, b, red);
+}
+
+// The FP64 reducing form (FP64 PCG and the outer loop of IO-CG) with a
+// register budget of four blocks per SM: left to itself the compiler fits
+// it in 32 registers and spills.
+__global__ void __launch_bounds__(TPB, 4)
+    k_spmv_sell_dot64(int n, int C, int sigma, const int64_t *__restrict__ offset,
+                      const double *__restrict__ val, const int32_t *__restrict__ col,
+                      const void *__restrict__ perm, int perm_bytes, const double *__restrict__ x,
+                      double *__restrict__ y, const double *__restrict__ b, Red red) {
+    sell_rows<double, true, true>(n, C, sigma, offset, val, col, perm, perm_bytes, x, y, b, red);
 }
 
 // Thread-per-row PackSELL SpMV fused with sum_i x_i y_i (solver use, any C),
@@ -883,6 +953,23 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
         return h ? launch_dual<PACKSELL_FMT_FP16, 16, 3>(A, perm, pb, x, y, s)
                  : launch_dual<PACKSELL_FMT_E8MY, 16, 3>(A, perm, pb, x, y, s);
     }
+    if (var == 13 && is_packed(A.p.format)) {
+        if (A.p.C != 32)
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: variant 13 needs C = 32");
+        const bool h = A.p.format == PACKSELL_FMT_FP16;
+        const int pf = round_words(A.max_width);
+        if (pf == 8)
+            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 8, 6>(A, perm, pb, x, y, s)
+                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 8, 6>(A, perm, pb, x, y, s);
+        if (pf == 10)
+            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 10, 6>(A, perm, pb, x, y, s)
+                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 10, 6>(A, perm, pb, x, y, s);
+        if (pf == 12)
+            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 12, 5>(A, perm, pb, x, y, s)
+                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 12, 5>(A, perm, pb, x, y, s);
+        return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 16, 5>(A, perm, pb, x, y, s)
+                 : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 16, 5>(A, perm, pb, x, y, s);
+    }
     if ((var == 5 || var == 6) && is_packed(A.p.format)) {
         if (A.p.C != 32)
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: the prefetch variants need C = 32");
@@ -921,10 +1008,14 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
             k_spmv_packed<PACKSELL_FMT_E8MY><<<g, TPB, 0, s>>>(
                 (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
             break;
-        case PACKSELL_FMT_SELL_F32:
-            k_spmv_sell<float><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
-                                                 (const float *)A.val, A.col, perm, pb, x, y);
+        case PACKSELL_FMT_SELL_F32: {
+            const cudaError_t e = launch_pdl(k_spmv_sell<float, false, true>, (unsigned)g, TPB, s,
+                                             (int)A.n, A.p.C, A.p.sigma, (const int64_t *)A.offset,
+                                             (const float *)A.val, (const int32_t *)A.col, perm,
+                                             pb, x, y, (const float *)nullptr, Red{});
+            if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (SELL)");
             break;
+        }
         default:
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: SELL_F64 needs packsell_spmv_f64");
     }
@@ -1045,18 +1136,20 @@ void launch_prefetch_dot(const Matrix &A, const float *x, float *y, const Red &r
 }
 
 template <int FMT, int PF, int MINB>
-void launch_pipe_dot(const Matrix &A, const float *x, float *y, const Red &red, cudaStream_t s) {
+cudaError_t launch_pipe_dot(const Matrix &A, const float *x, float *y, const Red &red,
+                            cudaStream_t s) {
     const int sg = A.p.sigma;
     const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
     if (A.perm_bytes) {
-        auto k = k_spmv_pipe<FMT, PF, MINB, true, true>;
-        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm,
-                                      A.perm_bytes, make_decode(A), x, y, red);
-    } else {
-        auto k = k_spmv_pipe<FMT, PF, MINB, true, false>;
-        k<<<dot_grid(k), TPB, 0, s>>>((int)A.n, sg, sh, A.p.k_left, A.offset, A.pack, A.perm, 0,
-                                      make_decode(A), x, y, red);
+        auto k = k_spmv_pipe<FMT, PF, MINB, true, true, true>;
+        return launch_pdl(k, (unsigned)dot_grid(k), TPB, s, (int)A.n, sg, sh, A.p.k_left,
+                          (const int64_t *)A.offset, (const uint32_t *)A.pack,
+                          (const void *)A.perm, A.perm_bytes, make_decode(A), x, y, red);
     }
+    auto k = k_spmv_pipe<FMT, PF, MINB, true, false, true>;
+    return launch_pdl(k, (unsigned)dot_grid(k), TPB, s, (int)A.n, sg, sh, A.p.k_left,
+                      (const int64_t *)A.offset, (const uint32_t *)A.pack, (const void *)A.perm, 0,
+                      make_decode(A), x, y, red);
 }
 
 int spmv_dot_blocks(const Matrix &) { return reduce_blocks(); }
@@ -1067,27 +1160,30 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
     const void *perm = A.perm;
     const int pb = A.perm_bytes;
     if (A.p.format == PACKSELL_FMT_SELL_F32) {
-        k_spmv_sell<float, true><<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
-                                                   (const float *)A.val, A.col, perm, pb, x, y,
-                                                   nullptr, red);
+        const cudaError_t e = launch_pdl(k_spmv_sell<float, true, true>, (unsigned)g, TPB, s,
+                                         (int)A.n, A.p.C, A.p.sigma, (const int64_t *)A.offset,
+                                         (const float *)A.val, (const int32_t *)A.col, perm, pb,
+                                         x, y, (const float *)nullptr, red);
+        if (e != cudaSuccess) return cuda_fail(e, "spmv_dot_f32 (SELL)");
     } else if (A.p.C == 32 && A.max_width <= 16) {
         // every row fits one round: the pipelined kernel loads the next
         // row's words while the current row is gathered
         const bool h = A.p.format == PACKSELL_FMT_FP16;
         const int pf = round_words(A.max_width);
-        if (pf == 8) {
-            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 8, 5>(A, x, y, red, s);
-            else launch_pipe_dot<PACKSELL_FMT_E8MY, 8, 5>(A, x, y, red, s);
-        } else if (pf == 10) {
-            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 10, 4>(A, x, y, red, s);
-            else launch_pipe_dot<PACKSELL_FMT_E8MY, 10, 4>(A, x, y, red, s);
-        } else if (pf == 12) {
-            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 12, 4>(A, x, y, red, s);
-            else launch_pipe_dot<PACKSELL_FMT_E8MY, 12, 4>(A, x, y, red, s);
-        } else {
-            if (h) launch_pipe_dot<PACKSELL_FMT_FP16, 16, 3>(A, x, y, red, s);
-            else launch_pipe_dot<PACKSELL_FMT_E8MY, 16, 3>(A, x, y, red, s);
-        }
+        cudaError_t e;
+        if (pf == 8)
+            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 8, 5>(A, x, y, red, s)
+                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 8, 5>(A, x, y, red, s);
+        else if (pf == 10)
+            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 10, 4>(A, x, y, red, s)
+                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 10, 4>(A, x, y, red, s);
+        else if (pf == 12)
+            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 12, 4>(A, x, y, red, s)
+                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 12, 4>(A, x, y, red, s);
+        else
+            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 16, 3>(A, x, y, red, s)
+                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 16, 3>(A, x, y, red, s);
+        if (e != cudaSuccess) return cuda_fail(e, "spmv_dot_f32 (pipelined)");
     } else if (A.p.C == 32) {
         // row-prefetch kernel, rounds fitted to the widest slice
         const bool h = A.p.format == PACKSELL_FMT_FP16;
@@ -1119,9 +1215,11 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
 
 packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
                              const Red &red, cudaStream_t s) {
-    k_spmv_sell<double, true><<<device_sms() * 4, TPB, 0, s>>>(
-        (int)A.n, A.p.C, A.p.sigma, A.offset, (const double *)A.val, A.col, A.perm, A.perm_bytes, x,
-        y, b, red);
+    const cudaError_t e = launch_pdl(k_spmv_sell_dot64, (unsigned)(device_sms() * 4),
+                                     TPB, s, (int)A.n, A.p.C, A.p.sigma, (const int64_t *)A.offset,
+                                     (const double *)A.val, (const int32_t *)A.col,
+                                     (const void *)A.perm, A.perm_bytes, x, y, b, red);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_dot_f64");
     PS_LAUNCH_CHECK("spmv_dot_f64");
     return PACKSELL_OK;
 }

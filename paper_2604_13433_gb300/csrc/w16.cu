@@ -4,7 +4,8 @@
 // of a round loaded at once (16-bit cache-streaming loads, rounds fitted to
 // the widest slice, a constant word stride for C = 32), FP32 fused
 // multiply-adds in stored order: the same chain as the 32-bit words'
-// kernels, on the E4M3 values widened exactly to FP32.
+// kernels, on the E4M3 values widened exactly to FP32. Launched with
+// programmatic dependent launch.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(TPB, MINB)
                const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
                float *__restrict__ y) {
     const int C = C32 ? 32 : Cr;  // a constant word stride when C = 32
+    grid_dep_launch();  // one pass over the rows: signal at block start
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int k = i / C, l = i - k * C;
@@ -43,12 +45,15 @@ __global__ void __launch_bounds__(TPB, MINB)
     const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
     int c = (k_left < blk) ? (int)(blk - k_left) : 0;
     float t = 0.f;
+    if (w <= 0) grid_dep_wait();
     for (int j0 = 0; j0 < w; j0 += PF) {
         const int wr = w - j0;
         uint32_t wd[PF];
 #pragma unroll
         for (int u = 0; u < PF; ++u)
             wd[u] = (u < wr) ? (uint32_t)__ldcs(pp + (C32 ? (j0 + u) * 32 : (int64_t)(j0 + u) * C)) : 0u;
+        // the first round's words load before the wait; x and y after it
+        if (j0 == 0) grid_dep_wait();
         bool f[PF];
         float xv[PF];
 #pragma unroll
@@ -68,7 +73,7 @@ __global__ void __launch_bounds__(TPB, MINB)
 }
 
 template <int PF, int MINB>
-void launch_w16(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+cudaError_t launch_w16(const Matrix &A, const void *perm, int pb, const float *x, float *y,
                 cudaStream_t s) {
     const int sg = A.p.sigma;
     const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
@@ -77,7 +82,8 @@ void launch_w16(const Matrix &A, const void *perm, int pb, const float *x, float
     // other slice heights keep 64-bit word offsets: fewer blocks per SM
     auto kern = pb ? (c32 ? k_spmv_w16<PF, MINB, true, true> : k_spmv_w16<PF, 3, true, false>)
                    : (c32 ? k_spmv_w16<PF, MINB, false, true> : k_spmv_w16<PF, 3, false, false>);
-    kern<<<g, TPB, 0, s>>>((int)A.n, A.p.C, sg, sh, A.p.k_left, A.offset, A.pack16, perm, pb, x, y);
+    return launch_pdl(kern, g, TPB, s, (int)A.n, A.p.C, sg, sh, A.p.k_left,
+                      (const int64_t *)A.offset, (const uint16_t *)A.pack16, perm, pb, x, y);
 }
 
 }  // namespace
@@ -89,9 +95,10 @@ packsell_status spmv_w16_impl(const Matrix &A, const float *x, float *y, cudaStr
     const void *perm = A.p.explicit_perm ? nullptr : A.perm;
     const int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     const int w = A.max_width;
-    if (w <= 8) launch_w16<8, 6>(A, perm, pb, x, y, s);
-    else if (w <= 12) launch_w16<12, 5>(A, perm, pb, x, y, s);
-    else launch_w16<16, 5>(A, perm, pb, x, y, s);
+    const cudaError_t e = w <= 8    ? launch_w16<8, 6>(A, perm, pb, x, y, s)
+                          : w <= 12 ? launch_w16<12, 5>(A, perm, pb, x, y, s)
+                                    : launch_w16<16, 5>(A, perm, pb, x, y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (16-bit words)");
     PS_LAUNCH_CHECK("packsell_spmv (16-bit words)");
     return PACKSELL_OK;
 }

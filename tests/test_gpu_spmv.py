@@ -30,6 +30,7 @@ def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0, rel_tol=Non
     variants = [packsell.SPMV_ROWTHREAD]
     if C == 32 and fmt in ("fp16", "e8my"):
         variants += list(packsell.SPMV_PREFETCH) + list(packsell.SPMV_DUAL) + list(packsell.SPMV_STAGE)
+        variants.append(packsell.SPMV_PDL)
     if C == 32 and csr.n > 0 and fmt in ("fp16", "e8my"):
         variants += list(packsell.SPMV_BULK_VARIANTS)
     if C == 1 and csr.n > 0 and fmt in ("fp16", "e8my"):
@@ -204,6 +205,36 @@ def test_pipelined_variant_short_rows_only():
         B, dev(I.uniform(B.m, seed=2)), reps=2)
 
 
+def test_dependent_launch_chain():
+    """Variant 13 loads its first words before it waits for the previous
+    kernel of its stream. In a chain y_{k+1} = A y_k on one stream each
+    product reads the vector the product before it has just written, and a
+    torch kernel halves the vector between some of them; every step must
+    equal the oracle's FP32 twin applied to the previous step, bit for bit."""
+    need_gpu()
+    packsell = P()
+    csr = I.stencil27(24, seed=5)
+    enc = O.encode(csr, C=32, sigma=256, D=15, fmt=FMT["fp16"])
+    A = encode_gpu(csr, fmt="fp16", C=32, sigma=256, D=15)  # y in original row order
+    packsell.packsell_set_spmv_variant(A, packsell.SPMV_PDL)
+    deq = enc.deq.astype(np.float32)
+    v = I.uniform(csr.m, seed=9)
+    vd = dev(v)
+    outs = []
+    for k in range(8):
+        if k % 3 == 2:
+            vd = vd * 0.5  # exact in FP32
+        vd = packsell.packsell_spmv(A, vd)
+        outs.append(vd)
+    packsell.packsell_check_status(A)
+    for k, yd in enumerate(outs):
+        if k % 3 == 2:
+            v = v * np.float32(0.5)
+        v = O.csr_spmv_fma_f32(csr, deq, v)
+        y = yd.cpu().numpy()
+        assert np.array_equal(y.view(np.uint32), v.view(np.uint32)), f"step {k}"
+
+
 def test_spmv_column_range_limit():
     """m = 2^31 - 1 columns (the format's limit): deltas above 2^30 need the
     31-bit dummy, one row ends at column m - 1. x (8 GB) lives only on the
@@ -296,7 +327,8 @@ def test_tune_spmv_picks_a_variant():
     A = encode_gpu(csr, fmt="fp16")
     x = dev(I.uniform(csr.m, seed=1))
     times = packsell.packsell_tune_spmv(A, x, reps=5)
-    assert set(times) == set(range(1, 11)) and all(t > 0 for t in times.values())
+    # 11 needs C = 1 and 12 slices of at most 16 words
+    assert set(times) == set(range(1, 11)) | {13} and all(t > 0 for t in times.values())
     y = packsell.packsell_spmv(A, x).cpu().numpy()  # variant 0 = tuned choice
     enc = O.encode(csr, fmt=O.FMT_FP16)
     twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), x.cpu().numpy())
