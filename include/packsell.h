@@ -231,7 +231,10 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
 #define PACKSELL_SPMV_VARIANTS 13
 
 /* SpMV kernel variants (all compute the same bits):
- *   0 auto (the plan's or the tuner's choice),
+ *   0 auto: the tuner's choice once packsell_tune_spmv has run, else by
+ *     shape: 11 for C = 1 PackSELL; for C = 32 PackSELL 12 when every slice
+ *     holds at most 16 words, 4 when padding exceeds 1/8 of the stored
+ *     words, otherwise 13; 1 for everything else,
  *   1 thread-per-row with direct loads (the paper's mapping, §5.1.1),
  *   2, 3, 4 bulk-staged: every warp streams its contiguous range of slices
  *     through a circular ring of shared-memory chunks filled by

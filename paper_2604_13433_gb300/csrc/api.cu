@@ -202,9 +202,15 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     const int64_t *offs = (const int64_t *)src;
     if (offs[0] != 0 || offs[h.n_slices] != h.n_words)
         return fail(PACKSELL_ERR_CORRUPT, "packsell_import: offsets do not match the word count");
-    for (int64_t k = 0; k < h.n_slices; ++k)
+    int64_t widest = 0;
+    for (int64_t k = 0; k < h.n_slices; ++k) {
         if (offs[k + 1] < offs[k] || (offs[k + 1] - offs[k]) % p.C)
             return fail(PACKSELL_ERR_CORRUPT, "packsell_import: offsets not C-aligned");
+        widest = std::max<int64_t>(widest, (offs[k + 1] - offs[k]) / p.C);
+    }
+    // kernels size their rounds by the widest slice: it must be the offsets' own
+    if (widest != h.max_width)
+        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: widest slice does not match the offsets");
 
     Matrix *A = new Matrix();
     A->n = h.n;

@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "device.cuh"
@@ -185,7 +186,10 @@ __global__ void __launch_bounds__(CW * 32, 4)
 
 template <int FMT, bool PERM>
 int csr_blocks() {
-    static int blocks = 0;  // persistent grid: every block resident at once
+    // persistent grid: every block resident at once (cached per process; calls
+    // from several host threads may compute it together and store the same value)
+    static std::atomic<int> cached{0};
+    int blocks = cached.load(std::memory_order_relaxed);
     if (!blocks) {
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -194,6 +198,7 @@ int csr_blocks() {
                 cudaSuccess)
             return 0;
         blocks = sms * std::max(per, 1);
+        cached.store(blocks, std::memory_order_relaxed);
     }
     return blocks;
 }

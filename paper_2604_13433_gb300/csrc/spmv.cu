@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "device.cuh"
 #include "internal.h"
@@ -310,13 +311,17 @@ __global__ void __launch_bounds__(TPB, MINB)
 template <int FMT, int PF, int MINB>
 packsell_status launch_dual(const Matrix &A, const void *perm, int pb, const float *x, float *y,
                             cudaStream_t s) {
-    static int blocks = 0;  // persistent grid: every block resident at once
+    // persistent grid: every block resident at once (cached per process; calls
+    // from several host threads may compute it together and store the same value)
+    static std::atomic<int> cached{0};
+    int blocks = cached.load(std::memory_order_relaxed);
     if (!blocks) {
         int dev = 0, sms = 0, per = 0;
         PS_CUDA(cudaGetDevice(&dev));
         PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_spmv_dual<FMT, PF, MINB>, TPB, 0));
         blocks = sms * (per > 0 ? per : 1);
+        cached.store(blocks, std::memory_order_relaxed);
     }
     const int sg = A.p.sigma;
     const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
@@ -380,7 +385,9 @@ packsell_status launch_prefetch_pdl(const Matrix &A, const void *perm, int pb, c
 
 template <int FMT, int PF, int MINB, bool PERM>
 int pipe_blocks() {
-    static int blocks = 0;  // persistent grid: every block resident at once
+    // persistent grid: every block resident at once (cached as in launch_dual)
+    static std::atomic<int> cached{0};
+    int blocks = cached.load(std::memory_order_relaxed);
     if (!blocks) {
         int dev = 0, sms = 0, per = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -389,6 +396,7 @@ int pipe_blocks() {
                 &per, k_spmv_pipe<FMT, PF, MINB, false, PERM>, TPB, 0) != cudaSuccess)
             return 0;
         blocks = sms * std::max(per, 1);
+        cached.store(blocks, std::memory_order_relaxed);
     }
     return blocks;
 }
@@ -904,7 +912,12 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
         A.part_blocks[v] = blocks;
         A.part_warps[v] = G;
     }
-    if (A.part[0]) A.auto_variant = 2;
+    // untuned default (variant 0), by matrix shape: every slice within one
+    // round -> the pipelined kernel; padding above 1/8 of the words (uneven
+    // rows) -> the TMA-staged variant 4; otherwise -> variant 13
+    if (A.max_width <= 16) A.auto_variant = 12;
+    else if (A.n_pad * 8 > A.n_words && A.part[2]) A.auto_variant = 4;
+    else A.auto_variant = 13;
     return plan_stage(A, s);
 }
 

@@ -135,3 +135,11 @@ def test_export_import_roundtrip_and_corruption():
     assert e.value.code == 9
     with pytest.raises(packsell.PackSELLError):
         packsell.packsell_import(blob[: len(blob) // 2])
+    # a header whose widest slice disagrees with the offsets (the kernels size
+    # their rounds by it): int32 at byte 96 of the header
+    assert int(np.frombuffer(blob, np.int32, 1, 96)[0]) == A.max_width
+    bad = bytearray(blob)
+    bad[96:100] = np.int32(1).tobytes()
+    with pytest.raises(packsell.PackSELLError) as e:
+        packsell.packsell_import(bytes(bad))
+    assert e.value.code == 9
