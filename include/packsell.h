@@ -348,6 +348,19 @@ packsell_status packsell_pattern_outer_f64(const packsell_matrix *A, double alph
                                            const double *u, const double *v, double *out,
                                            void *stream);
 
+/* Backward of y = A x (the adjoint of the §4.4 product; the paper
+ * differentiates nothing). Given x (float [m]) and dy = dL/dy (float [n]),
+ * both in original order:
+ *   dx   : NULL (skipped) or float [m], out: A^T dy, overwritten, with
+ *          atomic adds as in packsell_spmv_transpose
+ *   dval : NULL (skipped) or float [nnz], out: dL/da_ij = dy_i x_j at the
+ *          CSR position of a_ij (needs keep_rowptr = 1; gradient through
+ *          the quantiser taken as the identity)
+ * Asynchronous on `stream`. Errors: those of packsell_spmv_transpose and
+ * packsell_pattern_outer, which it runs. */
+packsell_status packsell_spmv_backward(const packsell_matrix *A, const float *x, const float *dy,
+                                       float *dx, float *dval, void *stream);
+
 
 /* ---------------------------------------------------------------------- */
 /* Solvers (§5.2.2): FP64 PCG and the mixed-precision inner-outer CG        */
@@ -414,6 +427,24 @@ packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matr
                              const double *inv_diag, const double *b, double *x,
                              const packsell_solve_opts *opts, void *work, size_t work_bytes,
                              double *h_hist, packsell_solve_result *result, void *stream);
+
+/* Backward of x = A^-1 b for SPD A: the adjoint solve A lam = dL/dx (A is
+ * symmetric, so A^T = A), with the operators and options of packsell_pcg,
+ * from lam = 0; then dL/db = lam and dL/da_ij = -lam_i x_j on the pattern.
+ *   x      : double [n], the forward solution
+ *   dL_dx  : double [n]
+ *   dL_db  : double [n], out: lam
+ *   dL_dA  : NULL (skipped) or double [nnz], out in CSR order (A_outer
+ *            encoded with keep_rowptr = 1), written on `stream` after the
+ *            solve
+ * Other arguments as packsell_pcg. The solve SYNCHRONISES; its status is
+ * returned (NOT_CONVERGED leaves the last iterate in dL_db and skips dL_dA). */
+packsell_status packsell_pcg_backward(const packsell_matrix *A_outer,
+                                      const packsell_matrix *A_inner, const double *inv_diag,
+                                      const double *x, const double *dL_dx, double *dL_db,
+                                      double *dL_dA, const packsell_solve_opts *opts, void *work,
+                                      size_t work_bytes, packsell_solve_result *result,
+                                      void *stream);
 
 /* packsell_pcg without any device allocation. The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory when

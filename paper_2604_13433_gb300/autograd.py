@@ -3,15 +3,14 @@
 Argument marshalling around the C ABI: every product, transpose, pattern
 gradient and solve runs in the CUDA library.
 
-* :func:`spmv` - y = A x. Backward: dx = A^T dy (packsell_spmv_transpose) and,
+* :func:`spmv` - y = A x. Backward (packsell_spmv_backward): dx = A^T dy and,
   when the CSR values A was encoded from require grad, dL/da_ij = dy_i x_j on
-  the pattern (packsell_pattern_outer); the quantiser is passed straight
-  through (dq(v)/dv = 1).
+  the pattern; the quantiser is passed straight through (dq(v)/dv = 1).
 * :func:`solve` - x = A^-1 b for SPD A given as CSR (rowptr, col, values) on
   the device, by packsell_pcg (FP64 PCG, or the mixed-precision inner-outer
-  CG with a PackSELL inner matrix). Backward: one adjoint solve A lam = dL/dx
-  (A is symmetric), then dL/db = lam and dL/da_ij = -lam_i x_j on the pattern
-  (packsell_pattern_outer_f64). Gradients with respect to parameters that
+  CG with a PackSELL inner matrix). Backward (packsell_pcg_backward): one
+  adjoint solve A lam = dL/dx (A is symmetric), then dL/db = lam and
+  dL/da_ij = -lam_i x_j on the pattern. Gradients with respect to parameters that
   build the values (face coefficients, say) follow by autograd through the
   user's own assembly of the values.
 """
@@ -33,13 +32,13 @@ class _SpMV(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dy):
         (x,) = ctx.saved_tensors
-        A = ctx.A
-        dy = dy.contiguous().float()
-        dval = dx = None
-        if ctx.needs_input_grad[0]:
-            dval = ps.packsell_pattern_outer(A, 1.0, dy, x).to(ctx.val_dtype)
-        if ctx.needs_input_grad[1]:
-            dx = ps.packsell_spmv_transpose(A, dy)
+        need_dval, need_dx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_dval or need_dx):
+            return None, None, None
+        dx, dval = ps.packsell_spmv_backward(ctx.A, x, dy.contiguous().float(),
+                                             need_dx=need_dx, need_dval=need_dval)
+        if dval is not None:
+            dval = dval.to(ctx.val_dtype)
         return dval, dx, None
 
 
@@ -75,12 +74,11 @@ class _Solve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         (x,) = ctx.saved_tensors
-        lam, _ = ps.packsell_pcg(ctx.A64, g.detach().double().contiguous(), **ctx.kw)
-        dval = db = None
-        if ctx.needs_input_grad[0]:
-            dval = ps.packsell_pattern_outer_f64(ctx.A64, -1.0, lam, x).to(ctx.val_dtype)
-        if ctx.needs_input_grad[1]:
-            db = lam.to(ctx.b_dtype)
+        need_dA = ctx.needs_input_grad[0]
+        lam, dA, _ = ps.packsell_pcg_backward(ctx.A64, x, g.detach().double().contiguous(),
+                                              need_dA=need_dA, **ctx.kw)
+        dval = dA.to(ctx.val_dtype) if need_dA else None
+        db = lam.to(ctx.b_dtype) if ctx.needs_input_grad[1] else None
         return dval, db, None, None, None
 
 

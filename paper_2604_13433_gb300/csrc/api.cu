@@ -396,6 +396,24 @@ packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, co
     return pattern_outer_impl(*M(A), alpha, u, v, out, as_stream(stream));
 }
 
+packsell_status packsell_spmv_backward(const packsell_matrix *A, const float *x, const float *dy,
+                                       float *dx, float *dval, void *stream) {
+    clear_error();
+    if (!A || (M(A)->n > 0 && !dy) || (dval && M(A)->m > 0 && !x))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_backward: NULL argument");
+    if (no_w16(*M(A), "packsell_spmv_backward") != PACKSELL_OK) return PACKSELL_ERR_INVALID_ARG;
+    if (dval && !M(A)->rowptr)  // checked before dx is written
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_spmv_backward: dval needs a matrix encoded with keep_rowptr");
+    cudaStream_t s = as_stream(stream);
+    if (dx) {
+        const packsell_status st = spmv_t_impl(*M(A), dy, dx, s);
+        if (st != PACKSELL_OK) return st;
+    }
+    if (dval) return pattern_outer_impl(*M(A), 1.0f, dy, x, dval, s);
+    return PACKSELL_OK;
+}
+
 packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream) {
     clear_error();
     if (!A || (M(A)->n > 0 && !out)) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_inv_diag: NULL argument");
@@ -493,6 +511,27 @@ packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matr
     if (!A_outer || !opts) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: NULL argument");
     return solve_impl(M(A_outer), A_inner ? M(A_inner) : nullptr, inv_diag, b, x, *opts, work,
                       work_bytes, h_hist, result, as_stream(stream));
+}
+
+packsell_status packsell_pcg_backward(const packsell_matrix *A_outer,
+                                      const packsell_matrix *A_inner, const double *inv_diag,
+                                      const double *x, const double *dL_dx, double *dL_db,
+                                      double *dL_dA, const packsell_solve_opts *opts, void *work,
+                                      size_t work_bytes, packsell_solve_result *result,
+                                      void *stream) {
+    clear_error();
+    if (!A_outer || !opts || (M(A_outer)->n > 0 && (!x || !dL_dx || !dL_db)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg_backward: NULL argument");
+    const Matrix &Ao = *M(A_outer);
+    if (dL_dA && (Ao.p.format != PACKSELL_FMT_SELL_F64 || !Ao.rowptr))
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_pcg_backward: dL_dA needs a SELL_F64 A_outer encoded with keep_rowptr");
+    cudaStream_t s = as_stream(stream);
+    if (Ao.n > 0) PS_CUDA(cudaMemsetAsync(dL_db, 0, sizeof(double) * (size_t)Ao.n, s));
+    packsell_status st = solve_impl(&Ao, A_inner ? M(A_inner) : nullptr, inv_diag, dL_dx, dL_db,
+                                    *opts, work, work_bytes, nullptr, result, s);
+    if (st != PACKSELL_OK || !dL_dA) return st;
+    return pattern_outer_f64_impl(Ao, -1.0, dL_db, x, dL_dA, s);
 }
 
 packsell_status packsell_pcg_noalloc(const packsell_matrix *A_outer,

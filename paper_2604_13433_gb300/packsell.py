@@ -95,6 +95,9 @@ SIGNATURES = {
     "packsell_pcg": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "packsell_pattern_outer_f64": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
+    "packsell_spmv_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "packsell_pcg_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t,
+                                             _P, _P]),
     "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
     "packsell_storage_rows": (ctypes.c_int, [_P, _P, _P]),
     "packsell_spmv_x16": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -216,7 +219,9 @@ def packsell_encode_csr(csr, device="cuda", **kw) -> PackSELLMatrix:
 
 
 def packsell_set_spmv_variant(A: PackSELLMatrix, variant: int) -> None:
-    """0 auto, 1 thread-per-row, 2-4 bulk-staged configurations, 5-6 row prefetch, 7-8 dual-row, 9-10 stage-planned."""
+    """0 auto, 1 thread-per-row, 2-4 bulk-staged configurations, 5-6 row prefetch,
+    7-8 dual-row, 9-10 stage-planned, 11 CSR order (C = 1), 12 pipelined (slices of
+    at most 16 words), 13 variant 5 with programmatic dependent launch."""
     _check(lib().packsell_set_spmv_variant(A.handle, int(variant)))
 
 
@@ -294,6 +299,20 @@ def packsell_pattern_outer(A: PackSELLMatrix, alpha: float, u: torch.Tensor, v: 
                                         _dev(v, torch.float32, "v", A.m),
                                         _dev(out, torch.float32, "out", A.nnz), _stream(stream)))
     return out
+
+
+def packsell_spmv_backward(A: PackSELLMatrix, x: torch.Tensor, dy: torch.Tensor, *,
+                           need_dx: bool = True, need_dval: bool = True, stream=None):
+    """Backward of y = A x: (dx = A^T dy, dval = dy_i x_j on the pattern in CSR
+    order), either None when not asked for (float32)."""
+    dx = torch.empty(A.m, dtype=torch.float32, device=dy.device) if need_dx else None
+    dval = torch.empty(A.nnz, dtype=torch.float32, device=dy.device) if need_dval else None
+    _check(lib().packsell_spmv_backward(
+        A.handle, _dev(x, torch.float32, "x", A.m) if need_dval else None,
+        _dev(dy, torch.float32, "dy", A.n),
+        dx.data_ptr() if dx is not None else None,
+        dval.data_ptr() if dval is not None else None, _stream(stream)))
+    return dx, dval
 
 
 def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
@@ -443,6 +462,34 @@ def packsell_pcg(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tensor | Non
     if check and code != 0:
         raise PackSELLError(code, lib().packsell_last_error().decode())
     return x, info
+
+
+def packsell_pcg_backward(A_outer: PackSELLMatrix, x: torch.Tensor, dL_dx: torch.Tensor, *,
+                          A_inner: PackSELLMatrix | None = None,
+                          inv_diag: torch.Tensor | None = None, rtol: float = 1e-10,
+                          m_in: int = 0, max_iters: int = 1000, check_every: int | None = None,
+                          use_graph: bool = True, need_dA: bool = True, stream=None):
+    """Backward of x = A^-1 b (A SPD): returns (dL_db, dL_dA, info); dL_db is
+    the adjoint solution lam of A lam = dL/dx, dL_dA = -lam_i x_j on the
+    pattern in CSR order (float64; None without need_dA)."""
+    n = A_outer.n
+    if check_every is None:
+        check_every = 1 if m_in > 0 else 10
+    opts = SolveOpts(float(rtol), int(m_in), int(max_iters), int(check_every), int(use_graph))
+    res = SolveResult()
+    db = torch.empty(n, dtype=torch.float64, device=dL_dx.device)
+    dA = torch.empty(A_outer.nnz, dtype=torch.float64, device=dL_dx.device) if need_dA else None
+    code = lib().packsell_pcg_backward(
+        A_outer.handle, A_inner.handle if A_inner is not None else None,
+        _dev(inv_diag, torch.float64, "inv_diag", n) if inv_diag is not None else None,
+        _dev(x, torch.float64, "x", n), _dev(dL_dx, torch.float64, "dL_dx", n), db.data_ptr(),
+        dA.data_ptr() if dA is not None else None, ctypes.byref(opts), None, 0, ctypes.byref(res),
+        _stream(stream))
+    info = {"iters": res.iters, "inner_iters": res.inner_iters, "relres": res.relres,
+            "relres_true": res.relres_true, "seconds": res.seconds,
+            "status": STATUS.get(code, str(code))}
+    _check(code)
+    return db, dA, info
 
 
 def packsell_pcg_noalloc(A_outer: PackSELLMatrix, b: torch.Tensor, x: torch.Tensor, *,

@@ -100,3 +100,48 @@ def test_solve_gradients_match_oracle_and_fd(m_in, fmt, D):
             vals.append(np.sum((x2 - xt_h) ** 2))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert np.isclose(theta.grad[f].item(), fd, rtol=1e-5, atol=1e-8)
+
+
+def test_backward_entry_points():
+    """packsell_spmv_backward and packsell_pcg_backward called directly: either
+    output alone, agreement with the calls they compose, and the keep_rowptr
+    requirement refused before anything is written."""
+    need_gpu()
+    ps = P()
+    csr = I.random_csr(200, 180, 0.04, seed=21)
+    A = ps.packsell_encode_csr(csr, fmt="fp16", keep_rowptr=True)
+    x = dev(I.uniform(180, seed=22))
+    dy = dev(I.uniform(200, seed=23))
+    dx, dval = ps.packsell_spmv_backward(A, x, dy)
+    dx_only, none1 = ps.packsell_spmv_backward(A, x, dy, need_dval=False)
+    none2, dval_only = ps.packsell_spmv_backward(A, x, dy, need_dx=False)
+    assert none1 is None and none2 is None
+    assert torch.equal(dval, dval_only)
+    row = np.repeat(np.arange(200), csr.row_lengths())
+    dy_h, x_h = dy.cpu().numpy(), x.cpu().numpy()
+    assert np.array_equal(dval.cpu().numpy(), (dy_h[row] * x_h[csr.col]).astype(np.float32))
+    deq = O.encode(csr, C=32, sigma=256, D=15, fmt=O.FMT_FP16).deq
+    dx_ref = _dense(csr, deq).T @ dy_h.astype(np.float64)
+    for d in (dx, dx_only):  # atomic adds: compared within FP32 rounding
+        assert np.allclose(d.cpu().numpy(), dx_ref, rtol=1e-5, atol=1e-5)
+    B = ps.packsell_encode_csr(csr, fmt="fp16")  # no keep_rowptr
+    with pytest.raises(ps.PackSELLError) as e:
+        ps.packsell_spmv_backward(B, x, dy)
+    assert e.value.code == 1
+
+    a, _ = I.poisson5_varcoef(12, seed=24)
+    A64 = ps.packsell_encode_csr(a, fmt="sell_f64", keep_rowptr=True)
+    b = dev(I.uniform(a.n, seed=25).astype(np.float64))
+    xs, _ = ps.packsell_pcg(A64, b, rtol=1e-12)
+    g = dev(I.normal(a.n, seed=26))
+    lam_ref, _ = ps.packsell_pcg(A64, g, rtol=1e-12)
+    lam, dA, info = ps.packsell_pcg_backward(A64, xs, g, rtol=1e-12)
+    assert info["status"] == "OK"
+    assert torch.equal(lam, lam_ref)  # the same solve from zero
+    assert torch.equal(dA, ps.packsell_pattern_outer_f64(A64, -1.0, lam_ref, xs))
+    lam2, none3, _ = ps.packsell_pcg_backward(A64, xs, g, rtol=1e-12, need_dA=False)
+    assert none3 is None and torch.equal(lam2, lam_ref)
+    A64n = ps.packsell_encode_csr(a, fmt="sell_f64")  # no keep_rowptr
+    with pytest.raises(ps.PackSELLError) as e:
+        ps.packsell_pcg_backward(A64n, xs, g, rtol=1e-12)
+    assert e.value.code == 1
