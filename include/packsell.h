@@ -160,6 +160,36 @@ packsell_status packsell_encode(const packsell_params *params, int64_t n, int64_
                                 const void *val, int32_t val_is_f64, void *stream,
                                 packsell_matrix **out);
 
+/* Locality reordering before encoding (host arrays, host code; no device is
+ * needed). §4.3 spends a dummy word wherever two consecutive columns of a
+ * row are 2^D or more apart; the paper names a locality-improving ordering as
+ * the way to fewer dummies and leaves it to future work (§7). Grouping rows
+ * of similar length into the same slices also cuts SELL padding at small
+ * sigma.
+ *
+ * packsell_reorder_rcm: reverse Cuthill-McKee order of the symmetrised
+ * pattern A + A^T of a square CSR matrix (rowptr int64 [n+1], col int32
+ * [nnz]; diagonal and duplicate entries ignored). Each connected component
+ * starts from a pseudo-peripheral vertex (George-Liu search from a vertex of
+ * least degree); a breadth-first search appends every vertex's unvisited
+ * neighbours in increasing degree, ties by index; the order is reversed.
+ * perm: int32 [n], out: perm[k] = the original row placed at position k.
+ * Errors: INVALID_ARG (NULL, n out of range, bad rowptr), RANGE (a column
+ * outside [0, n)), NO_MEMORY (host). */
+packsell_status packsell_reorder_rcm(int64_t n, const int64_t *rowptr, const int32_t *col,
+                                     int32_t *perm);
+
+/* B = P A P^T on host CSR arrays: row k of B is row perm[k] of A, column j
+ * becomes inv(perm)[j], columns sorted within each row; values (float, or
+ * double with val_is_f64 = 1) move with them. val and out_val are both NULL
+ * (pattern only) or both set. out_rowptr int64 [n+1], out_col int32 [nnz],
+ * out_val [nnz]. Solving with B: b_new = b[perm], x = x_new scattered back
+ * (x[perm[k]] = x_new[k]). Errors: INVALID_ARG (NULL, perm not a
+ * permutation), RANGE (a column outside [0, n)), NO_MEMORY (host). */
+packsell_status packsell_permute_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
+                                     const void *val, int32_t val_is_f64, const int32_t *perm,
+                                     int64_t *out_rowptr, int32_t *out_col, void *out_val);
+
 /* Free the matrix (synchronises the device first). NULL is accepted. */
 packsell_status packsell_destroy(packsell_matrix *A);
 

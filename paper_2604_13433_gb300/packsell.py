@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -96,6 +97,8 @@ SIGNATURES = {
     "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "packsell_pattern_outer_f64": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
     "packsell_spmv_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "packsell_reorder_rcm": (ctypes.c_int, [_I64, _P, _P, _P]),
+    "packsell_permute_csr": (ctypes.c_int, [_I64, _P, _P, _P, _I32, _P, _P, _P, _P]),
     "packsell_pcg_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t,
                                              _P, _P]),
     "packsell_inv_diag": (ctypes.c_int, [_P, _P, _P]),
@@ -208,6 +211,48 @@ def packsell_encode(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, 
         _dev(val, val.dtype, "val", nnz) if nnz else None, int(val.dtype == torch.float64),
         _stream(stream), ctypes.byref(h)))
     return PackSELLMatrix(h.value)
+
+
+def _host(a: np.ndarray, dtype, name: str) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != dtype:
+        raise TypeError(f"{name} must be {np.dtype(dtype)}, got {a.dtype}")
+    return a
+
+
+def packsell_reorder_rcm(rowptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """Reverse Cuthill-McKee order of a square host CSR pattern (host code):
+    perm[k] = the original row placed at position k (int32)."""
+    rowptr, col = _host(rowptr, np.int64, "rowptr"), _host(col, np.int32, "col")
+    n = rowptr.size - 1
+    perm = np.empty(max(n, 0), np.int32)
+    _check(lib().packsell_reorder_rcm(n, rowptr.ctypes.data, col.ctypes.data, perm.ctypes.data))
+    return perm
+
+
+def packsell_permute_csr(rowptr: np.ndarray, col: np.ndarray, val: np.ndarray | None,
+                         perm: np.ndarray):
+    """B = P A P^T on host CSR arrays (host code): returns (rowptr, col, val)
+    of B; val is None when not given."""
+    rowptr, col = _host(rowptr, np.int64, "rowptr"), _host(col, np.int32, "col")
+    perm = _host(perm, np.int32, "perm")
+    n = rowptr.size - 1
+    if perm.size != n:
+        raise ValueError(f"perm must have {n} elements")
+    f64 = 0
+    if val is not None:
+        val = np.ascontiguousarray(val)
+        if val.dtype not in (np.float32, np.float64):
+            raise TypeError("val must be float32 or float64")
+        f64 = int(val.dtype == np.float64)
+    orp = np.empty(n + 1, np.int64)
+    ocl = np.empty(col.size, np.int32)
+    ovl = np.empty(col.size, val.dtype) if val is not None else None
+    _check(lib().packsell_permute_csr(n, rowptr.ctypes.data, col.ctypes.data,
+                                      val.ctypes.data if val is not None else None, f64,
+                                      perm.ctypes.data, orp.ctypes.data, ocl.ctypes.data,
+                                      ovl.ctypes.data if ovl is not None else None))
+    return orp, ocl, ovl
 
 
 def packsell_encode_csr(csr, device="cuda", **kw) -> PackSELLMatrix:
@@ -393,8 +438,6 @@ def packsell_import(blob: bytes, stream=None) -> PackSELLMatrix:
 def packsell_arrays(A: PackSELLMatrix):
     """Host copies of the encoded arrays: dict with offset, perm, and pack
     (PackSELL) or val/col (SELL), parsed from the export blob."""
-    import numpy as np
-
     blob = packsell_export(A)
     hdr = 8 + 3 * 8 + ctypes.sizeof(Params) + 4 * 8 + 2 * 4
     pos = hdr
