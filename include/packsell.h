@@ -108,7 +108,9 @@ typedef struct packsell_params {
     int64_t k_left;        /* lower bandwidth used in Eq. 4; -1 computes it */
 } packsell_params;
 
-/* Defaults: C = 32, sigma = 256, D = 15, FP16, implicit permutation,
+/* Defaults (the parameters of §4.2-§4.3; C = 32, sigma = 256 and FP16 with
+ * D = 15 are the paper's FP16 configuration, §5.1.1): C = 32, sigma = 256,
+ * D = 15, FP16, implicit permutation,
  * keep_rowptr = 0, k_left = -1. */
 void packsell_params_default(packsell_params *p);
 
@@ -179,7 +181,8 @@ packsell_status packsell_encode(const packsell_params *params, int64_t n, int64_
 packsell_status packsell_reorder_rcm(int64_t n, const int64_t *rowptr, const int32_t *col,
                                      int32_t *perm);
 
-/* B = P A P^T on host CSR arrays: row k of B is row perm[k] of A, column j
+/* The reordering of §7's future work applied (§4.3 dummies depend on the
+ * column order). B = P A P^T on host CSR arrays: row k of B is row perm[k] of A, column j
  * becomes inv(perm)[j], columns sorted within each row; values (float, or
  * double with val_is_f64 = 1) move with them. val and out_val are both NULL
  * (pattern only) or both set. out_rowptr int64 [n+1], out_col int32 [nnz],
@@ -190,17 +193,19 @@ packsell_status packsell_permute_csr(int64_t n, const int64_t *rowptr, const int
                                      const void *val, int32_t val_is_f64, const int32_t *perm,
                                      int64_t *out_rowptr, int32_t *out_col, void *out_val);
 
-/* Free the matrix (synchronises the device first). NULL is accepted. */
+/* Free the matrix (synchronises the device first). NULL is accepted.
+ * Housekeeping with no counterpart in the paper. */
 packsell_status packsell_destroy(packsell_matrix *A);
 
 packsell_status packsell_get_info(const packsell_matrix *A, packsell_info *info);
 
-/* Serialise to a host blob: header, offset, perm, then pack (or val, col).
+/* Serialise the stored arrays of §4.3 (no counterpart in the paper) to a
+ * host blob: header, offset, perm, then pack (or val, col).
  * With h_blob == NULL only *bytes is set. Synchronises `stream`. */
 packsell_status packsell_export(const packsell_matrix *A, void *h_blob, size_t *bytes,
                                 void *stream);
 
-/* Rebuild a matrix from packsell_export's blob. The blob is validated on the
+/* Rebuild a matrix (§4.3's arrays) from packsell_export's blob. The blob is validated on the
  * device (every row decoded, columns checked against m, value words counted
  * against nnz) before the call returns; a bad blob gives CORRUPT and no
  * matrix. Synchronises `stream`. */
@@ -211,16 +216,17 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 /* Products (§4.4 PackSELL SpMV; §3 SELL SpMV)                              */
 /* ---------------------------------------------------------------------- */
 
-/* y = A x. x: float [m], y: float [n] (original order, or storage order with
- * explicit_perm). FP32 accumulation; each row is summed by one thread in
- * stored order with fused multiply-adds, so the result is bitwise
- * reproducible. Words with flag 0 (dummies, padding) read no x and add
+/* y = A x (Eq. 1) by the §4.4 algorithm. x: float [m], y: float [n]
+ * (original order, or storage order with explicit_perm). FP32
+ * accumulation; each row is summed as one chain of fused multiply-adds in
+ * stored order, so the result is bitwise reproducible. Words with flag 0 (dummies, padding) read no x and add
  * nothing. Works for PackSELL and SELL_F32 matrices. No allocation. */
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
                               void *stream);
 
-/* y = A x from and to host memory: enqueues on `stream` the copy of h_x
- * (float [m], host; pinned memory lets the copy run asynchronously) into the
+/* y = A x (Eq. 1, the §4.4 algorithm) from and to host memory: enqueues on
+ * `stream` the copy of h_x (float [m], host; pinned memory lets the copy run
+ * asynchronously) into the
  * caller's device buffer d_x, packsell_spmv(A, d_x, d_y), and the copy of
  * d_y (float [n], device) into h_y (host). The caller owns all four buffers
  * and must keep them until the stream reaches the end of the call; h_y is
@@ -240,7 +246,8 @@ packsell_status packsell_spmv_host(const packsell_matrix *A, const float *h_x, f
 packsell_status packsell_spmv_x16(const packsell_matrix *A, const uint16_t *x, uint16_t *y,
                                   void *stream);
 
-/* y = A x in double for a SELL_F64 matrix (the FP64 outer operator). */
+/* y = A x in double for a SELL_F64 matrix (§3's SELL-C-sigma; the FP64
+ * operator of §5.2.2's outer iteration). */
 packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
                                   void *stream);
 
@@ -306,7 +313,8 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     packsell_import returns and no product writes it (PackSELL, C = 32). */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
-/* Autotune the SpMV variant for this matrix: time every available variant
+/* Autotune the SpMV variant (the §4.4 product in several kernel mappings;
+ * no counterpart in the paper) for this matrix: time every available variant
  * (`reps` launches each after a warm-up, CUDA events on `stream`) on the
  * caller's x [m] and y [n], and make variant 0 run the fastest. Writes y.
  * Synchronises `stream`. If h_times is not NULL it receives the average
@@ -315,7 +323,8 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
                                    float *h_times, void *stream);
 
-/* Read and clear the matrix's device status word (synchronises `stream`).
+/* Housekeeping (no counterpart in the paper): read and clear the matrix's
+ * device status word (synchronises `stream`).
  * Returns PACKSELL_ERR_TIMEOUT if a kernel's bounded wait on a shared-memory
  * stage ran out since the last check (the kernel then skipped the rest of
  * its work), else PACKSELL_OK. */
@@ -329,7 +338,8 @@ packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
 typedef struct packsell_batch packsell_batch; /* opaque plan */
 
-/* Build a plan for y_i = A_i x_i, i < count. A: host array of PackSELL
+/* Many §4.4 products in one launch (the paper runs one matrix at a time).
+ * Build a plan for y_i = A_i x_i, i < count. A: host array of PackSELL
  * matrices with C = 32 (FP16 and E8MY may be mixed); x, y: host arrays of
  * device pointers (x_i float [m_i], y_i float [n_i]) bound to the plan. The
  * plan uploads one descriptor per matrix and a work list of (matrix, slice
@@ -340,12 +350,12 @@ packsell_status packsell_batch_create(int32_t count, const packsell_matrix *cons
                                       const float *const *x, float *const *y, void *stream,
                                       packsell_batch **out);
 
-/* One launch computing every y_i = A_i x_i of the plan (asynchronous; no
+/* One launch computing every y_i = A_i x_i (§4.4) of the plan (asynchronous; no
  * allocation, so it can be captured in a CUDA graph). Each row is summed as
  * packsell_spmv sums it (same bits). */
 packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream);
 
-/* Work-list statistics: total stored words, algorithmic bytes of one launch
+/* Work-list statistics of a batch plan (no counterpart in the paper): total stored words, algorithmic bytes of one launch
  * (words, offsets, perm, x and y once), number of work items. */
 packsell_status packsell_batch_info(const packsell_batch *B, int64_t *words, int64_t *bytes,
                                     int32_t *items);
@@ -356,13 +366,15 @@ packsell_status packsell_batch_destroy(packsell_batch *B);
 /* Backward (adjoint) products                                              */
 /* ---------------------------------------------------------------------- */
 
-/* dx = A^T dy (float [m]), written from the packed layout with atomic adds:
+/* The adjoint of Eq. 1 over the §4.3 layout: dx = A^T dy (float [m]),
+ * written from the packed layout with atomic adds:
  * the result is overwritten (not accumulated) and its rounding depends on
  * the order of the adds. */
 packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *dy,
                                         float *dx, void *stream);
 
-/* out[q] = alpha * u_i * v_j for every stored nonzero a_ij, with q its CSR
+/* The gradient of Eq. 1 with respect to the stored values: out[q] =
+ * alpha * u_i * v_j for every stored nonzero a_ij, with q its CSR
  * position. u: float [n] (original row order), v: float [m], out: float
  * [nnz]. This is dL/dA on the pattern for y = A x (u = dL/dy, v = x,
  * alpha = 1) and for x = A^-1 b (u = adjoint solution, v = x, alpha = -1).
@@ -370,7 +382,8 @@ packsell_status packsell_spmv_transpose(const packsell_matrix *A, const float *d
 packsell_status packsell_pattern_outer(const packsell_matrix *A, float alpha, const float *u,
                                        const float *v, float *out, void *stream);
 
-/* out[q] = alpha * u_i * v_j in double for a SELL_F64 matrix encoded with
+/* As packsell_pattern_outer, for the §5.2.2 solve: out[q] = alpha * u_i *
+ * v_j in double for a SELL_F64 matrix encoded with
  * keep_rowptr = 1 (u: double [n], v: double [m], out: double [nnz], CSR
  * order): dL/dA on the pattern of x = A^-1 b is pattern_outer(-1, lam, x)
  * with lam the adjoint solution of A^T lam = dL/dx. */
@@ -415,7 +428,8 @@ typedef struct packsell_solve_result {
     double seconds;      /* device time of the solve (CUDA events) */
 } packsell_solve_result;
 
-/* out[i] = 1 / a_ii (double [n]) for a square SELL_F64 matrix, in the
+/* The Jacobi preconditioner of §5.2 (diagonal scaling): out[i] = 1 / a_ii
+ * (double [n]) for a square SELL_F64 matrix, in the
  * original row order: the Jacobi preconditioner of packsell_pcg. Rows whose
  * diagonal is missing or zero get 1. */
 packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream);
@@ -427,12 +441,12 @@ packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *s
  * and either perm mode. Errors: INVALID_ARG on a NULL argument. */
 packsell_status packsell_storage_rows(const packsell_matrix *A, int32_t *rows, void *stream);
 
-/* Device workspace bytes packsell_pcg needs for n unknowns (has_diag: a Jacobi
+/* Device workspace bytes the §5.2.2 solvers (packsell_pcg) need for n unknowns (has_diag: a Jacobi
  * preconditioner is passed). */
 size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag,
                                     int32_t max_iters);
 
-/* Solve A x = b for SPD A.
+/* Solve A x = b for SPD A (§5.2.2: FP64 PCG, or the inner-outer CG).
  *   A_outer : SELL_F64 matrix (square, implicit permutation): the FP64
  *             operator of the outer iteration and of the residual check
  *   A_inner : PackSELL (FP16 / E8MY) or SELL_F32 copy of the same matrix for
@@ -458,7 +472,7 @@ packsell_status packsell_pcg(const packsell_matrix *A_outer, const packsell_matr
                              const packsell_solve_opts *opts, void *work, size_t work_bytes,
                              double *h_hist, packsell_solve_result *result, void *stream);
 
-/* Backward of x = A^-1 b for SPD A: the adjoint solve A lam = dL/dx (A is
+/* Backward of the §5.2.2 solve x = A^-1 b for SPD A: the adjoint solve A lam = dL/dx (A is
  * symmetric, so A^T = A), with the operators and options of packsell_pcg,
  * from lam = 0; then dL/db = lam and dL/da_ij = -lam_i x_j on the pattern.
  *   x      : double [n], the forward solution
