@@ -75,7 +75,8 @@ typedef enum packsell_status {
  *         grid (§4.2.2); D in [1, 22].
  * SELL_F32 / SELL_F64 : plain SELL-C-sigma (§3) with separate FP32 / FP64
  *         value and int32 column arrays: the baseline format and the FP64
- *         outer operator of the mixed-precision solver. D is ignored.  * W16_E4M3: 16-bit words (W = 16, one of the other word sizes of §4.2.1):
+ *         outer operator of the mixed-precision solver. D is ignored.
+ * W16_E4M3: 16-bit words (W = 16, one of the other word sizes of §4.2.1):
  *         bit 0 flag, bits 1..7 delta (D = 7, needs D = 7), bits 8..15 an
  *         FP8 E4M3 value (OCP: 4 exponent bits, bias 7, 3 fraction bits,
  *         largest finite 448, round to nearest even; a value that rounds
@@ -219,8 +220,9 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 /* y = A x (Eq. 1) by the §4.4 algorithm. x: float [m], y: float [n]
  * (original order, or storage order with explicit_perm). FP32
  * accumulation; each row is summed as one chain of fused multiply-adds in
- * stored order, so the result is bitwise reproducible. Words with flag 0 (dummies, padding) read no x and add
- * nothing. Works for PackSELL and SELL_F32 matrices. No allocation. */
+ * stored order, so the result is bitwise reproducible. Words with flag 0
+ * (dummies, padding) read no x and add nothing. Works for PackSELL and
+ * SELL_F32 matrices. No allocation. */
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
                               void *stream);
 
@@ -355,8 +357,9 @@ packsell_status packsell_batch_create(int32_t count, const packsell_matrix *cons
  * packsell_spmv sums it (same bits). */
 packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream);
 
-/* Work-list statistics of a batch plan (no counterpart in the paper): total stored words, algorithmic bytes of one launch
- * (words, offsets, perm, x and y once), number of work items. */
+/* Work-list statistics of a batch plan (no counterpart in the paper): total
+ * stored words, algorithmic bytes of one launch (words, offsets, perm, x and
+ * y once), number of work items. */
 packsell_status packsell_batch_info(const packsell_batch *B, int64_t *words, int64_t *bytes,
                                     int32_t *items);
 
