@@ -4,6 +4,8 @@ unique (ties), so the tests check what defines it - a breadth-first search
 from each component's root that appends unvisited neighbours in increasing
 degree, reversed - plus exact cases (a path, components), the permutation
 against numpy, and the word counts of the oracle's encoder before and after."""
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 
@@ -127,7 +129,6 @@ def test_reorder_errors():
 
 
 def _words(rowptr, col, n, D, sigma=256):
-    from types import SimpleNamespace
     csr = SimpleNamespace(n=n, m=n, rowptr=rowptr, col=col, val=np.ones(col.size))
     return O.encode(csr, C=32, sigma=sigma, D=D, fmt=O.FMT_E8MY if D != 15 else O.FMT_FP16).n_words
 
@@ -137,7 +138,7 @@ def test_rcm_word_counts():
     order gathers rows of similar length into slices (2^16 rows: 4,022,080 ->
     2,065,472 words). 7-point grid 32^3 at D = 9 (the plane of 1,024 columns
     against 2^9, as 65,536 against 2^15 on 256^3): the diagonal level sets
-    narrow most plane gaps (289,248 -> 275,840 words)."""
+    narrow part of the plane gaps (289,248 -> 275,840 words)."""
     csr = I.zipf_irregular(1 << 16, seed=0)
     perm = ps.packsell_reorder_rcm(csr.rowptr, csr.col)
     rp, cl, _ = ps.packsell_permute_csr(csr.rowptr, csr.col, None, perm)
@@ -147,3 +148,26 @@ def test_rcm_word_counts():
     perm = ps.packsell_reorder_rcm(g.rowptr, g.col)
     rp, cl, _ = ps.packsell_permute_csr(g.rowptr, g.col, None, perm)
     assert (_words(g.rowptr, g.col, g.n, 9), _words(rp, cl, g.n, 9)) == (289_248, 275_840)
+
+
+def test_reordered_system_solves_the_original():
+    """The documented use: B = P A P^T, b_new = b[perm], x[perm] = x_new. With
+    B x_new = b_new the scattered x solves A x = b (FP64 dense solves of a
+    small SPD matrix; the product identity B x[perm] = (A x)[perm] on the
+    oracle's FP64 CSR product)."""
+    csr, _ = I.poisson5_varcoef(12, seed=31)
+    perm = ps.packsell_reorder_rcm(csr.rowptr, csr.col)
+    rp, cl, vl = ps.packsell_permute_csr(csr.rowptr, csr.col, csr.val, perm)
+    B = SimpleNamespace(n=csr.n, m=csr.m, rowptr=rp, col=cl, val=vl)
+    x = I.uniform(csr.n, seed=32).astype(np.float64)
+    assert np.allclose(O.csr_spmv_f64(B, vl, x[perm]), O.csr_spmv_f64(csr, csr.val, x)[perm],
+                       rtol=1e-14, atol=1e-14)
+    dense = np.zeros((csr.n, csr.n))
+    dense[np.repeat(np.arange(csr.n), np.diff(rp)), cl] = vl
+    b = I.uniform(csr.n, seed=33).astype(np.float64)
+    x_new = np.linalg.solve(dense, b[perm])
+    xs = np.empty_like(x_new)
+    xs[perm] = x_new
+    A = np.zeros((csr.n, csr.n))
+    A[np.repeat(np.arange(csr.n), np.diff(csr.rowptr)), csr.col] = csr.val
+    assert np.allclose(A @ xs, b, rtol=1e-10, atol=1e-10)
