@@ -237,21 +237,27 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
         return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
     src += 8 * (h.n_slices + 1);
     if (h.perm_bytes) {
-        cudaMemcpyAsync(A->perm, src, (size_t)h.perm_bytes * h.n, cudaMemcpyHostToDevice, s);
+        if (cudaMemcpyAsync(A->perm, src, (size_t)h.perm_bytes * h.n, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
         src += (size_t)h.perm_bytes * h.n;
     }
     size_t nw = (size_t)std::max<int64_t>(h.n_words, 1);
     if (is_packed(p.format)) {
         if (cudaMalloc(&A->pack, 4 * nw) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
-        cudaMemcpyAsync(A->pack, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
+        if (cudaMemcpyAsync(A->pack, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
     } else {
         size_t eb = p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
         if (cudaMalloc(&A->val, eb * nw) != cudaSuccess || cudaMalloc(&A->col, 4 * nw) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
-        cudaMemcpyAsync(A->val, src, eb * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
-        src += eb * (size_t)h.n_words;
-        cudaMemcpyAsync(A->col, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s);
+        if (cudaMemcpyAsync(A->val, src, eb * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(A->col, src + eb * (size_t)h.n_words, 4 * (size_t)h.n_words,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
     }
     packsell_status st = validate_impl(*A, s);
     if (st != PACKSELL_OK) return bail(st);

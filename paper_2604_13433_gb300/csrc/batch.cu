@@ -195,11 +195,16 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
         batch_free(B);
         return fail(PACKSELL_ERR_NO_MEMORY, "packsell_batch_create: plan arrays");
     }
-    cudaMemcpyAsync(B->d_mats, B->h_mats.data(), sizeof(BatchMat) * count, cudaMemcpyHostToDevice, s);
-    if (!items.empty())
-        cudaMemcpyAsync(B->d_items, items.data(), sizeof(BatchItem) * items.size(),
-                        cudaMemcpyHostToDevice, s);
-    PS_CUDA(cudaStreamSynchronize(s));
+    cudaError_t e = cudaMemcpyAsync(B->d_mats, B->h_mats.data(), sizeof(BatchMat) * count,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpyAsync(B->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        batch_free(B);
+        return cuda_fail(e, "packsell_batch_create: plan copy");
+    }
     *out = B;
     return PACKSELL_OK;
 }

@@ -529,10 +529,9 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
             return bail(e == cudaErrorMemoryAllocation
                             ? fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: temporaries")
                             : cuda_fail(e, "cudaMallocAsync"));
-        cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-        cudaMemsetAsync(kl, 0, 8, s);
-        cudaMemsetAsync(total, 0, 8, s);
-        cudaMemsetAsync(maxw, 0, 4, s);
+        if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) || (e = cudaMemsetAsync(kl, 0, 8, s)) ||
+            (e = cudaMemsetAsync(total, 0, 8, s)) || (e = cudaMemsetAsync(maxw, 0, 4, s)))
+            return bail(cuda_fail(e, "packsell_encode: cudaMemsetAsync"));
         if (cudaMalloc(&A->offset, sizeof(int64_t) * (S + 1)) != cudaSuccess ||
             (perm_bytes && cudaMalloc(&A->perm, (size_t)perm_bytes * n) != cudaSuccess) ||
             (p.keep_rowptr && cudaMalloc(&A->rowptr, sizeof(int64_t) * (n + 1)) != cudaSuccess))
@@ -564,18 +563,20 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         PS_LAUNCH_CHECK("packsell_encode: kernels");
         packsell_status sst = scan_exclusive(slice_words, A->offset, S, s);
         if (sst != PACKSELL_OK) return bail(sst);
-        if (p.keep_rowptr)
-            cudaMemcpyAsync(A->rowptr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s);
+        if (p.keep_rowptr && (e = cudaMemcpyAsync(A->rowptr, rowptr, sizeof(int64_t) * (n + 1),
+                                                  cudaMemcpyDeviceToDevice, s)))
+            return bail(cuda_fail(e, "packsell_encode: row pointer copy"));
 
         DevStatus hst{};
         unsigned long long hkl = 0, htotal = 0;
         int hmaxw = 0;
         int64_t nw = 0;
-        cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&hkl, kl, 8, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&htotal, total, 8, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&hmaxw, maxw, 4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&nw, A->offset + S, 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(&hkl, kl, 8, cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(&htotal, total, 8, cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(&hmaxw, maxw, 4, cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(&nw, A->offset + S, 8, cudaMemcpyDeviceToHost, s)))
+            return bail(cuda_fail(e, "packsell_encode: read-back"));
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "packsell_encode: synchronize"));
         if (hst.code != 0)
@@ -715,8 +716,8 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     unsigned long long *cnt = nullptr;
     PS_CUDA(T.get(&st, sizeof(DevStatus)));
     PS_CUDA(T.get(&cnt, 8));
-    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    cudaMemsetAsync(cnt, 0, 8, s);
+    PS_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    PS_CUDA(cudaMemsetAsync(cnt, 0, 8, s));
     if (A.n > 0) {
         int g = blocks_for(A.n);
         if (is_packed(A.p.format))
@@ -731,8 +732,8 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     }
     DevStatus hst{};
     unsigned long long hc = 0;
-    cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&hc, cnt, 8, cudaMemcpyDeviceToHost, s);
+    PS_CUDA(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    PS_CUDA(cudaMemcpyAsync(&hc, cnt, 8, cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
     if (hst.code)
         return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad word, column or perm at index " +
