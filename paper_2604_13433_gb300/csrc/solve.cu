@@ -414,9 +414,14 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
         init.rtol = o.rtol;
         init.max_iters = o.max_iters;
         init.restart = 1;
-        cudaMemcpyAsync(w.sc, &init, sizeof(init), cudaMemcpyHostToDevice, s);
-        cudaMemsetAsync(w.counter, 0, 64, s);
-        cudaMemsetAsync(w.q, 0, 8 * n, s);
+        // every copy, memset and synchronisation of the host loop is checked
+        auto ck = [&](cudaError_t e) {
+            if (e != cudaSuccess) st = cuda_fail(e, "packsell_pcg: copy or synchronize");
+            return e == cudaSuccess;
+        };
+        if (!ck(cudaMemcpyAsync(w.sc, &init, sizeof(init), cudaMemcpyHostToDevice, s)) ||
+            !ck(cudaMemsetAsync(w.counter, 0, 64, s)) || !ck(cudaMemsetAsync(w.q, 0, 8 * n, s)))
+            goto out;
         if (ev0) cudaEventRecord(ev0, s);
         if (io && inv_diag) k_f64_to_f32<<<G, VTPB, 0, s>>>(n, inv_diag, w.M32);
 
@@ -489,7 +494,7 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 st = body(s);
                 if (st != PACKSELL_OK) goto out;
             }
-            cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+            if (!ck(cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) goto out;
             if (cudaStreamSynchronize(s) != cudaSuccess) {
                 st = cuda_fail(cudaGetLastError(), "packsell_pcg: iteration");
                 goto out;
@@ -504,8 +509,9 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 // the recurrence says converged: check the true residual
                 st = residual(nullptr, FIN_RT);
                 if (st != PACKSELL_OK) goto out;
-                cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
-                cudaStreamSynchronize(s);
+                if (!ck(cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s)) ||
+                    !ck(cudaStreamSynchronize(s)))
+                    goto out;
                 relres_true = h.bb > 0.0 ? sqrt(h.rt / h.bb) : 0.0;
                 if (relres_true < o.rtol) {
                     converged = true;
@@ -516,13 +522,14 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                 if (st != PACKSELL_OK) goto out;
                 if (!io) k_pcg_init<double><<<G, VTPB, 0, s>>>(n, w.r, inv_diag, w.p, red(FIN_RZ_INIT));
                 int one = 1, zero = 0;
-                cudaMemcpyAsync(&w.sc->restart, &one, sizeof(int), cudaMemcpyHostToDevice, s);
-                cudaMemcpyAsync(&w.sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
-                cudaStreamSynchronize(s);
+                if (!ck(cudaMemcpyAsync(&w.sc->restart, &one, sizeof(int), cudaMemcpyHostToDevice, s)) ||
+                    !ck(cudaMemcpyAsync(&w.sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s)) ||
+                    !ck(cudaStreamSynchronize(s)))
+                    goto out;
             }
         }
         if (ev1) cudaEventRecord(ev1, s);
-        cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (!ck(cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) goto out;
         PS_CUDA(cudaStreamSynchronize(s));
         if (h_hist)
             PS_CUDA(cudaMemcpy(h_hist, w.hist, sizeof(double) * (size_t)(std::min(h.iter, o.max_iters) + 1),
@@ -531,8 +538,9 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
             st = residual(nullptr, FIN_RT);
             if (st != PACKSELL_OK) goto out;
             SolveScalars h2{};
-            cudaMemcpyAsync(&h2, w.sc, sizeof(h2), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
+            if (!ck(cudaMemcpyAsync(&h2, w.sc, sizeof(h2), cudaMemcpyDeviceToHost, s)) ||
+                !ck(cudaStreamSynchronize(s)))
+                goto out;
             relres_true = h2.bb > 0.0 ? sqrt(h2.rt / h2.bb) : 0.0;
         }
         if (res) {
