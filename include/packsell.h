@@ -495,21 +495,27 @@ packsell_status packsell_pcg_backward(const packsell_matrix *A_outer,
 
 /* packsell_pcg without any device allocation. The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory when
- * they solve - code running while a stream is being captured into a CUDA
- * graph, processes whose allocator must not grow, plugins given a fixed
- * memory budget. It takes the same arguments as packsell_pcg minus the
- * workspace: the workspace comes from one static device array of 8 MiB in
- * the library (enough for about 160,000 unknowns with IO-CG and 260,000 with
- * FP64 PCG; every GPU that loads the library holds it until the process
- * exits). A system whose workspace would
- * not fit (packsell_pcg_workspace_bytes > 8 MiB) is rejected with
- * PACKSELL_ERR_INVALID_ARG and a message giving both sizes.
+ * they solve - an application that reserved the device's memory up front
+ * for its own pool, where a cudaMalloc would fail or fragment that pool;
+ * a plugin handed a fixed memory budget by its host; a latency-bound loop
+ * that must not take cudaMalloc's or cudaFree's implicit synchronisation.
+ * It takes the same arguments as packsell_pcg minus the workspace: the
+ * workspace comes from one static device array of 8 MiB in the library
+ * (enough for about 160,000 unknowns with IO-CG and 260,000 with FP64 PCG;
+ * every GPU that loads the library holds it until the process exits). A
+ * system whose workspace would not fit (packsell_pcg_workspace_bytes >
+ * 8 MiB) is rejected with PACKSELL_ERR_INVALID_ARG and a message giving
+ * both sizes.
  * - It allocates nothing: no cudaMalloc/cudaFree, no stream, event or graph;
- *   it runs directly on `stream` and synchronises it before returning
+ *   it runs directly on `stream`, reads the solver's scalars back to the
+ *   host as it iterates, and synchronises `stream` before returning
  *   (result->seconds is host wall time).
  * - The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress) with that device current and keeps it for later
+ *   calls on that device; make that first call before any stream capture
+ *   begins. A cudaDeviceReset invalidates the kept address, as it does every
+ *   matrix of the library: do not call the library on a device after
+ *   resetting it.
  * - All calls share the array and every call re-initialises what must start
  *   from zero, so results do not depend on earlier calls; but calls that
  *   overlap on the GPU (other threads or streams) race on it: serialise them. */

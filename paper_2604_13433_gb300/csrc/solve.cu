@@ -530,10 +530,11 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
         }
         if (ev1) cudaEventRecord(ev1, s);
         if (!ck(cudaMemcpyAsync(&h, w.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) goto out;
-        PS_CUDA(cudaStreamSynchronize(s));
-        if (h_hist)
-            PS_CUDA(cudaMemcpy(h_hist, w.hist, sizeof(double) * (size_t)(std::min(h.iter, o.max_iters) + 1),
-                               cudaMemcpyDeviceToHost));
+        if (!ck(cudaStreamSynchronize(s))) goto out;
+        if (h_hist &&
+            !ck(cudaMemcpy(h_hist, w.hist, sizeof(double) * (size_t)(std::min(h.iter, o.max_iters) + 1),
+                           cudaMemcpyDeviceToHost)))
+            goto out;
         if (relres_true < 0.0) {
             st = residual(nullptr, FIN_RT);
             if (st != PACKSELL_OK) goto out;
@@ -570,11 +571,12 @@ out:
 }
 
 // ---- the solver without allocation -------------------------------------
-// Some callers cannot allocate device memory at the time they solve: code
-// running inside a stream capture or under an allocator that must not grow,
-// plugins handed a fixed memory budget. For them the whole solver workspace
-// lives in one static device array, sized for systems of up to about 160,000
-// unknowns (IO-CG) or 260,000 (FP64 PCG). Every call shares it.
+// Some callers cannot allocate device memory at the time they solve: an
+// application that reserved the device's memory for its own pool, a plugin
+// given a fixed budget, a loop that must not take cudaMalloc's implicit
+// synchronisation. For them the whole solver workspace lives in one static
+// device array, sized for systems of up to about 160,000 unknowns (IO-CG)
+// or 260,000 (FP64 PCG). Every call shares it.
 constexpr size_t kNoAllocBytes = (size_t)8 << 20;  // 8 MiB
 static __device__ __align__(256) unsigned char g_pcg_scratch[kNoAllocBytes];
 
@@ -585,7 +587,9 @@ std::mutex g_scratch_mu;
 }  // namespace
 
 // Device address of g_pcg_scratch on the current device (looked up once per
-// device; the name is only a host-side stand-in for it).
+// device, with that device current; in host code the name is only a
+// host-side stand-in for it). A cudaDeviceReset invalidates the kept address
+// together with every other device object of the library.
 static packsell_status noalloc_scratch(void **out) {
     int dev = 0;
     PS_CUDA(cudaGetDevice(&dev));

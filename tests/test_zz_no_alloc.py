@@ -1,6 +1,8 @@
 """packsell_pcg_noalloc: the solver for callers that cannot allocate device
-memory while they solve (inside a stream capture, under a fixed budget). Its
-workspace is the library's static 8 MiB device array. This file is collected
+memory while they solve (an application whose memory is reserved for its own
+pool, a plugin with a fixed budget, a loop that must not take cudaMalloc's
+implicit synchronisation). Its workspace is the library's static 8 MiB device
+array. This file is collected
 last on purpose (its name), and passes alone in a fresh process as well as
 after the other tests.
 
