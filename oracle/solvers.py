@@ -76,38 +76,41 @@ def pcg(A, b, x0=None, tol=1e-10, maxit=10000, inv_diag=None, val=None):
     return x, it, hist
 
 
-def inner_pcg_f32(A, deq, r, m_in, inv_diag=None):
+def inner_pcg_f32(A, deq, r, m_in, inv_diag=None, dtype=np.float32):
     """m_in PCG iterations on A z = r from z = 0 in simulated single precision.
 
     The right-hand side is r / ||r||_2 (rounded to float32); the result is
     scaled back by ||r||_2 in double. Vectors are float32, dot products are
     accumulated in double, scalars alpha and beta are rounded to float32 before
     they scale a vector, and A v is the quantised matrix applied in double and
-    rounded to float32.
+    rounded to float32. ``dtype`` is the working precision of the vectors and
+    scalars (float32 for the inner solve of §5.2.2; float64 takes the
+    rounding out, so the same steps are plain CG in double precision).
     """
+    dt = np.dtype(dtype).type
     s = float(np.linalg.norm(r))
     if s == 0.0:
         return np.zeros_like(r, dtype=np.float64)
-    rr = (np.asarray(r, np.float64) / s).astype(np.float32)
-    M = None if inv_diag is None else np.asarray(inv_diag, np.float32)
+    rr = (np.asarray(r, np.float64) / s).astype(dt)
+    M = None if inv_diag is None else np.asarray(inv_diag, dt)
     xx = np.zeros_like(rr)
-    z = rr if M is None else (M * rr).astype(np.float32)
+    z = rr if M is None else (M * rr).astype(dt)
     p = z.copy()
     rz = _dot(rr, z)
     for _ in range(m_in):
         if rz == 0.0:
             break
-        q = csr_spmv_f64(A, deq, p).astype(np.float32)
+        q = csr_spmv_f64(A, deq, p).astype(dt)
         pq = _dot(p, q)
         if pq <= 0.0:
             break
-        a = np.float32(rz / pq)
-        xx = (xx + a * p).astype(np.float32)
-        rr = (rr - a * q).astype(np.float32)
-        z = rr if M is None else (M * rr).astype(np.float32)
+        a = dt(rz / pq)
+        xx = (xx + a * p).astype(dt)
+        rr = (rr - a * q).astype(dt)
+        z = rr if M is None else (M * rr).astype(dt)
         rz_new = _dot(rr, z)
-        bta = np.float32(rz_new / rz)
-        p = (z + bta * p).astype(np.float32)
+        bta = dt(rz_new / rz)
+        p = (z + bta * p).astype(dt)
         rz = rz_new
     return xx.astype(np.float64) * s
 

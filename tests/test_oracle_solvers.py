@@ -153,3 +153,46 @@ def test_adjoint_grads_match_finite_differences():
         bm[i] -= h
         fd = (loss(theta, bp) - loss(theta, bm)) / (2 * h)
         assert np.isclose(lam[i], fd, rtol=1e-5, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# the inner solve of IO-CG (§5.2.2), pinned against independent references
+# --------------------------------------------------------------------------
+def _inner_case(seed):
+    a, _ = I.poisson5_varcoef(6, seed=seed)  # 36 unknowns, SPD
+    e = O.encode(a, C=32, sigma=256, D=15, fmt=O.FMT_FP16)
+    d = _dense(a, e.deq)
+    r = I.uniform(a.n, seed=seed + 1).astype(np.float64) * 3.0
+    return a, e.deq, d, r
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_inner_pcg_without_rounding_is_an_exact_solve(jacobi):
+    """With the float32 rounding taken out and m_in = n, CG on an SPD system
+    of n unknowns reaches the solution (finite termination, §5.2.2's CG):
+    the result must equal the dense solve of q(A) z = r to rounding. A wrong
+    alpha, beta or rescaling does not terminate at the solution."""
+    a, deq, d, r = _inner_case(40)
+    M = 1.0 / np.diag(d) if jacobi else None
+    z = S.inner_pcg_f32(a, deq, r, a.n, inv_diag=M, dtype=np.float64)
+    ref = np.linalg.solve(d, r)
+    assert np.allclose(z, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_inner_pcg_iterates_follow_fp64_pcg(k):
+    """Its first k iterates are those of the FP64 Jacobi PCG (pinned on its
+    own above) started from zero on r / ||r||, scaled by ||r||, up to float32
+    rounding; in double precision they agree to rounding of double."""
+    a, deq, d, r = _inner_case(41)
+    M = 1.0 / np.diag(d)
+    s = np.linalg.norm(r)
+    ref, _, _ = S.pcg(a, r / s, tol=0.0, maxit=k, inv_diag=M, val=deq)
+    ref = ref * s
+    z32 = S.inner_pcg_f32(a, deq, r, k, inv_diag=M)
+    z64 = S.inner_pcg_f32(a, deq, r, k, inv_diag=M, dtype=np.float64)
+    scale = np.abs(ref).max()
+    assert np.abs(z64 - ref).max() <= 1e-12 * scale
+    err32 = np.abs(z32 - ref).max()
+    assert err32 <= 2e-5 * scale
+    assert err32 > 0.0  # the float32 rounding is really simulated

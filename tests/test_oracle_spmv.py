@@ -88,3 +88,27 @@ def test_backward_error():
     y2[3] += 1e-3
     want = 1e-3 / (np.abs(A).sum(axis=1).max() * np.abs(x).max())
     assert np.isclose(O.backward_error(y2, csr, v, x), want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("w", [8, 64, 512])
+def test_error_bound_is_reached_on_a_row_of_ties(w):
+    """A row 1, u, u, ..., u (u = 2^-24, w stored words, x = 1): every fused
+    multiply-add 1 + u is an exact tie that rounds to even, i.e. back to 1, so
+    the FP32 chain loses u at each of its w - 1 later steps. The error is
+    (w - 1) u while sum |a_ij x_j| is about 1: the bound gamma_w * sum must
+    hold, and must be within a factor of two of the error here (a bound off
+    by a factor, or missing w, fails one of the two). 2^-24 is exact in FP16
+    (its smallest subnormal) and in every E8MY."""
+    u = 2.0 ** -24
+    csr = I.CSR(n=1, m=w, rowptr=np.array([0, w], np.int64), col=np.arange(w, dtype=np.int32),
+                val=np.array([1.0] + [u] * (w - 1)))
+    e = O.encode(csr, C=32, sigma=1, D=15, fmt=O.FMT_FP16)
+    assert np.array_equal(e.deq, csr.val)
+    x = np.ones(w, np.float32)
+    y32 = O.csr_spmv_fma_f32(csr, e.deq.astype(np.float32), x)
+    exact = O.csr_spmv_f64(csr, e.deq, x.astype(np.float64))
+    assert y32[0] == 1.0
+    err = abs(float(y32[0]) - exact[0])
+    assert err == (w - 1) * u
+    bound = float(O.spmv_error_bound(csr, e.deq, x, np.array([w]))[0])
+    assert err <= bound <= 2.0 * err
