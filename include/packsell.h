@@ -219,10 +219,11 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
 
 /* y = A x (Eq. 1) by the §4.4 algorithm. x: float [m], y: float [n]
  * (original order, or storage order with explicit_perm). FP32
- * accumulation; each row is summed as one chain of fused multiply-adds in
- * stored order, so the result is bitwise reproducible. Words with flag 0
- * (dummies, padding) read no x and add nothing. Works for PackSELL and
- * SELL_F32 matrices. No allocation. */
+ * accumulation; variants 1-13 sum each row as one chain of fused
+ * multiply-adds in stored order; variant 14 (CSR order, split rows) sums a
+ * row in a fixed tree order. Every variant gives the same bits from run to
+ * run. Words with flag 0 (dummies, padding) read no x and add nothing. Works
+ * for PackSELL and SELL_F32 matrices. No allocation. */
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y,
                               void *stream);
 
@@ -267,11 +268,11 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 
 /* Number of SpMV kernel variants (1..PACKSELL_SPMV_VARIANTS). */
-#define PACKSELL_SPMV_VARIANTS 13
+#define PACKSELL_SPMV_VARIANTS 14
 
-/* SpMV kernel variants (all compute the same bits):
+/* SpMV kernel variants (1-13 compute the same bits; 14 rounds differently):
  *   0 auto: the tuner's choice once packsell_tune_spmv has run, else by
- *     shape: 11 for C = 1 PackSELL; for C = 32 PackSELL 12 when every slice
+ *     shape: 14 for C = 1 PackSELL; for C = 32 PackSELL 12 when every slice
  *     holds at most 16 words, 4 when padding exceeds 1/8 of the stored
  *     words, otherwise 13; 1 for everything else,
  *   1 thread-per-row with direct loads (the paper's mapping, §5.1.1),
@@ -299,7 +300,6 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     its lanes sum one row each; a long row is walked 256 words at a time
  *     with a warp prefix sum of the deltas for the columns, parallel gathers
  *     and one in-order chain of fused multiply-adds. Same bits as variant 1.
- *     The plan's default for C = 1 PackSELL matrices.
  *  12 pipelined persistent (PackSELL, C = 32): each thread walks rows i,
  *     i + stride, ... and loads the next row's words (and the slice offsets
  *     of the row after it) before it decodes and gathers the current row, so
@@ -312,7 +312,19 @@ packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *
  *     of the stream drains, load the offsets and their first round of words,
  *     and only then wait for that kernel to complete before they read x or
  *     write y. Safe because a matrix is complete when packsell_encode or
- *     packsell_import returns and no product writes it (PackSELL, C = 32). */
+ *     packsell_import returns and no product writes it (PackSELL, C = 32).
+ *  14 split rows in CSR order (PackSELL with C = 1; the future-work form of
+ *     §7 as variant 11): at encode time the rows are cut into tiles of at
+ *     most 253 words and 256 rows, and longer rows become items of their
+ *     own. All 32 lanes of a warp share a tile's words (16-byte loads, four
+ *     words per lane per round): the columns (Eq. 2 from the left offset of
+ *     Eq. 4) are a segmented prefix sum of the deltas restarting at each row
+ *     start, and the products are summed per row by a segmented sum across
+ *     the lanes; a long row is walked 256 words at a time, each lane summing
+ *     its words, then a butterfly reduction. The order is fixed (the same
+ *     bits on every run) but is a tree, not the stored-order chain: each row
+ *     is within gamma_w * sum_j |a_ij x_j| of the exact product (w stored
+ *     words of the row). The plan's default for C = 1 PackSELL matrices. */
 packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 
 /* Autotune the SpMV variant (the §4.4 product in several kernel mappings;

@@ -244,7 +244,7 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     }
     size_t nw = (size_t)std::max<int64_t>(h.n_words, 1);
     if (is_packed(p.format)) {
-        if (cudaMalloc(&A->pack, 4 * nw) != cudaSuccess)
+        if (cudaMalloc(&A->pack, 4 * (nw + kWordTail)) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
         if (cudaMemcpyAsync(A->pack, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
@@ -272,10 +272,11 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     if (!A || variant < 0 || variant > PACKSELL_SPMV_VARIANTS)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: bad argument");
     Matrix *m = reinterpret_cast<Matrix *>(A);
-    if (variant == 11) {
-        if (!m->csr_items)
-            return fail(PACKSELL_ERR_INVALID_ARG,
-                        "packsell_set_spmv_variant: variant 11 needs a PackSELL matrix with C = 1");
+    if (variant == 11 || variant == 14) {
+        if (!(variant == 11 ? m->csr_items : m->split_items))
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_set_spmv_variant: variant " +
+                                                      std::to_string(variant) +
+                                                      " needs a PackSELL matrix with C = 1");
         m->variant = variant;
         return PACKSELL_OK;
     }
@@ -314,7 +315,8 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
         if (var >= 2 && !is_packed(m->p.format)) continue;
         if (var == 11 && !m->csr_items) continue;
-        if (((var >= 5 && var <= 10) || var >= 12) && m->p.C != 32) continue;
+        if (var == 14 && !m->split_items) continue;
+        if (((var >= 5 && var <= 10) || var == 12 || var == 13) && m->p.C != 32) continue;
         if (var == 12 && m->max_width > 16) continue;
         if (var >= 9 && var <= 10 && !m->stage[var - 9].part) continue;
         if (var >= 2 && var <= 4 && !m->part[var - 2]) continue;

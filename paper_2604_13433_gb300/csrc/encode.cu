@@ -466,6 +466,7 @@ void free_matrix_arrays(Matrix *A) {
     for (int v = 0; v < Matrix::kBulkVariants; ++v) cudaFree(A->part[v]);
     stage_free(*A);
     csr_plan_free(*A);
+    split_plan_free(*A);
 }
 
 }  // namespace
@@ -598,7 +599,9 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
                     (int)n, rows_total, p.C, p.sigma, A->p.k_left, kl, rowptr, col, field,
                     A->perm, perm_bytes, A->offset, A->pack16);
         } else if (packed) {
-            if (cudaMalloc(&A->pack, sizeof(uint32_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
+            // kWordTail spare words: a 16-byte vector load that starts at the
+            // last words of the array stays inside the allocation
+            if (cudaMalloc(&A->pack, sizeof(uint32_t) * (nw + kWordTail)) != cudaSuccess)
                 return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
             int64_t rows_total = S * p.C;
             if (rows_total > 0)

@@ -56,7 +56,14 @@ struct Matrix {
     // CSR-order kernel, as int2 pairs
     void *csr_items = nullptr;
     int csr_nitems = 0;
+    // variant 14 (C = 1): work items of the split-row kernel, as int2 pairs
+    void *split_items = nullptr;
+    int split_nitems = 0;
 };
+
+// Spare words allocated after a matrix's packed word array (never read as
+// data): 16-byte vector loads of the last words stay inside the allocation.
+constexpr int64_t kWordTail = 4;
 
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
 inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PACKSELL_FMT_SELL_F64; }
@@ -91,6 +98,12 @@ packsell_status plan_csr(Matrix &A, cudaStream_t s);
 void csr_plan_free(Matrix &A);
 packsell_status launch_csr(const Matrix &A, const void *perm, int pb, const float *x, float *y,
                            cudaStream_t s);
+// split.cu
+packsell_status plan_split(Matrix &A, cudaStream_t s);
+void split_plan_free(Matrix &A);
+packsell_status launch_split(const Matrix &A, const void *perm, int pb, const float *x, float *y,
+                             cudaStream_t s);
+
 packsell_status launch_stage(const Matrix &A, int v, const void *perm, int pb, const float *x,
                              float *y, cudaStream_t s);
 

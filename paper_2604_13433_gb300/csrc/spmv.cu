@@ -884,9 +884,14 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
     }
     A.auto_variant = 1;
     if (is_packed(A.p.format) && A.p.C == 1 && A.n > 0 && A.n < INT32_MAX) {
-        const packsell_status st = plan_csr(A, s);
+        packsell_status st = plan_csr(A, s);
         if (st != PACKSELL_OK) return st;
-        if (A.csr_items) A.auto_variant = 11;
+        st = plan_split(A, s);
+        if (st != PACKSELL_OK) return st;
+        // untuned default for CSR order: the split-row kernel (all lanes busy
+        // on rows of any length); variant 11 keeps the stored-order chain
+        if (A.split_items) A.auto_variant = 14;
+        else if (A.csr_items) A.auto_variant = 11;
         return PACKSELL_OK;
     }
     // the bulk kernel indexes a warp's words with 32-bit integers
@@ -928,6 +933,7 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
     int g = grid_for(A.n);
     const int var = A.variant == 0 ? A.auto_variant : A.variant;
     if (var == 11 && is_packed(A.p.format)) return launch_csr(A, perm, pb, x, y, s);
+    if (var == 14 && is_packed(A.p.format)) return launch_split(A, perm, pb, x, y, s);
     if (var == 12 && is_packed(A.p.format)) {
         if (A.p.C != 32 || A.max_width > 16)
             return fail(PACKSELL_ERR_INVALID_ARG,

@@ -34,7 +34,8 @@ SPMV_STAGE = (9, 10)
 SPMV_CSR = 11  # C = 1 PackSELL matrices (rows stored one after another)
 SPMV_PIPE = 12  # C = 32, next row's words loaded while the current one is gathered
 SPMV_PDL = 13  # C = 32, variant 5 with programmatic dependent launch
-SPMV_VARIANTS = 13
+SPMV_SPLIT = 14  # C = 1, all lanes of a warp share a tile's words (split rows)
+SPMV_VARIANTS = 14
 
 
 class PackSELLError(RuntimeError):

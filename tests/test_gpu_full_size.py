@@ -34,7 +34,9 @@ def irr4m():
 
 def test_irregular_4M_spmv_both_layouts(irr4m):
     """SELL slices (C = 32, sigma = 256, explicit order, tuned variant) and
-    CSR order (C = 1, variant 11): every output row bitwise the twin."""
+    CSR order (C = 1, variant 11): every output row bitwise the twin; the
+    split-row CSR kernel (variant 14, the bench's CSR-order default): every
+    row within the gamma_w bound of the oracle's FP64 product."""
     ps = P()
     csr, deq32, rows = irr4m
     x = I.uniform(csr.m, seed=4)
@@ -51,6 +53,13 @@ def test_irregular_4M_spmv_both_layouts(irr4m):
         ps.packsell_set_spmv_variant(B, v)
         y = ps.packsell_spmv(B, xd).cpu().numpy()
         assert np.array_equal(y.view(np.uint32), twin.view(np.uint32)), f"variant {v}"
+    ps.packsell_set_spmv_variant(B, ps.SPMV_SPLIT)
+    y = ps.packsell_spmv(B, xd).cpu().numpy().astype(np.float64)
+    enc_words = np.diff(ps.packsell_arrays(B)["offset"])  # C = 1: one row per slice
+    ref = O.csr_spmv_f64(csr, deq32.astype(np.float64), x.astype(np.float64))
+    bound = O.spmv_error_bound(csr, deq32.astype(np.float64), x, enc_words)
+    bad = np.nonzero(~(np.abs(y - ref) <= bound))[0]
+    assert bad.size == 0, f"variant 14: {bad.size} rows beyond the bound, first {bad[:5]}"
     ps.packsell_check_status(B)
 
 

@@ -59,7 +59,24 @@ def check_spmv(csr, fmt, D, C=32, sigma=256, explicit=False, seed=0, rel_tol=Non
     assert np.all(np.abs(y - ref) <= bound)
     if rel_tol is not None and np.abs(ref).max() > 0:
         assert np.abs(y - ref).max() / np.abs(ref).max() <= rel_tol
+    if C == 1 and csr.n > 0 and fmt in ("fp16", "e8my"):
+        check_split(packsell, A, xd, ref, bound)
     return A, enc, x, y
+
+
+def check_split(packsell, A, xd, ref, bound):
+    """Variant 14 (split rows, CSR order) sums a row as a fixed tree, not the
+    stored-order chain: every row within the gamma_w forward-error bound of
+    the oracle's FP64 product on the same quantised values, and the same bits
+    on a second run."""
+    packsell.packsell_set_spmv_variant(A, packsell.SPMV_SPLIT)
+    y1 = packsell.packsell_spmv(A, xd).cpu().numpy()
+    y2 = packsell.packsell_spmv(A, xd).cpu().numpy()
+    assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    err = np.abs(y1.astype(np.float64) - ref)
+    bad = np.nonzero(~(err <= bound))[0]
+    assert bad.size == 0, f"variant 14: {bad.size} rows beyond the bound, first {bad[:5]}"
+    packsell.packsell_set_spmv_variant(A, packsell.SPMV_AUTO)
 
 
 CASES = [
@@ -177,14 +194,16 @@ def test_spmv_csr_order_tile_edges():
     """Row lengths around the 256-word tile limit and the 64-row tile cap,
     empty rows, and rows with many dummies (D = 2)."""
     need_gpu()
-    lengths = [0, 1, 255, 256, 257, 0, 511, 512, 513, 3] + [4] * 70 + [0] * 40 + [256, 1, 1000, 2]
+    lengths = ([0, 1, 255, 256, 257, 0, 511, 512, 513, 3] + [4] * 70 + [0] * 40 +
+               [256, 1, 1000, 2, 253, 254, 252, 1, 250, 3, 0, 0] + [1] * 700 + [0] * 300)
     csr = _lengths_csr(lengths, 5000, seed=1)
     for fmt, D in (("fp16", 15), ("e8my", 2)):
         check_spmv(csr, fmt, D, C=1, sigma=1)
     packsell = P()
     A = encode_gpu(csr, fmt="fp16", C=1, sigma=1)
     times = packsell.packsell_tune_spmv(A, dev(I.uniform(csr.m, seed=2)), reps=3)
-    assert packsell.SPMV_CSR in times and 5 not in times  # C = 32 variants are skipped
+    assert packsell.SPMV_CSR in times and packsell.SPMV_SPLIT in times
+    assert 5 not in times  # C = 32 variants are skipped
 
 
 def test_pipelined_variant_short_rows_only():
