@@ -40,8 +40,7 @@
 namespace packsell {
 namespace {
 
-constexpr int ST = 256;       // words a warp holds per chunk: SRD rounds of 128
-constexpr int SRD = ST / 128;
+constexpr int ST = 256;       // words a warp holds per chunk: 8 consecutive words per lane
 constexpr int SCT = ST - 3;   // tile words at most (room for the aligned-down start)
 constexpr int SR_MAX = 256;   // tile rows at most
 constexpr int SW = 8;         // warps per block
@@ -49,38 +48,41 @@ constexpr uint32_t kAbs = 0x80000000u;  // column scan: the value is an absolute
 
 // Column scan operator on (absolute?, value) packed in one word: a later
 // absolute column replaces what came before, a later relative delta adds to
-// it. Columns and their partial sums stay below 2^31.
-__device__ __forceinline__ uint32_t col_comb(uint32_t a, uint32_t b) { return (b & kAbs) ? b : a + b; }
+// it (b + (a masked off when b is absolute)). Columns and their partial sums
+// stay below 2^31.
+__device__ __forceinline__ uint32_t col_comb(uint32_t a, uint32_t b) {
+    return b + (a & ~(uint32_t)((int32_t)b >> 31));
+}
 
 __device__ __forceinline__ int split_left(int row, int sigma, int sig_shift, long long k_left) {
     const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
     return k_left < blk ? (int)(blk - k_left) : 0;
 }
 
+// Where row `row`'s product goes in y (through the sigma permutation when
+// y is in the original order).
 template <bool PERM>
-__device__ __forceinline__ void split_store(int row, int sigma, int sig_shift, const void *perm,
-                                            int perm_bytes, float t, float *__restrict__ y) {
-    int io = row;
-    if (PERM) {
-        const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
-        io = blk + (perm_bytes == 1 ? (int)((const uint8_t *)perm)[row]
-                                    : (int)((const uint16_t *)perm)[row]);
-    }
-    y[io] = t;
+__device__ __forceinline__ int split_out(int row, int sigma, int sig_shift, const void *perm,
+                                         int perm_bytes) {
+    if (!PERM) return row;
+    const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
+    return blk + (perm_bytes == 1 ? (int)((const uint8_t *)perm)[row]
+                                  : (int)((const uint16_t *)perm)[row]);
 }
 
 __device__ __forceinline__ uint4 ld_words4(const uint32_t *p) {
     return __ldcs(reinterpret_cast<const uint4 *>(p));
 }
 
-__device__ __forceinline__ uint32_t w4(const uint4 &v, int j) {
-    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
-}
-
 template <int FMT>
 __device__ __forceinline__ float split_value(uint32_t wd, Decode dc) {
     if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
     return __uint_as_float(wd & dc.vmask);
+}
+
+// delta of a word: D bits when it carries a value, 31 bits otherwise
+__device__ __forceinline__ uint32_t split_delta(uint32_t wd, Decode dc) {
+    return (wd >> 1) & ((wd & 1u) ? dc.dmask : 0x7fffffffu);
 }
 
 // Work item: a tile of rows [r0, r0 + nrows) holding nwd words from word
@@ -92,17 +94,25 @@ struct __align__(16) SplitItem {
     int meta;
 };
 
-// The first ST words of an item, aligned down to 16 bytes: lane l holds the
-// words at 128u + 4l .. 128u + 4l + 3 of round u (0 past the item's end).
-__device__ __forceinline__ void split_load(const uint32_t *__restrict__ pack, long long base,
-                                           int nwd, int lane, uint4 (&wv)[SRD]) {
-    const long long a0 = base & ~3ll;
-    const int lim = (int)(base - a0) + nwd;
-#pragma unroll
-    for (int u = 0; u < SRD; ++u) {
-        const int p = 128 * u + 4 * lane;
-        wv[u] = p < lim ? ld_words4(pack + a0 + p) : make_uint4(0, 0, 0, 0);
-    }
+// ST words from `first` (a multiple of 4): lane l holds the 8 consecutive
+// words first + 8l .. first + 8l + 7 (0 from `lim` on).
+__device__ __forceinline__ void split_load(const uint32_t *__restrict__ pack, long long first,
+                                           int lim, int lane, uint4 (&wv)[2]) {
+    const int p = 8 * lane;
+    wv[0] = p < lim ? ld_words4(pack + first + p) : make_uint4(0, 0, 0, 0);
+    wv[1] = p + 4 < lim ? ld_words4(pack + first + p + 4) : make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ void split_load_item(const uint32_t *__restrict__ pack,
+                                                const SplitItem &d, int lane, uint4 (&wv)[2]) {
+    const long long a0 = d.base & ~3ll;
+    const int nwd = d.meta < 0 ? -d.meta : (d.meta & 0xFFFF);
+    split_load(pack, a0, (int)(d.base - a0) + nwd, lane, wv);
+}
+
+__device__ __forceinline__ void unpack8(const uint4 (&wv)[2], uint32_t (&w)[8]) {
+    w[0] = wv[0].x; w[1] = wv[0].y; w[2] = wv[0].z; w[3] = wv[0].w;
+    w[4] = wv[1].x; w[5] = wv[1].y; w[6] = wv[1].z; w[7] = wv[1].w;
 }
 
 // One row of more than SCT words: chunks of ST words (the first one already
@@ -115,198 +125,218 @@ __device__ __forceinline__ void split_long_row(int row, long long base, int nwd,
                                                const uint32_t *__restrict__ pack,
                                                const void *__restrict__ perm, int perm_bytes,
                                                Decode dc, const float *__restrict__ x,
-                                               float *__restrict__ y, int lane, uint4 (&cur)[SRD]) {
+                                               float *__restrict__ y, int lane, uint4 (&cur)[2]) {
     const long long a0 = base & ~3ll;
     const int lead = (int)(base - a0), lim = lead + nwd;
     uint32_t carry = (uint32_t)split_left(row, sigma, sig_shift, k_left);
     float t = 0.f;
     for (int k0 = 0; k0 < lim; k0 += ST) {
-        uint4 nxt[SRD];
+        uint4 nxt[2];
+        split_load(pack, a0 + k0 + ST, lim - k0 - ST, lane, nxt);
+        uint32_t wd[8], cs[8], acc = 0;
+        unpack8(cur, wd);
 #pragma unroll
-        for (int u = 0; u < SRD; ++u) {
-            const int p = k0 + ST + 128 * u + 4 * lane;
-            nxt[u] = p < lim ? ld_words4(pack + a0 + p) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < SRD; ++u) {
-            uint32_t wd[4], cs[4], acc = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int p = k0 + 128 * u + 4 * lane + j;
-                wd[j] = (p >= lead && p < lim) ? w4(cur[u], j) : 0u;
-                const uint32_t f = wd[j] & 1u;
-                acc += (wd[j] >> 1) & (f ? dc.dmask : 0x7fffffffu);
-                cs[j] = acc;
-            }
-            uint32_t inc = acc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += v;
-            }
-            const uint32_t before = carry + inc - acc;
-            carry += __shfl_sync(0xffffffffu, inc, 31);
-            float xv[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) xv[j] = (wd[j] & 1u) ? __ldg(x + (before + cs[j])) : 0.f;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (wd[j] & 1u) t = fmaf(split_value<FMT>(wd[j], dc), xv[j], t);
-        }
-#pragma unroll
-        for (int u = 0; u < SRD; ++u) cur[u] = nxt[u];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) split_store<PERM>(row, sigma, sig_shift, perm, perm_bytes, t, y);
-}
-
-// A tile of rows [r0, r0 + nrows) with its nwd (<= SCT) words in wv.
-template <int FMT, bool PERM>
-__device__ __forceinline__ void split_tile(int r0, int nrows, long long base, int nwd, int sigma,
-                                           int sig_shift, long long k_left,
-                                           const int64_t *__restrict__ offset,
-                                           const void *__restrict__ perm, int perm_bytes,
-                                           Decode dc, const float *__restrict__ x,
-                                           float *__restrict__ y, int lane, const uint4 (&wv)[SRD],
-                                           int *__restrict__ srow) {
-    const long long a0 = base & ~3ll;
-    const int lead = (int)(base - a0), lim = lead + nwd;
-    int4 *srow4 = reinterpret_cast<int4 *>(srow);
-#pragma unroll
-    for (int u = 0; u < SRD; ++u) srow4[32 * u + lane] = make_int4(-1, -1, -1, -1);
-    __syncwarp();
-    // mark where each row starts; an empty row's product is 0
-    for (int k = lane; k < nrows; k += 32) {
-        const int r = r0 + k;
-        const int64_t o0 = offset[r], o1 = offset[r + 1];
-        if (o1 > o0) srow[(int)(o0 - a0)] = r;
-        else split_store<PERM>(r, sigma, sig_shift, perm, perm_bytes, 0.f, y);
-    }
-    __syncwarp();
-    int hr[SRD][4];    // storage row starting at the word, or -1
-    float pv[SRD][4];  // value * x of every word (0 without a value)
-    uint32_t carry = 0;
-#pragma unroll
-    for (int u = 0; u < SRD; ++u) {
-        const int4 h = srow4[32 * u + lane];
-        hr[u][0] = h.x;
-        hr[u][1] = h.y;
-        hr[u][2] = h.z;
-        hr[u][3] = h.w;
-        uint32_t wd[4], cs[4], acc = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int p = 128 * u + 4 * lane + j;
-            wd[j] = (p >= lead && p < lim) ? w4(wv[u], j) : 0u;
-            const uint32_t f = wd[j] & 1u;
-            const uint32_t d = (wd[j] >> 1) & (f ? dc.dmask : 0x7fffffffu);
-            const uint32_t e =
-                hr[u][j] >= 0 ? kAbs | ((uint32_t)split_left(hr[u][j], sigma, sig_shift, k_left) + d) : d;
-            acc = col_comb(acc, e);
+        for (int j = 0; j < 8; ++j) {
+            const int p = k0 + 8 * lane + j;
+            if ((unsigned)(p - lead) >= (unsigned)nwd) wd[j] = 0u;
+            acc += split_delta(wd[j], dc);
             cs[j] = acc;
         }
         uint32_t inc = acc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc = col_comb(v, inc);
+            if (lane >= o) inc += v;
         }
-        // the earlier rounds' state comes first (it matters up to the lane's
-        // first row start)
-        const uint32_t up = __shfl_up_sync(0xffffffffu, inc, 1);
-        const uint32_t exc = lane == 0 ? carry : col_comb(carry, up);
-        carry = col_comb(carry, __shfl_sync(0xffffffffu, inc, 31));
-        float xv[4];
+        const uint32_t before = carry + inc - acc;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+        float xv[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t c = col_comb(exc, cs[j]) & ~kAbs;
-            xv[j] = (wd[j] & 1u) ? __ldg(x + c) : 0.f;
-        }
+        for (int j = 0; j < 8; ++j) xv[j] = (wd[j] & 1u) ? __ldg(x + (before + cs[j])) : 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            pv[u][j] = (wd[j] & 1u) ? split_value<FMT>(wd[j], dc) * xv[j] : 0.f;
+        for (int j = 0; j < 8; ++j)
+            if (wd[j] & 1u) t = fmaf(split_value<FMT>(wd[j], dc), xv[j], t);
+        cur[0] = nxt[0];
+        cur[1] = nxt[1];
     }
-    // segmented suffix sums, last round first; `in` is what flows into the
-    // round's last lane from the words after it (0 past the tile's end)
-    float in = 0.f;
 #pragma unroll
-    for (int u = SRD - 1; u >= 0; --u) {
-        float seg[4], s = 0.f;
-        bool hh = false;
-#pragma unroll
-        for (int j = 3; j >= 0; --j) {
-            s += pv[u][j];
-            seg[j] = s;
-            if (hr[u][j] >= 0) {
-                s = 0.f;
-                hh = true;
-            }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) y[split_out<PERM>(row, sigma, sig_shift, perm, perm_bytes)] = t;
+}
+
+// A tile of rows [r0, r0 + nrows) with its nwd (<= SCT) words in wv. For
+// each position of the tile, s_lft holds kAbs | (left offset of Eq. 4) where
+// a row starts and 0 elsewhere, and s_io the row's index in y where a row
+// starts: both are computed once per row, not once per word.
+template <int FMT, bool PERM>
+__device__ __forceinline__ void split_tile(int r0, int nrows, long long base, int nwd, int sigma,
+                                           int sig_shift, long long k_left,
+                                           const void *__restrict__ perm, int perm_bytes,
+                                           Decode dc, const float *__restrict__ x,
+                                           float *__restrict__ y, int lane, const uint4 (&wv)[2],
+                                           uint32_t *__restrict__ s_lft, int *__restrict__ s_io,
+                                           const uint32_t *__restrict__ soff) {
+    const long long a0 = base & ~3ll;
+    const int lead = (int)(base - a0);
+    uint4 *lft4 = reinterpret_cast<uint4 *>(s_lft);
+    lft4[2 * lane] = make_uint4(0, 0, 0, 0);
+    lft4[2 * lane + 1] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    // mark where each row starts (the low halves of the tile's offsets were
+    // copied to soff one item ahead: differences within a tile are below 2^8,
+    // so they are exact modulo 2^32); an empty row's product is 0
+    const uint32_t a0lo = (uint32_t)a0;
+    for (int k = lane; k < nrows; k += 32) {
+        const int r = r0 + k;
+        const uint32_t o0 = soff[k], o1 = soff[k + 1];
+        const int io = split_out<PERM>(r, sigma, sig_shift, perm, perm_bytes);
+        if (o1 != o0) {
+            const int pos = (int)(o0 - a0lo);
+            s_lft[pos] = kAbs | (uint32_t)split_left(r, sigma, sig_shift, k_left);
+            s_io[pos] = io;
+        } else {
+            y[io] = 0.f;
         }
-        // U: the lane's words before its first row start plus, while no row
-        // start intervenes, the same of the lanes after it
-        float U = s;
-        bool F = hh;
-        if (lane == 31 && !F) U += in;
+    }
+    __syncwarp();
+    uint32_t hl[8], wd[8], cs[8], acc = 0;
+    {
+        const uint4 l0 = lft4[2 * lane], l1 = lft4[2 * lane + 1];
+        hl[0] = l0.x; hl[1] = l0.y; hl[2] = l0.z; hl[3] = l0.w;
+        hl[4] = l1.x; hl[5] = l1.y; hl[6] = l1.z; hl[7] = l1.w;
+    }
+    unpack8(wv, wd);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float v = __shfl_down_sync(0xffffffffu, U, o);
-            const bool g = __shfl_down_sync(0xffffffffu, F ? 1 : 0, o) != 0;
-            if (lane + o < 32 && !F) {
-                U += v;
-                F = g;
-            }
+    for (int j = 0; j < 8; ++j) {
+        const int p = 8 * lane + j;
+        if ((unsigned)(p - lead) >= (unsigned)nwd) wd[j] = 0u;
+        acc = col_comb(acc, hl[j] + split_delta(wd[j], dc));  // a row start: kAbs | left + d
+        cs[j] = acc;
+    }
+    uint32_t inc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = col_comb(v, inc);
+    }
+    uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc = 0u;  // the tile's first word starts a row
+    float pv[8];  // value * x of every word (0 without a value)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t c = col_comb(exc, cs[j]) & ~kAbs;
+        const float xv = (wd[j] & 1u) ? __ldg(x + c) : 0.f;
+        pv[j] = (wd[j] & 1u) ? split_value<FMT>(wd[j], dc) * xv : 0.f;
+    }
+    // segmented suffix sums: in the lane, then across the lanes
+    float seg[8], s = 0.f;
+#pragma unroll
+    for (int j = 7; j >= 0; --j) {
+        s += pv[j];
+        seg[j] = s;
+        if (hl[j] & kAbs) s = 0.f;
+    }
+    // U: the lane's words before its first row start plus, while no row
+    // start intervenes, the same of the lanes after it
+    const unsigned heads = __ballot_sync(0xffffffffu, (hl[0] | hl[1] | hl[2] | hl[3] | hl[4] |
+                                                        hl[5] | hl[6] | hl[7]) & kAbs);
+    float U = s;
+    bool F = (heads >> lane) & 1u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float v = __shfl_down_sync(0xffffffffu, U, o);
+        if (lane + o < 32 && !F) {
+            U += v;
+            // heads in lanes lane + o .. lane + 2o - 1 end the run
+            F = ((heads >> (lane + o)) & ((1u << o) - 1u)) != 0u;
         }
-        float nxt_in = __shfl_down_sync(0xffffffffu, U, 1);
-        if (lane == 31) nxt_in = in;
-        in = __shfl_sync(0xffffffffu, U, 0);
-        // the lane's last row start takes what flows in from the lanes after it
-        bool last = true;
+    }
+    float nxt_in = __shfl_down_sync(0xffffffffu, U, 1);
+    if (lane == 31) nxt_in = 0.f;
+    // the lane's last row start takes what flows in from the lanes after it
+    bool last = true;
 #pragma unroll
-        for (int j = 3; j >= 0; --j) {
-            if (hr[u][j] >= 0) {
-                const float tot = last ? seg[j] + nxt_in : seg[j];
-                last = false;
-                split_store<PERM>(hr[u][j], sigma, sig_shift, perm, perm_bytes, tot, y);
-            }
+    for (int j = 7; j >= 0; --j) {
+        if (hl[j] & kAbs) {
+            y[s_io[8 * lane + j]] = last ? seg[j] + nxt_in : seg[j];
+            last = false;
         }
     }
     __syncwarp();
 }
 
-// Persistent grid: warp w takes items w, w + W, ...; the next item's
-// descriptor loads while the current one is processed, and its first words
-// once that is done, so a warp keeps loads in flight across its items.
+// 4-byte asynchronous global -> shared copies (cp.async), in groups
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_older() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // all but the newest group done
+}
+
+// Start copying the low 32 bits of a tile's nrows + 1 row offsets (int64,
+// little-endian) into soff; every lane commits one group per item (empty for
+// a long row) so the group counts stay equal.
+__device__ __forceinline__ void split_prefetch_offsets(const SplitItem &d, bool live,
+                                                       const int64_t *__restrict__ offset,
+                                                       uint32_t *soff, int lane) {
+    if (live && d.meta >= 0) {
+        const int nrows = d.meta >> 16;
+        for (int k = lane; k <= nrows; k += 32) cp_async4(soff + k, offset + d.r0 + k);
+    }
+    cp_async_commit();
+}
+
+// Persistent grid: warp w takes items w, w + W, w + 2W, ... in a two-deep
+// pipeline: while item k is processed, item k + 1's words (registers) and row
+// offsets (shared memory, cp.async) are in flight, and item k + 2's
+// descriptor; so a warp waits on one memory round trip (its gathers) per
+// item rather than on the whole chain descriptor -> offsets -> words -> x.
 template <int FMT, bool PERM>
-__global__ void __launch_bounds__(SW * 32)
+__global__ void __launch_bounds__(SW * 32, 4)
     k_spmv_split(int sigma, int sig_shift, long long k_left, const int64_t *__restrict__ offset,
                  const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
                  Decode dc, const SplitItem *__restrict__ items, int nitems,
                  const float *__restrict__ x, float *__restrict__ y) {
-    __shared__ __align__(16) int s_row[SW][ST];  // storage row starting at a position, or -1
+    __shared__ __align__(16) uint32_t s_lft[SW][ST];             // kAbs | left at row starts
+    __shared__ __align__(16) int s_io[SW][ST];                   // y index at row starts
+    __shared__ __align__(16) uint32_t s_off[SW][2][SR_MAX + 4];  // tile row offsets (low halves), two items
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     int it = gw;
     if (it >= nitems) return;
-    SplitItem d = items[it];
-    uint4 wv[SRD];
-    split_load(pack, d.base, d.meta < 0 ? -d.meta : (d.meta & 0xFFFF), lane, wv);
+    SplitItem d = items[it], dn{0, 0, 0};
+    if (it + nwarps < nitems) dn = items[it + nwarps];
+    uint4 wv[2];
+    split_load_item(pack, d, lane, wv);
+    split_prefetch_offsets(d, true, offset, s_off[wl][0], lane);
+    int buf = 0;
     for (; it < nitems; it += nwarps) {
-        const int nit = it + nwarps;
-        SplitItem dn;
-        if (nit < nitems) dn = items[nit];
+        const bool has_next = it + nwarps < nitems;
+        SplitItem dnn{0, 0, 0};
+        if (it + 2 * nwarps < nitems) dnn = items[it + 2 * nwarps];
+        uint4 wn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        if (has_next) split_load_item(pack, dn, lane, wn);
+        split_prefetch_offsets(dn, has_next, offset, s_off[wl][buf ^ 1], lane);
+        cp_async_wait_older();  // this item's offsets have landed (this lane's copies)
+        __syncwarp();           // ... and every other lane's
         if (d.meta < 0)
             split_long_row<FMT, PERM>(d.r0, d.base, -d.meta, sigma, sig_shift, k_left, pack, perm,
                                       perm_bytes, dc, x, y, lane, wv);
         else
             split_tile<FMT, PERM>(d.r0, d.meta >> 16, d.base, d.meta & 0xFFFF, sigma, sig_shift,
-                                  k_left, offset, perm, perm_bytes, dc, x, y, lane, wv, s_row[wl]);
-        if (nit < nitems) {
-            d = dn;
-            split_load(pack, d.base, d.meta < 0 ? -d.meta : (d.meta & 0xFFFF), lane, wv);
-        }
+                                  k_left, perm, perm_bytes, dc, x, y, lane, wv, s_lft[wl],
+                                  s_io[wl], s_off[wl][buf]);
+        __syncwarp();  // every lane is done with s_off[buf] before it is refilled
+        d = dn;
+        dn = dnn;
+        wv[0] = wn[0];
+        wv[1] = wn[1];
+        buf ^= 1;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <int FMT, bool PERM>
