@@ -54,9 +54,11 @@ __device__ __forceinline__ uint32_t col_comb(uint32_t a, uint32_t b) {
     return b + (a & ~(uint32_t)((int32_t)b >> 31));
 }
 
-__device__ __forceinline__ int split_left(int row, int sigma, int sig_shift, long long k_left) {
+// Left offset of Eq. 4 for a row (kl = k_left, at most 2^31 - 1 here: a
+// larger k_left gives 0 for every row below 2^31).
+__device__ __forceinline__ int split_left(int row, int sigma, int sig_shift, int kl) {
     const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
-    return k_left < blk ? (int)(blk - k_left) : 0;
+    return max(blk - kl, 0);
 }
 
 // Where row `row`'s product goes in y (through the sigma permutation when
@@ -121,7 +123,7 @@ __device__ __forceinline__ void unpack8(const uint4 (&wv)[2], uint32_t (&w)[8]) 
 // decoded and gathered.
 template <int FMT, bool PERM>
 __device__ __forceinline__ void split_long_row(int row, long long base, int nwd, int sigma,
-                                               int sig_shift, long long k_left,
+                                               int sig_shift, int k_left,
                                                const uint32_t *__restrict__ pack,
                                                const void *__restrict__ perm, int perm_bytes,
                                                Decode dc, const float *__restrict__ x,
@@ -170,7 +172,7 @@ __device__ __forceinline__ void split_long_row(int row, long long base, int nwd,
 // starts: both are computed once per row, not once per word.
 template <int FMT, bool PERM>
 __device__ __forceinline__ void split_tile(int r0, int nrows, long long base, int nwd, int sigma,
-                                           int sig_shift, long long k_left,
+                                           int sig_shift, int k_left,
                                            const void *__restrict__ perm, int perm_bytes,
                                            Decode dc, const float *__restrict__ x,
                                            float *__restrict__ y, int lane, const uint4 (&wv)[2],
@@ -221,27 +223,28 @@ __device__ __forceinline__ void split_tile(int r0, int nrows, long long base, in
     }
     uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
     if (lane == 0) exc = 0u;  // the tile's first word starts a row
+    // every valid word's column is now absolute (the tile's first word starts
+    // a row): the flag bit is folded into the base pointer
+    const float *__restrict__ xb = x - (size_t)kAbs;
     float pv[8];  // value * x of every word (0 without a value)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint32_t c = col_comb(exc, cs[j]) & ~kAbs;
-        const float xv = (wd[j] & 1u) ? __ldg(x + c) : 0.f;
+        const float xv = (wd[j] & 1u) ? __ldg(xb + col_comb(exc, cs[j])) : 0.f;
         pv[j] = (wd[j] & 1u) ? split_value<FMT>(wd[j], dc) * xv : 0.f;
     }
-    // segmented suffix sums: in the lane, then across the lanes
-    float seg[8], s = 0.f;
+    // segmented suffix sums. A: the lane's words before its first row start
+    uint32_t hm = 0;  // row starts among the lane's words
 #pragma unroll
-    for (int j = 7; j >= 0; --j) {
-        s += pv[j];
-        seg[j] = s;
-        if (hl[j] & kAbs) s = 0.f;
-    }
-    // U: the lane's words before its first row start plus, while no row
-    // start intervenes, the same of the lanes after it
-    const unsigned heads = __ballot_sync(0xffffffffu, (hl[0] | hl[1] | hl[2] | hl[3] | hl[4] |
-                                                        hl[5] | hl[6] | hl[7]) & kAbs);
-    float U = s;
-    bool F = (heads >> lane) & 1u;
+    for (int j = 0; j < 8; ++j) hm |= (hl[j] >> 31) << j;
+    const int fh = hm ? __ffs(hm) - 1 : 8;
+    float A = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (j < fh) A += pv[j];
+    // U: A plus, while no row start intervenes, the same of the lanes after it
+    const unsigned heads = __ballot_sync(0xffffffffu, hm != 0u);
+    float U = A;
+    bool F = hm != 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const float v = __shfl_down_sync(0xffffffffu, U, o);
@@ -251,15 +254,16 @@ __device__ __forceinline__ void split_tile(int r0, int nrows, long long base, in
             F = ((heads >> (lane + o)) & ((1u << o) - 1u)) != 0u;
         }
     }
-    float nxt_in = __shfl_down_sync(0xffffffffu, U, 1);
-    if (lane == 31) nxt_in = 0.f;
-    // the lane's last row start takes what flows in from the lanes after it
-    bool last = true;
+    float s = __shfl_down_sync(0xffffffffu, U, 1);
+    if (lane == 31) s = 0.f;
+    // from the lane's end backwards: what flows in from the later lanes, then
+    // each word; a row start closes its row's sum
 #pragma unroll
     for (int j = 7; j >= 0; --j) {
+        s += pv[j];
         if (hl[j] & kAbs) {
-            y[s_io[8 * lane + j]] = last ? seg[j] + nxt_in : seg[j];
-            last = false;
+            y[s_io[8 * lane + j]] = s;
+            s = 0.f;
         }
     }
     __syncwarp();
@@ -295,7 +299,7 @@ __device__ __forceinline__ void split_prefetch_offsets(const SplitItem &d, bool 
 // item rather than on the whole chain descriptor -> offsets -> words -> x.
 template <int FMT, bool PERM>
 __global__ void __launch_bounds__(SW * 32, 4)
-    k_spmv_split(int sigma, int sig_shift, long long k_left, const int64_t *__restrict__ offset,
+    k_spmv_split(int sigma, int sig_shift, int k_left, const int64_t *__restrict__ offset,
                  const uint32_t *__restrict__ pack, const void *__restrict__ perm, int perm_bytes,
                  Decode dc, const SplitItem *__restrict__ items, int nitems,
                  const float *__restrict__ x, float *__restrict__ y) {
@@ -421,6 +425,7 @@ packsell_status launch_split(const Matrix &A, const void *perm, int pb, const fl
     const int sg = A.p.sigma;
     const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
     const Decode dc = make_decode(A);
+    const int kl = (int)std::min<int64_t>(A.p.k_left, INT32_MAX);
     const bool h = A.p.format == PACKSELL_FMT_FP16;
     const SplitItem *it = reinterpret_cast<const SplitItem *>(A.split_items);
     // a persistent grid (fewer blocks when there are fewer items)
@@ -432,20 +437,20 @@ packsell_status launch_split(const Matrix &A, const void *perm, int pb, const fl
         blocks = std::min(blocks, want);
         if (h)
             k_spmv_split<PACKSELL_FMT_FP16, true><<<blocks, SW * 32, 0, s>>>(
-                sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
+                sg, sh, kl, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
         else
             k_spmv_split<PACKSELL_FMT_E8MY, true><<<blocks, SW * 32, 0, s>>>(
-                sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
+                sg, sh, kl, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
     } else {
         blocks = h ? split_blocks<PACKSELL_FMT_FP16, false>() : split_blocks<PACKSELL_FMT_E8MY, false>();
         if (!blocks) return fail(PACKSELL_ERR_CUDA, "packsell_spmv: device query failed");
         blocks = std::min(blocks, want);
         if (h)
             k_spmv_split<PACKSELL_FMT_FP16, false><<<blocks, SW * 32, 0, s>>>(
-                sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
+                sg, sh, kl, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
         else
             k_spmv_split<PACKSELL_FMT_E8MY, false><<<blocks, SW * 32, 0, s>>>(
-                sg, sh, A.p.k_left, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
+                sg, sh, kl, A.offset, A.pack, perm, pb, dc, it, A.split_nitems, x, y);
     }
     PS_LAUNCH_CHECK("packsell_spmv (split rows)");
     return PACKSELL_OK;
