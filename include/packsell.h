@@ -257,13 +257,18 @@ packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, dou
 /* Y = A X for k right-hand sides (an extension: the paper evaluates k = 1).
  * X: float, row-major [m x k] with leading dimension ldx >= k; Y: float,
  * row-major [n x k] with ldy >= k (rows in storage order with explicit_perm).
- * A group of 1-16 lanes shares each row (more for wider k); the words are
- * decoded once per lane and every real word feeds the row's k columns with
- * fused multiply-adds in stored order, so column q of Y equals packsell_spmv
- * with x = X[:, q] bit for bit. k = 1 with ldx = ldy = 1 runs the SpMV
- * itself. 16-byte X/Y loads need k, ldx, ldy divisible by 4 and 16-byte
- * aligned X and Y; other layouts take scalar loads. PackSELL and SELL_F32
- * matrices. Errors: INVALID_ARG (k < 1, ld < k, SELL_F64). No allocation. */
+ * C > 1 (and SELL_F32): a group of 1-16 lanes shares each row (more for
+ * wider k); the words are decoded once per lane and every real word feeds
+ * the row's k columns with fused multiply-adds in stored order, so column q
+ * of Y equals the thread-per-row packsell_spmv with x = X[:, q] bit for bit.
+ * C = 1 PackSELL (CSR order): the split-row kernel (all lanes of a warp
+ * share a tile's words, four columns at a time, segmented sums across the
+ * lanes): every entry within gamma_w * sum_j |a_ij X_jq| of the exact
+ * product, the same bits on every run. k = 1 with ldx = ldy = 1 runs the
+ * SpMV itself. 16-byte X/Y loads need k, ldx, ldy divisible by 4 and
+ * 16-byte aligned X and Y; other layouts take scalar loads. PackSELL and
+ * SELL_F32 matrices. Errors: INVALID_ARG (k < 1, ld < k, SELL_F64). No
+ * allocation. */
 packsell_status packsell_spmm(const packsell_matrix *A, int32_t k, const float *X,
                               int64_t ldx, float *Y, int64_t ldy, void *stream);
 
@@ -352,22 +357,54 @@ packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
 typedef struct packsell_batch packsell_batch; /* opaque plan */
 
-/* Many §4.4 products in one launch (the paper runs one matrix at a time).
- * Build a plan for y_i = A_i x_i, i < count. A: host array of PackSELL
- * matrices with C = 32 (FP16 and E8MY may be mixed); x, y: host arrays of
- * device pointers (x_i float [m_i], y_i float [n_i]) bound to the plan. The
- * plan uploads one descriptor per matrix and a work list of (matrix, slice
- * range) items of about equal word counts; warps of one persistent launch
- * take items round-robin. Reads each matrix's offsets (SYNCHRONISES
- * `stream`). The matrices and vectors must outlive the plan. */
+/* Many §4.4 products in one launch per layout (the paper runs one matrix at
+ * a time). Build a plan for y_i = A_i x_i, i < count. A: host array of
+ * PackSELL matrices with C = 32 or C = 1 (FP16 and E8MY, sigma and the
+ * permutation mode may be mixed); x, y: host arrays of device pointers (x_i
+ * float [m_i], y_i float [n_i]) bound to the plan. The plan uploads one
+ * descriptor per matrix and work lists:
+ *  - C = 32 matrices: (matrix, slice range) items of about equal word counts,
+ *    taken round-robin by the warps of one persistent launch, one thread per
+ *    row (each row's sum is the bits of packsell_spmv);
+ *  - C = 1 matrices (CSR order, §7's future work): the items of the
+ *    split-row kernel of packsell_spmm (tiles of at most 125 words and 128
+ *    rows, rows of more words on their own, long rows first), taken by the
+ *    warps of a second persistent launch; every row within gamma_w * sum_j
+ *    |a_ij x_j| of the exact product, the same bits on every run.
+ * Reads each matrix's offsets (SYNCHRONISES `stream`). The matrices and
+ * vectors must outlive the plan. */
 packsell_status packsell_batch_create(int32_t count, const packsell_matrix *const *A,
                                       const float *const *x, float *const *y, void *stream,
                                       packsell_batch **out);
 
-/* One launch computing every y_i = A_i x_i (§4.4) of the plan (asynchronous; no
- * allocation, so it can be captured in a CUDA graph). Each row is summed as
- * packsell_spmv sums it (same bits). */
+/* Every y_i = A_i x_i (§4.4) of a plan from packsell_batch_create: one
+ * launch for the C = 32 matrices and one for the C = 1 matrices
+ * (asynchronous; no allocation, so it can be captured in a CUDA graph).
+ * Errors: INVALID_ARG for a plan from packsell_batch_create_spmm. */
 packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream);
+
+/* Many products with k right-hand sides (Y_i = A_i X_i; the paper evaluates
+ * k = 1 on one matrix at a time) in one launch. A: host array of `count`
+ * PackSELL matrices with C = 1 (CSR order); X, Y: host arrays of device
+ * pointers, X_i float row-major [m_i x k] with leading dimension ldx[i] >= k,
+ * Y_i float [n_i x k] with ldy[i] >= k (rows in storage order with
+ * explicit_perm); ldx, ldy: host arrays, or NULL for k. The plan holds the
+ * split-row items of every matrix (see packsell_batch_create); one
+ * persistent launch takes them all, each tile computing four columns at a
+ * time (16-byte X and Y accesses when k and every leading dimension are
+ * multiples of 4 and every block is 16-byte aligned). Every entry of Y_i is
+ * within gamma_w * sum_j |a_ij X_jq| of the exact product. Reads each
+ * matrix's offsets (SYNCHRONISES `stream`). Errors: INVALID_ARG (k < 1, a
+ * matrix that is not PackSELL with C = 1, a NULL block, ld < k), NO_MEMORY,
+ * CUDA. */
+packsell_status packsell_batch_create_spmm(int32_t count, const packsell_matrix *const *A, int32_t k,
+                                           const float *const *X, const int64_t *ldx,
+                                           float *const *Y, const int64_t *ldy, void *stream,
+                                           packsell_batch **out);
+
+/* Run a plan from packsell_batch_create_spmm (asynchronous, one launch, no
+ * allocation). Errors: INVALID_ARG for a plan from packsell_batch_create. */
+packsell_status packsell_batch_spmm(const packsell_batch *B, void *stream);
 
 /* Work-list statistics of a batch plan (no counterpart in the paper): total
  * stored words, algorithmic bytes of one launch (words, offsets, perm, x and

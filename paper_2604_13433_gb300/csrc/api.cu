@@ -489,6 +489,26 @@ packsell_status packsell_batch_spmv(const packsell_batch *B, void *stream) {
     return batch_spmv(*reinterpret_cast<const Batch *>(B), as_stream(stream));
 }
 
+packsell_status packsell_batch_create_spmm(int32_t count, const packsell_matrix *const *A, int32_t k,
+                                           const float *const *X, const int64_t *ldx,
+                                           float *const *Y, const int64_t *ldy, void *stream,
+                                           packsell_batch **out) {
+    clear_error();
+    if (!out || count < 1 || !A || !X || !Y)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create_spmm: bad argument");
+    Batch *B = nullptr;
+    packsell_status st = batch_create_mm(count, reinterpret_cast<const Matrix *const *>(A), k, X, ldx,
+                                         Y, ldy, as_stream(stream), &B);
+    *out = reinterpret_cast<packsell_batch *>(B);
+    return st;
+}
+
+packsell_status packsell_batch_spmm(const packsell_batch *B, void *stream) {
+    clear_error();
+    if (!B) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_spmm: NULL plan");
+    return batch_spmm(*reinterpret_cast<const Batch *>(B), as_stream(stream));
+}
+
 packsell_status packsell_batch_info(const packsell_batch *B, int64_t *words, int64_t *bytes,
                                     int32_t *items) {
     clear_error();

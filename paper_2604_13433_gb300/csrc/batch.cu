@@ -1,10 +1,13 @@
-// Batched PackSELL SpMV: many matrices of uneven sizes in one persistent
-// launch. A plan holds, on the device, one descriptor per matrix (its word,
-// offset and perm arrays, parameters and bound x/y vectors) and a work list of
-// items (matrix, slice range) of roughly equal word counts. Warps take items
-// round-robin; lane l of a warp computes row l of each slice of its item
-// (thread-per-row, stored order, fused multiply-adds: the same bits as
-// packsell_spmv on each matrix alone).
+// Batched PackSELL products: many matrices of uneven sizes per launch.
+// A plan holds, on the device, one descriptor per matrix (its word, offset and
+// perm arrays, parameters and bound vectors) and work lists:
+//  * matrices with C = 32: items (matrix, slice range) of roughly equal word
+//    counts; warps take items round-robin and lane l of a warp computes row l
+//    of each slice of its item (thread-per-row, stored order, fused
+//    multiply-adds: the same bits as packsell_spmv on each matrix alone);
+//  * matrices with C = 1 (CSR order): the split-row items of multi.cu (tiles
+//    of rows and single long rows, long rows first), one persistent launch
+//    of the split-row kernel for all of them, with k right-hand sides.
 #include <cuda_fp16.h>
 #include <string.h>
 
@@ -40,6 +43,12 @@ struct Batch {
     BatchItem *d_items = nullptr;
     std::vector<BatchMat> h_mats;
     int64_t words = 0, rows = 0, bytes = 0;
+    // CSR-order (C = 1) matrices: split-row descriptors and items
+    int k = 1;       // right-hand sides (1: a batched SpMV plan)
+    bool vec = false;  // every X and Y allows 16-byte accesses
+    SplitMat *d_smats = nullptr;
+    MultiItem *d_mitems = nullptr;
+    int n_mitems = 0;
 };
 
 namespace {
@@ -115,7 +124,31 @@ void batch_free(Batch *B) {
     if (!B) return;
     cudaFree(B->d_mats);
     cudaFree(B->d_items);
+    cudaFree(B->d_smats);
+    cudaFree(B->d_mitems);
     delete B;
+}
+
+// Upload the split-row part of a plan: descriptors (one per matrix, C = 32
+// matrices included but never referenced) and items.
+static packsell_status upload_split(Batch *B, const std::vector<SplitMat> &smats,
+                                    std::vector<MultiItem> &mitems, cudaStream_t s) {
+    if (mitems.empty()) return PACKSELL_OK;
+    multi_items_order(mitems);
+    if (mitems.size() >= (size_t)INT32_MAX)
+        return fail(PACKSELL_ERR_RANGE, "packsell_batch_create: too many items");
+    if (cudaMalloc(&B->d_smats, sizeof(SplitMat) * smats.size()) != cudaSuccess ||
+        cudaMalloc(&B->d_mitems, sizeof(MultiItem) * mitems.size()) != cudaSuccess)
+        return fail(PACKSELL_ERR_NO_MEMORY, "packsell_batch_create: plan arrays");
+    cudaError_t e = cudaMemcpyAsync(B->d_smats, smats.data(), sizeof(SplitMat) * smats.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_mitems, mitems.data(), sizeof(MultiItem) * mitems.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_batch_create: plan copy");
+    B->n_mitems = (int)mitems.size();
+    return PACKSELL_OK;
 }
 
 packsell_status batch_create(int count, const Matrix *const *A, const float *const *x,
@@ -127,6 +160,8 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
     B->h_mats.resize(count);
     std::vector<BatchItem> items;
     std::vector<int64_t> offs;
+    std::vector<SplitMat> smats(count);
+    std::vector<MultiItem> mitems;
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -139,17 +174,17 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
     int64_t total_words = 0;
     for (int i = 0; i < count; ++i) {
         const Matrix *m = A[i];
-        if (!m || !is_packed(m->p.format) || m->p.C != 32) {
+        if (!m || !is_packed(m->p.format) || (m->p.C != 32 && m->p.C != 1)) {
             batch_free(B);
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create: matrix " + std::to_string(i) +
-                                                      " is not a PackSELL matrix with C = 32");
+                                                      " is not a PackSELL matrix with C = 32 or C = 1");
         }
         if ((m->m > 0 && !x[i]) || (m->n > 0 && !y[i])) {
             batch_free(B);
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create: NULL vector for matrix " +
                                                       std::to_string(i));
         }
-        total_words += m->n_words;
+        if (m->p.C == 32) total_words += m->n_words;
     }
     // items of about total / (8 * warps) words (at least 2048), whole slices
     const int64_t target = std::max<int64_t>(2048, total_words / std::max<int64_t>(1, 8 * warps));
@@ -171,15 +206,21 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
         d.dmask = (1u << m->p.D) - 1u;
         d.vmask = ~((2u << m->p.D) - 1u);
         B->h_mats[i] = d;
+        smats[i] = split_mat(*m, x[i], 1, y[i], 1, 1);
         B->words += m->n_words;
         B->rows += m->n;
         B->bytes += 4 * m->n_words + 8 * (m->n_slices + 1) + (int64_t)d.perm_bytes * m->n + 4 * m->m +
                     4 * m->n;
+        if (m->n == 0) continue;
         offs.resize(m->n_slices + 1);
         if (cudaMemcpy(offs.data(), m->offset, 8 * (m->n_slices + 1), cudaMemcpyDeviceToHost) !=
             cudaSuccess) {
             batch_free(B);
             return fail(PACKSELL_ERR_CUDA, "packsell_batch_create: reading offsets");
+        }
+        if (m->p.C == 1) {
+            multi_items_append(offs.data(), m->n, i, mitems);
+            continue;
         }
         int k0 = 0;
         for (int k = 0; k < m->n_slices; ++k) {
@@ -205,6 +246,65 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
         batch_free(B);
         return cuda_fail(e, "packsell_batch_create: plan copy");
     }
+    const packsell_status st = upload_split(B, smats, mitems, s);
+    if (st != PACKSELL_OK) {
+        batch_free(B);
+        return st;
+    }
+    *out = B;
+    return PACKSELL_OK;
+}
+
+packsell_status batch_create_mm(int count, const Matrix *const *A, int k, const float *const *X,
+                                const int64_t *ldx, float *const *Y, const int64_t *ldy,
+                                cudaStream_t s, Batch **out) {
+    *out = nullptr;
+    if (count < 1 || k < 1)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create_spmm: count < 1 or k < 1");
+    Batch *B = new Batch();
+    B->count = count;
+    B->k = k;
+    std::vector<SplitMat> smats(count);
+    std::vector<MultiItem> mitems;
+    std::vector<int64_t> offs;
+    bool vec = k % 4 == 0;
+    for (int i = 0; i < count; ++i) {
+        const Matrix *m = A[i];
+        const int64_t lx = ldx ? ldx[i] : k, ly = ldy ? ldy[i] : k;
+        if (!m || !is_packed(m->p.format) || m->p.C != 1) {
+            batch_free(B);
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create_spmm: matrix " +
+                                                      std::to_string(i) +
+                                                      " is not a PackSELL matrix with C = 1");
+        }
+        if ((m->m > 0 && !X[i]) || (m->n > 0 && !Y[i]) || lx < k || ly < k) {
+            batch_free(B);
+            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_create_spmm: NULL block or "
+                                                  "leading dimension below k for matrix " +
+                                                      std::to_string(i));
+        }
+        vec = vec && lx % 4 == 0 && ly % 4 == 0 && ((uintptr_t)X[i] & 15) == 0 &&
+              ((uintptr_t)Y[i] & 15) == 0;
+        smats[i] = split_mat(*m, X[i], lx, Y[i], ly, k);
+        B->words += m->n_words;
+        B->rows += m->n;
+        B->bytes += 4 * m->n_words + 8 * (m->n_slices + 1) +
+                    (int64_t)(m->p.explicit_perm ? 0 : m->perm_bytes) * m->n + 4 * (int64_t)k * (m->m + m->n);
+        if (m->n == 0) continue;
+        offs.resize(m->n_slices + 1);
+        if (cudaMemcpy(offs.data(), m->offset, 8 * (m->n_slices + 1), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            batch_free(B);
+            return fail(PACKSELL_ERR_CUDA, "packsell_batch_create_spmm: reading offsets");
+        }
+        multi_items_append(offs.data(), m->n, i, mitems);
+    }
+    B->vec = vec;
+    const packsell_status st = upload_split(B, smats, mitems, s);
+    if (st != PACKSELL_OK) {
+        batch_free(B);
+        return st;
+    }
     *out = B;
     return PACKSELL_OK;
 }
@@ -212,14 +312,24 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
 void batch_stats(const Batch &B, int64_t *words, int64_t *bytes, int32_t *items) {
     if (words) *words = B.words;
     if (bytes) *bytes = B.bytes;
-    if (items) *items = B.nitems;
+    if (items) *items = B.nitems + B.n_mitems;
 }
 
 packsell_status batch_spmv(const Batch &B, cudaStream_t s) {
-    if (B.nitems == 0) return PACKSELL_OK;
-    k_spmv_batched<<<B.blocks, BTPB, 0, s>>>(B.d_mats, B.d_items, B.nitems);
-    PS_LAUNCH_CHECK("packsell_batch_spmv");
-    return PACKSELL_OK;
+    if (!B.d_mats)
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_batch_spmv: a plan from packsell_batch_create_spmm (use packsell_batch_spmm)");
+    if (B.nitems > 0) {
+        k_spmv_batched<<<B.blocks, BTPB, 0, s>>>(B.d_mats, B.d_items, B.nitems);
+        PS_LAUNCH_CHECK("packsell_batch_spmv");
+    }
+    return launch_multi(SplitMat{}, B.d_smats, B.d_mitems, B.n_mitems, 1, false, s);
+}
+
+packsell_status batch_spmm(const Batch &B, cudaStream_t s) {
+    if (B.d_mats)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_spmm: the plan is a batched SpMV plan");
+    return launch_multi(SplitMat{}, B.d_smats, B.d_mitems, B.n_mitems, B.k, B.vec, s);
 }
 
 }  // namespace packsell

@@ -467,6 +467,7 @@ void free_matrix_arrays(Matrix *A) {
     stage_free(*A);
     csr_plan_free(*A);
     split_plan_free(*A);
+    multi_plan_free(*A);
 }
 
 }  // namespace

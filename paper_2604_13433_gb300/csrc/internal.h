@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "packsell.h"
 
@@ -56,9 +57,12 @@ struct Matrix {
     // CSR-order kernel, as int2 pairs
     void *csr_items = nullptr;
     int csr_nitems = 0;
-    // variant 14 (C = 1): work items of the split-row kernel, as int2 pairs
+    // variant 14 (C = 1): work items of the split-row kernel
     void *split_items = nullptr;
     int split_nitems = 0;
+    // C = 1: work items of the split-row SpMM (multi.cu)
+    void *multi_items = nullptr;
+    int multi_nitems = 0;
 };
 
 // Spare words allocated after a matrix's packed word array (never read as
@@ -98,6 +102,35 @@ packsell_status plan_csr(Matrix &A, cudaStream_t s);
 void csr_plan_free(Matrix &A);
 packsell_status launch_csr(const Matrix &A, const void *perm, int pb, const float *x, float *y,
                            cudaStream_t s);
+// multi.cu: split-row products with k right-hand sides over CSR-order
+// (C = 1) PackSELL matrices, one matrix or a batch in one launch
+constexpr int kMultiTileWords = 125;  // words of a tile at most
+constexpr int kMultiTileRows = 128;   // rows of a tile at most
+struct SplitMat {  // one matrix of a split-row product and its vectors
+    const uint32_t *pack;
+    const int64_t *offset;
+    const void *perm;  // NULL: y in storage order
+    const float *X;    // [m x k], row-major, leading dimension ldx
+    float *Y;          // [n x k], row-major, leading dimension ldy
+    long long ldx, ldy;
+    int k, sigma, sig_shift, kl, perm_bytes, fmt;
+    uint32_t dmask, vmask;
+};
+struct __align__(16) MultiItem {  // a tile (meta = rows << 16 | words) or a long row (meta = -words)
+    long long base;
+    int r0;
+    int meta;
+    int mat;
+    int pad0, pad1, pad2;
+};
+SplitMat split_mat(const Matrix &A, const float *X, int64_t ldx, float *Y, int64_t ldy, int k);
+void multi_items_append(const int64_t *off, int64_t n, int mat, std::vector<MultiItem> &items);
+void multi_items_order(std::vector<MultiItem> &items);
+packsell_status multi_plan(Matrix &A, cudaStream_t s);
+void multi_plan_free(Matrix &A);
+packsell_status launch_multi(const SplitMat &single, const SplitMat *mats, const MultiItem *items,
+                             int nitems, int k, bool vec, cudaStream_t s);
+
 // split.cu
 packsell_status plan_split(Matrix &A, cudaStream_t s);
 void split_plan_free(Matrix &A);
@@ -126,6 +159,10 @@ struct Batch;
 packsell_status batch_create(int count, const Matrix *const *A, const float *const *x,
                              float *const *y, cudaStream_t s, Batch **out);
 packsell_status batch_spmv(const Batch &B, cudaStream_t s);
+packsell_status batch_create_mm(int count, const Matrix *const *A, int k, const float *const *X,
+                                const int64_t *ldx, float *const *Y, const int64_t *ldy,
+                                cudaStream_t s, Batch **out);
+packsell_status batch_spmm(const Batch &B, cudaStream_t s);
 void batch_free(Batch *B);
 void batch_stats(const Batch &B, int64_t *words, int64_t *bytes, int32_t *items);
 

@@ -228,6 +228,13 @@ packsell_status spmm_impl(const Matrix &A, int k, const float *X, int64_t ldx, f
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
     const bool vec = k % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 &&
                      ((uintptr_t)X & 15) == 0 && ((uintptr_t)Y & 15) == 0;
+    // CSR order (C = 1): split rows, all lanes of a warp sharing a tile's words
+    if (A.multi_items) {
+        const packsell_status st = launch_multi(split_mat(A, X, ldx, Y, ldy, k), nullptr,
+                                                (const MultiItem *)A.multi_items, A.multi_nitems, k,
+                                                vec, s);
+        return st;
+    }
     // lanes per row and column groups per lane: one pass for k <= 128
     if (k <= 4) launch_spmm_v<1, 1>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);
     else if (k <= 8) launch_spmm_v<1, 2>(vec, A, perm, pb, k, X, ldx, Y, ldy, s);

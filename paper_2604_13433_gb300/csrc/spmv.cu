@@ -888,6 +888,8 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
         if (st != PACKSELL_OK) return st;
         st = plan_split(A, s);
         if (st != PACKSELL_OK) return st;
+        st = multi_plan(A, s);
+        if (st != PACKSELL_OK) return st;
         // untuned default for CSR order: the split-row kernel (all lanes busy
         // on rows of any length); variant 11 keeps the stored-order chain
         if (A.split_items) A.auto_variant = 14;

@@ -108,6 +108,8 @@ SIGNATURES = {
     "packsell_spmv_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "packsell_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P]),
     "packsell_batch_spmv": (ctypes.c_int, [_P, _P]),
+    "packsell_batch_create_spmm": (ctypes.c_int, [_I32, _P, _I32, _P, _P, _P, _P, _P, _P]),
+    "packsell_batch_spmm": (ctypes.c_int, [_P, _P]),
     "packsell_batch_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "packsell_batch_destroy": (ctypes.c_int, [_P]),
 }
@@ -599,6 +601,59 @@ class PackSELLBatch:
 
 def packsell_batch_create(mats, xs, ys, stream=None) -> PackSELLBatch:
     return PackSELLBatch(mats, xs, ys, stream)
+
+
+class PackSELLBatchMM:
+    """A batched-SpMM plan (``packsell_batch*`` from packsell_batch_create_spmm):
+    Y_i = A_i X_i for C = 1 matrices, X_i [m_i x k] and Y_i [n_i x k] row-major
+    (leading dimension = row stride), kept alive with the plan."""
+
+    def __init__(self, mats, Xs, Ys, stream=None):
+        if not (len(mats) == len(Xs) == len(Ys)) or not mats:
+            raise ValueError("need equally many matrices, X and Y (at least one)")
+        k = int(Xs[0].shape[1])
+        cnt = len(mats)
+        for m, X, Y in zip(mats, Xs, Ys):
+            if X.dim() != 2 or Y.dim() != 2 or X.shape != (m.m, k) or Y.shape != (m.n, k):
+                raise ValueError("X_i must be [m_i x k] and Y_i [n_i x k]")
+            if X.dtype != torch.float32 or Y.dtype != torch.float32 or not X.is_cuda or not Y.is_cuda:
+                raise ValueError("X_i and Y_i must be float32 CUDA tensors")
+            if X.stride(1) != 1 or Y.stride(1) != 1:
+                raise ValueError("X_i and Y_i must be row-major (unit column stride)")
+        A = (ctypes.c_void_p * cnt)(*[m.handle.value for m in mats])
+        Xp = (ctypes.c_void_p * cnt)(*[X.data_ptr() for X in Xs])
+        Yp = (ctypes.c_void_p * cnt)(*[Y.data_ptr() for Y in Ys])
+        lx = (ctypes.c_int64 * cnt)(*[max(X.stride(0), k) for X in Xs])
+        ly = (ctypes.c_int64 * cnt)(*[max(Y.stride(0), k) for Y in Ys])
+        h = ctypes.c_void_p()
+        _check(lib().packsell_batch_create_spmm(cnt, A, k, Xp, lx, Yp, ly, _stream(stream),
+                                                ctypes.byref(h)))
+        self._h, self.mats, self.Xs, self.Ys, self.k = h, list(mats), list(Xs), list(Ys), k
+        w, b, it = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().packsell_batch_info(h, ctypes.byref(w), ctypes.byref(b), ctypes.byref(it)))
+        self.words, self.bytes, self.items = w.value, b.value, it.value
+
+    def spmm(self, stream=None):
+        _check(lib().packsell_batch_spmm(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().packsell_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def packsell_batch_create_spmm(mats, Xs, Ys, stream=None) -> PackSELLBatchMM:
+    return PackSELLBatchMM(mats, Xs, Ys, stream)
+
+
+def packsell_batch_spmm(B: PackSELLBatchMM, stream=None) -> None:
+    B.spmm(stream)
 
 
 def packsell_batch_spmv(B: PackSELLBatch, stream=None) -> None:

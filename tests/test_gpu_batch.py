@@ -53,6 +53,77 @@ def test_batch_matches_single_spmv_and_twin():
         assert np.array_equal(ys[j].cpu().numpy().view(np.uint32), twin.view(np.uint32))
 
 
+def _split_bound_check(y, csr, deq, X, words):
+    X = np.asarray(X, np.float64).reshape(csr.m, -1)
+    y = np.asarray(y, np.float64).reshape(csr.n, -1)
+    ref = O.csr_spmm_f64(csr, deq, X)
+    absref = O.csr_spmm_f64(csr, np.abs(deq), np.abs(X))
+    w = np.maximum(np.asarray(words, np.float64), 1.0)[:, None]
+    bound = (w * 2.0 ** -24 / (1 - w * 2.0 ** -24)) * absref
+    bad = np.argwhere(~(np.abs(y - ref) <= bound))
+    assert bad.size == 0, f"{len(bad)} entries beyond gamma_w, first {bad[:3].tolist()}"
+
+
+def test_batch_mixes_slice_heights():
+    """C = 32 and C = 1 (CSR order) matrices in one plan: the C = 32 ones give
+    packsell_spmv's bits, the C = 1 ones (split rows) stay within gamma_w of
+    the oracle; empty rows, sigma sorting and both orders among them."""
+    need_gpu()
+    ps = P()
+    rng = np.random.default_rng(3)
+    mats, csrs, xs, ys, encs = [], [], [], [], []
+    for i in range(30):
+        C = 1 if i % 2 else 32
+        csr = (I.zipf_irregular(int(rng.integers(500, 6000)), seed=200 + i) if i % 3 == 0 else
+               I.random_csr(int(rng.integers(1, 2500)), int(rng.integers(1, 2500)),
+                            float(rng.uniform(0.001, 0.02)), seed=i, empty_rows=0.1, long_gaps=True))
+        fmt, D = ("fp16", 15) if i % 4 < 2 else ("e8my", int(rng.integers(1, 16)))
+        sigma = [1, 64, 1, 256][i % 4]
+        expl = i % 5 == 0
+        mats.append(ps.packsell_encode_csr(csr, fmt=fmt, D=D, C=C, sigma=sigma, explicit_perm=expl))
+        encs.append(O.encode(csr, C=C, sigma=sigma, D=D, fmt=FMT[fmt]))
+        csrs.append(csr)
+        xs.append(dev(I.uniform(csr.m, seed=300 + i)))
+        ys.append(torch.full((csr.n,), float("nan"), device="cuda"))
+    B = ps.packsell_batch_create(mats, xs, ys)
+    B.spmv()
+    torch.cuda.synchronize()
+    for A, csr, x, y, enc in zip(mats, csrs, xs, ys, encs):
+        yv = y.cpu().numpy()
+        if A.C == 32:
+            ref = ps.packsell_spmv(A, x)
+            assert torch.equal(y.view(torch.int32), ref.view(torch.int32))
+            continue
+        if A.explicit_perm:
+            yo = np.empty_like(yv)
+            yo[O.storage_rows(enc)] = yv
+            yv = yo
+        _split_bound_check(yv, csr, enc.deq, x.cpu().numpy(), enc.words)
+
+
+@pytest.mark.parametrize("k", [1, 4, 16])
+def test_batched_spmm_csr_order(k):
+    """Batched SpMM over C = 1 matrices in one launch: every Y_i within
+    gamma_w of the oracle's product; k = 1 takes the one-column form."""
+    need_gpu()
+    ps = P()
+    batch = I.zipf_batch(24, seed=9, nmin=200, nmax=20000)
+    mats, Xs, Ys, encs = [], [], [], []
+    for j, c in enumerate(batch):
+        fmt, D = ("fp16", 15) if j % 2 else ("e8my", 9)
+        mats.append(ps.packsell_encode_csr(c, fmt=fmt, D=D, C=1, sigma=1))
+        encs.append(O.encode(c, C=1, sigma=1, D=D, fmt=FMT[fmt]))
+        Xs.append(dev(np.random.default_rng(j).uniform(-1, 1, (c.m, k)).astype(np.float32)))
+        Ys.append(torch.full((c.n, k), float("nan"), device="cuda"))
+    B = ps.packsell_batch_create_spmm(mats, Xs, Ys)
+    B.spmm()
+    torch.cuda.synchronize()
+    for c, X, Y, enc in zip(batch, Xs, Ys, encs):
+        _split_bound_check(Y.cpu().numpy(), c, enc.deq, X.cpu().numpy(), enc.words)
+    with pytest.raises(ps.PackSELLError):  # an SpMM plan does not run as a batched SpMV
+        ps._check(ps.lib().packsell_batch_spmv(B._h, None))
+
+
 def test_batch_rejects_bad_matrices():
     need_gpu()
     ps = P()
@@ -64,3 +135,7 @@ def test_batch_rejects_bad_matrices():
     A8 = ps.packsell_encode_csr(csr, fmt="fp16", C=8)
     with pytest.raises(ps.PackSELLError):
         ps.packsell_batch_create([A8], [x], [y])
+    A32 = ps.packsell_encode_csr(csr, fmt="fp16", C=32)
+    X, Y = torch.zeros(100, 4, device="cuda"), torch.empty(100, 4, device="cuda")
+    with pytest.raises(ps.PackSELLError):  # batched SpMM takes C = 1 matrices only
+        ps.packsell_batch_create_spmm([A32], [X], [Y])

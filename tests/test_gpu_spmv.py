@@ -450,9 +450,50 @@ def test_spmm_strided_layouts(fmt, C, sigma, explicit, k):
     Y = Y[:, 2:k + 2]
     if explicit:
         Y = Y[np.argsort(O.storage_rows(O.encode(csr, C=C, sigma=sigma, D=15, fmt=O.FMT_FP16)))]
+    if C == 1 and enc is not None:  # CSR order: the split-row SpMM, held to gamma_w
+        assert_within_bound(Y, csr, deq, Xw[:, 1:k + 1], enc.words)
+        return
     for r in range(k):
         twin = O.csr_spmv_fma_f32(csr, deq.astype(np.float32), np.ascontiguousarray(Xw[:, r + 1]))
         assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32)), f"column {r}"
+
+
+def assert_within_bound(Y, csr, deq, X, words):
+    """Every entry of Y (original row order) within gamma_w * sum_j |a_ij X_jq|
+    of the oracle's FP64 product, w the stored words of the row."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    ref = O.csr_spmm_f64(csr, deq, X)
+    absref = O.csr_spmm_f64(csr, np.abs(deq), np.abs(X))
+    w = np.maximum(np.asarray(words, np.float64), 1.0)[:, None]
+    u = 2.0 ** -24
+    bound = (w * u / (1 - w * u)) * absref
+    bad = np.argwhere(~(np.abs(Y.astype(np.float64) - ref) <= bound))
+    assert bad.size == 0, f"{len(bad)} entries beyond gamma_w, first {bad[:3].tolist()}"
+
+
+@pytest.mark.parametrize("fmt,D,sigma,k", [("fp16", 15, 1, 4), ("e8my", 11, 1, 16), ("fp16", 15, 256, 64),
+                                           ("e8my", 5, 1, 3), ("fp16", 15, 1, 1), ("e8my", 3, 100, 8)])
+def test_spmm_csr_order_split_rows(fmt, D, sigma, k):
+    """SpMM on CSR-order matrices (C = 1) runs the split-row kernel: power-law
+    rows up to 4,096 words (tiles and long rows), four columns per pass,
+    every entry within gamma_w of the oracle, the same bits on a second run;
+    k = 1 with a strided X takes the one-column form."""
+    need_gpu()
+    packsell = P()
+    csr = I.zipf_irregular(20000, seed=40 + k)
+    enc = O.encode(csr, C=1, sigma=sigma, D=D, fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, D=D, C=1, sigma=sigma)
+    X = np.random.default_rng(k).uniform(-1, 1, (csr.m, k)).astype(np.float32)
+    if k == 1:  # a column of a wider array: not the SpMV route
+        Xw = dev(np.repeat(X, 2, axis=1))
+        Xd, Yd = Xw[:, :1], torch.empty(csr.n, 2, device="cuda")[:, :1]
+    else:
+        Xd, Yd = dev(X), torch.empty(csr.n, k, device="cuda")
+    packsell.packsell_spmm(A, Xd, Yd)
+    Y1 = Yd.cpu().numpy().copy()
+    packsell.packsell_spmm(A, Xd, Yd)
+    assert np.array_equal(Y1.view(np.uint32), Yd.cpu().numpy().view(np.uint32))
+    assert_within_bound(Y1, csr, enc.deq, X, enc.words)
 
 
 @pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 3), ("sell_f32", 15)])
