@@ -94,6 +94,8 @@ def lib():
                                             ctypes.c_int]
         L.orc_quantize.argtypes = [i64, P, i32, i32, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -109,6 +111,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the OpenMP loops (the host baseline's 1-core and all-core runs)."""
+    lib().orc_set_threads(int(n))
 
 
 # --------------------------------------------------------------------------

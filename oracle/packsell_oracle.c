@@ -533,6 +533,17 @@ int orc_quantize(int64_t nnz, const double *val, int32_t fmt, int32_t D, uint32_
     return ORC_OK;
 }
 
+/* Set the number of threads of the OpenMP loops above (timing of the host
+ * baseline on one core and on all cores; no effect without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of threads the OpenMP loops above use (1 without OpenMP). */
 int orc_num_threads(void)
 {
