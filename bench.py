@@ -47,7 +47,7 @@ KERNEL_SOURCES = ("spmv.cu", "device.cuh", "reduce.cuh")
 KERNEL_NAMES = {1: "k_spmv_packed", 2: "k_spmv_bulk", 3: "k_spmv_bulk", 4: "k_spmv_bulk",
                 5: "k_spmv_prefetch", 6: "k_spmv_prefetch", 7: "k_spmv_dual", 8: "k_spmv_dual",
                 9: "k_spmv_stage", 10: "k_spmv_stage", 11: "k_spmv_csr", 12: "k_spmv_pipe",
-                13: "k_spmv_prefetch"}
+                13: "k_spmv_prefetch", 14: "k_spmv_split"}
 
 
 def parse():
