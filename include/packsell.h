@@ -342,6 +342,58 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant);
 packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
                                    float *h_times, void *stream);
 
+/* The value quantiser of §4.2.2 on its own (step one of the encoder): field[p]
+ * = the value field of val[p] in `format` with D delta bits, as it sits in a
+ * word's upper bits (FP16: the binary16 pattern << 16, round to nearest
+ * even, D = 15; E8MY: the FP32 pattern rounded half away from zero with the
+ * low D + 1 bits clear, D in [1, 22]; W16_E4M3: the FP8 E4M3 code, D = 7).
+ * val: float [n] (val_is_f64 = 0) or double [n] (1), device; field: uint32
+ * [n], device. SYNCHRONISES `stream`. Errors: INVALID_ARG (format, D),
+ * RANGE (a value rounds past the format's largest), NONFINITE (Inf or NaN);
+ * on those *h_bad_index (nullable, host) receives the first offending index
+ * found and the fields are unspecified. */
+packsell_status packsell_quantize(int32_t format, int32_t D, int64_t n, const void *val,
+                                  int32_t val_is_f64, uint32_t *field, int64_t *h_bad_index,
+                                  void *stream);
+
+/* One candidate of packsell_tune_format. */
+typedef struct packsell_format_trial {
+    packsell_params params; /* C, sigma, D, format tried (implicit permutation) */
+    double error;       /* bound on the SpMV backward error of §5.1.2 with this value format */
+    int32_t admissible; /* 1: every value fits and error <= the ceiling (then timed) */
+    int32_t variant;    /* fastest SpMV variant (0: not timed) */
+    int64_t n_words;    /* stored words (0: not timed) */
+    double bytes;       /* algorithmic bytes of one SpMV (0: not timed) */
+    double ms;          /* milliseconds per SpMV with that variant (0: not timed) */
+} packsell_format_trial;
+
+/* Autotuner of the format's knobs (the paper leaves them to the user: slice
+ * height and sort block of §3, delta/value split D and value format of
+ * §4.2-§4.3, whose accuracy §5.1.2 measures as a backward error). For a CSR
+ * matrix (device arrays as packsell_encode) and a backward-error ceiling:
+ *  1. for each value format - FP16 (D = 15) and E8MY with D = 15, 11, 7, 3,
+ *     1 (E8M7 .. E8M21) - a kernel bounds the backward error
+ *     ||y - A x||_inf / (||A||_inf ||x||_inf) of an SpMV with it by
+ *     (max_i sum_j |a_ij - q(a_ij)| + gamma_w max_i sum_j |q(a_ij)|) /
+ *     max_i sum_j |a_ij|, w = twice the longest row (each nonzero takes at
+ *     most one dummy), gamma_w = w u / (1 - w u), u = 2^-24;
+ *  2. every format within the ceiling is encoded in each layout - C = 32
+ *     with sigma = 256 and sigma = 65,536, and C = 1 (CSR order) - and its
+ *     SpMV variants timed as packsell_tune_spmv does (on the caller's x [m]
+ *     and y [n], `reps` launches each; y is overwritten);
+ *  3. *best = the parameters of the fastest (implicit permutation, k_left
+ *     computed), to pass to packsell_encode.
+ * h_trials (host, max_trials entries, nullable when max_trials = 0) receives
+ * every candidate in the order above (18 at most), *n_trials (nullable)
+ * their count. SYNCHRONISES `stream`; allocates and frees each candidate.
+ * Errors: INVALID_ARG, RANGE (no format within the ceiling), and those of
+ * packsell_encode. */
+packsell_status packsell_tune_format(int64_t n, int64_t m, int64_t nnz, const int64_t *rowptr,
+                                     const int32_t *col, const void *val, int32_t val_is_f64,
+                                     double max_error, const float *x, float *y, int32_t reps,
+                                     packsell_params *best, packsell_format_trial *h_trials,
+                                     int32_t max_trials, int32_t *n_trials, void *stream);
+
 /* Housekeeping (no counterpart in the paper): read and clear the matrix's
  * device status word (synchronises `stream`).
  * Returns PACKSELL_ERR_TIMEOUT if a kernel's bounded wait on a shared-memory

@@ -295,19 +295,20 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     return PACKSELL_OK;
 }
 
-packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
-                                   float *h_times, void *stream) {
-    clear_error();
-    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y) || reps < 1)
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
-    Matrix *m = reinterpret_cast<Matrix *>(A);
-    cudaStream_t s = as_stream(stream);
+namespace packsell {
+// Time every SpMV variant available for the matrix (`reps` launches each
+// after three untimed ones, CUDA events on `s`); the fastest in *best_var.
+static packsell_status tune_variants(Matrix *m, const float *x, float *y, int reps, float *h_times,
+                                     cudaStream_t s, int *best_var, float *best_ms_out) {
     const int nvar = PACKSELL_SPMV_VARIANTS;
     if (h_times)
         for (int v = 0; v < nvar; ++v) h_times[v] = 0.f;
     cudaEvent_t e0, e1;
     PS_CUDA(cudaEventCreate(&e0));
-    PS_CUDA(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(PACKSELL_ERR_CUDA, "packsell_tune_spmv: event");
+    }
     const int keep = m->variant;
     int best = m->auto_variant;
     float best_ms = 0.f;
@@ -342,8 +343,113 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     m->variant = keep;
-    if (st == PACKSELL_OK) m->auto_variant = best;
+    if (st == PACKSELL_OK) {
+        m->auto_variant = best;
+        if (best_var) *best_var = best;
+        if (best_ms_out) *best_ms_out = best_ms;
+    }
     return st;
+}
+}  // namespace packsell
+
+packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y, int32_t reps,
+                                   float *h_times, void *stream) {
+    clear_error();
+    if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y) || reps < 1)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
+    return tune_variants(reinterpret_cast<Matrix *>(A), x, y, reps, h_times, as_stream(stream),
+                         nullptr, nullptr);
+}
+
+packsell_status packsell_quantize(int32_t format, int32_t D, int64_t n, const void *val,
+                                  int32_t val_is_f64, uint32_t *field, int64_t *h_bad_index,
+                                  void *stream) {
+    clear_error();
+    if (n < 0 || (n > 0 && (!val || !field)))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_quantize: bad argument");
+    return quantize_impl(format, D, n, val, val_is_f64, field, h_bad_index, as_stream(stream));
+}
+
+packsell_status packsell_tune_format(int64_t n, int64_t m, int64_t nnz, const int64_t *rowptr,
+                                     const int32_t *col, const void *val, int32_t val_is_f64,
+                                     double max_error, const float *x, float *y, int32_t reps,
+                                     packsell_params *best, packsell_format_trial *h_trials,
+                                     int32_t max_trials, int32_t *n_trials, void *stream) {
+    clear_error();
+    if (n < 1 || m < 1 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)) || !x || !y ||
+        !best || reps < 1 || !(max_error > 0.0) || (max_trials > 0 && !h_trials) || max_trials < 0)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_format: bad argument");
+    cudaStream_t s = as_stream(stream);
+    // value formats, most value bits last; layouts of §3 (SELL-C-sigma) and CSR order
+    struct Fmt { int fmt, D; };
+    const Fmt fmts[] = {{PACKSELL_FMT_FP16, 15}, {PACKSELL_FMT_E8MY, 15}, {PACKSELL_FMT_E8MY, 11},
+                        {PACKSELL_FMT_E8MY, 7},  {PACKSELL_FMT_E8MY, 3},  {PACKSELL_FMT_E8MY, 1}};
+    struct Lay { int C, sigma; };
+    const Lay lays[] = {{32, 256}, {32, 65536}, {1, 1}};
+    const double u = 0x1p-24;
+    double err[6];
+    bool ok[6];
+    for (int f = 0; f < 6; ++f) {
+        double e[3];
+        int64_t maxlen = 0;
+        int bad = 0;
+        const packsell_status st = format_error_impl(n, rowptr, val, val_is_f64, fmts[f].fmt, fmts[f].D,
+                                                     s, e, &maxlen, &bad);
+        if (st != PACKSELL_OK) return st;
+        // |y_hat - A x|_i <= (sum_j |a_ij - q(a_ij)| + gamma_w sum_j |q(a_ij)|) ||x||_inf with
+        // w <= 2 nnz_i stored words (one dummy per nonzero at most, 32-bit words)
+        const double w = 2.0 * (double)std::max<int64_t>(maxlen, 1);
+        const double gw = w * u / (1.0 - w * u);
+        err[f] = e[2] > 0.0 ? (e[0] + gw * e[1]) / e[2] : 0.0;
+        ok[f] = bad == 0 && err[f] <= max_error;
+    }
+    int count = 0, best_i = -1;
+    double best_ms = 0.0;
+    packsell_params bp{};
+    for (const Lay &L : lays) {
+        for (int f = 0; f < 6; ++f) {
+            packsell_params p;
+            packsell_params_default(&p);
+            p.C = L.C;
+            p.sigma = L.sigma;
+            p.D = fmts[f].D;
+            p.format = fmts[f].fmt;
+            packsell_format_trial t{};
+            t.params = p;
+            t.error = err[f];
+            t.admissible = ok[f] ? 1 : 0;
+            if (ok[f]) {
+                Matrix *Am = nullptr;
+                packsell_status st = encode_impl(p, n, m, nnz, rowptr, col, val, val_is_f64, s, &Am);
+                if (st != PACKSELL_OK) return st;
+                int var = 0;
+                float ms = 0.f;
+                st = tune_variants(Am, x, y, reps, nullptr, s, &var, &ms);
+                t.variant = var;
+                t.ms = ms;
+                t.n_words = Am->n_words;
+                t.bytes = 4.0 * (double)Am->n_words + 8.0 * (double)(Am->n_slices + 1) +
+                          (double)Am->perm_bytes * (double)n + 4.0 * (double)(m + n);
+                cudaStreamSynchronize(s);
+                destroy_matrix(Am);
+                if (st != PACKSELL_OK) return st;
+                if (best_i < 0 || ms < best_ms) {
+                    best_i = count;
+                    best_ms = ms;
+                    bp = p;
+                }
+            }
+            if (count < max_trials) h_trials[count] = t;
+            ++count;
+        }
+    }
+    if (n_trials) *n_trials = std::min(count, max_trials);
+    if (best_i < 0)
+        return fail(PACKSELL_ERR_RANGE, "packsell_tune_format: no format meets the error ceiling "
+                                        "(the finest, E8M21, bounds it by " +
+                                            std::to_string(err[5]) + ")");
+    *best = bp;
+    return PACKSELL_OK;
 }
 
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream) {

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -752,6 +753,123 @@ __global__ void k_storage_rows(int n, int sigma, const void *perm, int perm_byte
                                int32_t *__restrict__ rows) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         rows[i] = orig_row(i, sigma, perm, perm_bytes);
+}
+
+// ---- quantisation on its own, and the quantisation error of a format ----
+namespace {
+
+// Per row: s_err = sum |a_ij - q(a_ij)|, s_q = sum |q(a_ij)|, s_a = sum |a_ij|
+// in double, then the maxima over the rows (non-negative doubles order as
+// their bit patterns, so the maxima are atomicMax on the patterns). A value
+// the format cannot hold sets `bad`.
+template <typename T>
+__global__ void k_format_error(int n, const int64_t *__restrict__ rowptr, const T *__restrict__ val,
+                               int fmt, int D, unsigned long long *out, int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double se = 0.0, sq = 0.0, sa = 0.0;
+    unsigned long long len = 0;
+    if (i < n) {
+        const int64_t a = rowptr[i], b = rowptr[i + 1];
+        len = (unsigned long long)(b - a);
+        for (int64_t p = a; p < b; ++p) {
+            const T v = val[p];
+            uint32_t f = 0;
+            const int err = fmt == PACKSELL_FMT_FP16 ? field_fp16(v, f) : field_e8my(v, D, f);
+            if (err) {
+                atomicExch(bad, err);
+                continue;
+            }
+            const double q = fmt == PACKSELL_FMT_FP16
+                                 ? (double)__half2float(__ushort_as_half((unsigned short)(f >> 16)))
+                                 : (double)__uint_as_float(f);
+            se += fabs((double)v - q);
+            sq += fabs(q);
+            sa += fabs((double)v);
+        }
+    }
+    unsigned long long e = __double_as_longlong(se), q = __double_as_longlong(sq),
+                       aa = __double_as_longlong(sa);
+    // a warp's maxima in full 64-bit precision: a shuffle reduction
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        q = max(q, __shfl_xor_sync(0xffffffffu, q, o));
+        aa = max(aa, __shfl_xor_sync(0xffffffffu, aa, o));
+        len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, e);
+        atomicMax(out + 1, q);
+        atomicMax(out + 2, aa);
+        atomicMax(out + 3, len);
+    }
+}
+
+}  // namespace
+
+packsell_status quantize_impl(int fmt, int D, int64_t n, const void *val, int is64, uint32_t *field,
+                              int64_t *bad_index, cudaStream_t s) {
+    if (bad_index) *bad_index = -1;
+    if (!(fmt == PACKSELL_FMT_FP16 && D == 15) && !(fmt == PACKSELL_FMT_E8MY && D >= 1 && D <= 22) &&
+        !(fmt == PACKSELL_FMT_W16_E4M3 && D == 7))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_quantize: bad format or D");
+    if (n == 0) return PACKSELL_OK;
+    DevStatus *st = nullptr;
+    PS_CUDA(cudaMallocAsync(&st, sizeof(DevStatus), s));
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    const int qb = (int)std::min<int64_t>((n + TPB - 1) / TPB, 152 * 32);
+    if (e == cudaSuccess) {
+        if (is64) k_quantize<double><<<qb, TPB, 0, s>>>(n, (const double *)val, fmt, D, field, st);
+        else k_quantize<float><<<qb, TPB, 0, s>>>(n, (const float *)val, fmt, D, field, st);
+        e = cudaGetLastError();
+    }
+    DevStatus h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(st, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_quantize");
+    if (h.code) {
+        if (bad_index) *bad_index = h.index;
+        return fail((packsell_status)h.code, "packsell_quantize: value " + std::to_string(h.index) +
+                                                 (h.code == PACKSELL_ERR_RANGE ? " overflows the format"
+                                                                               : " is not finite"));
+    }
+    return PACKSELL_OK;
+}
+
+packsell_status format_error_impl(int64_t n, const int64_t *rowptr, const void *val, int is64,
+                                  int fmt, int D, cudaStream_t s, double out[3], int64_t *max_len,
+                                  int *bad) {
+    out[0] = out[1] = out[2] = 0.0;
+    *max_len = 0;
+    *bad = 0;
+    if (n == 0) return PACKSELL_OK;
+    unsigned long long *d = nullptr;
+    PS_CUDA(cudaMallocAsync(&d, 4 * sizeof(unsigned long long) + sizeof(int), s));
+    int *dbad = reinterpret_cast<int *>(d + 4);
+    cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long) + sizeof(int), s);
+    if (e == cudaSuccess) {
+        if (is64)
+            k_format_error<double><<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, (const double *)val,
+                                                                  fmt, D, d, dbad);
+        else
+            k_format_error<float><<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, (const float *)val,
+                                                                 fmt, D, d, dbad);
+        e = cudaGetLastError();
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "packsell_tune_format: quantisation error");
+    for (int k = 0; k < 3; ++k) {
+        double v;
+        memcpy(&v, &h[k], sizeof v);
+        out[k] = v;
+    }
+    *max_len = (int64_t)h[3];
+    return PACKSELL_OK;
 }
 
 packsell_status storage_rows_impl(const Matrix &A, int32_t *rows, cudaStream_t s) {

@@ -85,7 +85,16 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
                             const int64_t *rowptr, const int32_t *col, const void *val,
                             int val_is_f64, cudaStream_t s, Matrix **out);
 packsell_status validate_impl(const Matrix &A, cudaStream_t s);
+void destroy_matrix(Matrix *A);
 packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_t s);
+packsell_status quantize_impl(int fmt, int D, int64_t n, const void *val, int is64, uint32_t *field,
+                              int64_t *bad_index, cudaStream_t s);
+// max_i sum_j |a_ij - q(a_ij)|, max_i sum_j |q(a_ij)|, max_i sum_j |a_ij| for a
+// format (out[0..2]), the longest row, and a nonzero *bad if a value does
+// not fit the format
+packsell_status format_error_impl(int64_t n, const int64_t *rowptr, const void *val, int is64,
+                                  int fmt, int D, cudaStream_t s, double out[3], int64_t *max_len,
+                                  int *bad);
 
 // stage.cu
 packsell_status plan_stage(Matrix &A, cudaStream_t s);

@@ -60,6 +60,12 @@ class Info(ctypes.Structure):
                 ("col", ctypes.c_void_p), ("offset", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
 
 
+class FormatTrial(ctypes.Structure):
+    _fields_ = [("params", Params), ("error", ctypes.c_double), ("admissible", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("n_words", ctypes.c_int64), ("bytes", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("m_in", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
@@ -93,6 +99,9 @@ SIGNATURES = {
     "packsell_set_spmv_variant": (ctypes.c_int, [_P, _I32]),
     "packsell_check_status": (ctypes.c_int, [_P, _P]),
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
+    "packsell_quantize": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P]),
+    "packsell_tune_format": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, ctypes.c_double,
+                                            _P, _P, _I32, _P, _P, _I32, _P, _P]),
     "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
     "packsell_pcg": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
     "packsell_pcg_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -214,6 +223,59 @@ def packsell_encode(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, 
         _dev(val, val.dtype, "val", nnz) if nnz else None, int(val.dtype == torch.float64),
         _stream(stream), ctypes.byref(h)))
     return PackSELLMatrix(h.value)
+
+
+def packsell_quantize(val: torch.Tensor, fmt="fp16", D: int = 15, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """The value quantiser of §4.2.2 on a CUDA tensor (float32 or float64):
+    the uint32 value fields (as an int32 tensor of the same bits) that the
+    encoder places in the words' upper bits."""
+    fmt_code = _FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    if val.dtype not in (torch.float32, torch.float64):
+        raise TypeError("val must be float32 or float64")
+    n = val.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=val.device)
+    bad = ctypes.c_int64(-1)
+    _check(lib().packsell_quantize(fmt_code, D, n, _dev(val, val.dtype, "val", n) if n else None,
+                                   int(val.dtype == torch.float64),
+                                   _dev(out, torch.int32, "out", n) if n else None,
+                                   ctypes.byref(bad), _stream(stream)))
+    return out
+
+
+_FORMAT_NAMES = {FMT_FP16: "fp16", FMT_E8MY: "e8my"}
+
+
+def packsell_tune_format(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, n: int,
+                         m: int, max_error: float, x: torch.Tensor, y: torch.Tensor | None = None,
+                         reps: int = 20, stream=None):
+    """Pick slice height, sort block, value format and delta bits for a CSR
+    matrix under a backward-error ceiling (packsell_tune_format). Returns
+    (params, trials): params a dict of the keyword arguments for
+    packsell_encode (C, sigma, D, fmt), trials one dict per candidate."""
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+    if val.dtype not in (torch.float32, torch.float64):
+        raise TypeError("val must be float32 or float64")
+    nnz = col.numel()
+    best = Params()
+    cap = 32
+    trials = (FormatTrial * cap)()
+    cnt = ctypes.c_int32()
+    _check(lib().packsell_tune_format(
+        n, m, nnz, _dev(rowptr, torch.int64, "rowptr", n + 1), _dev(col, torch.int32, "col"),
+        _dev(val, val.dtype, "val", nnz), int(val.dtype == torch.float64), float(max_error),
+        _dev(x, torch.float32, "x", m), _dev(y, torch.float32, "y", n), reps, ctypes.byref(best),
+        trials, cap, ctypes.byref(cnt), _stream(stream)))
+    params = {"C": best.C, "sigma": best.sigma, "D": best.D, "fmt": _FORMAT_NAMES[best.format]}
+    out = []
+    for t in trials[:cnt.value]:
+        out.append({"C": t.params.C, "sigma": t.params.sigma, "D": t.params.D,
+                    "fmt": _FORMAT_NAMES[t.params.format], "error": t.error,
+                    "admissible": bool(t.admissible), "variant": t.variant, "n_words": t.n_words,
+                    "bytes": t.bytes, "ms": t.ms})
+    return params, out
 
 
 def _host(a: np.ndarray, dtype, name: str) -> np.ndarray:
