@@ -394,6 +394,18 @@ packsell_status packsell_tune_format(int64_t n, int64_t m, int64_t nnz, const in
                                      packsell_params *best, packsell_format_trial *h_trials,
                                      int32_t max_trials, int32_t *n_trials, void *stream);
 
+/* Diagnostics (no counterpart in the paper): the number of polls after
+ * which the TMA-staged SpMV variants (2-4, 9, 10) give up waiting for a
+ * chunk of words to land in shared memory; polls < 0 restores the default
+ * (2^24). A kernel that gives up records PACKSELL_ERR_TIMEOUT in the
+ * matrix's status word (packsell_check_status), skips the rest of its rows
+ * (their y entries are left as they were), and before it returns waits -
+ * with the default limit, whatever is set here - for every copy it has
+ * issued. polls = 0 makes every such wait give up at once: the way to
+ * exercise that path. Applies to later launches in the process, on every
+ * device; not to be changed while SpMVs of those variants run. */
+packsell_status packsell_set_wait_limit(int64_t polls);
+
 /* Housekeeping (no counterpart in the paper): read and clear the matrix's
  * device status word (synchronises `stream`).
  * Returns PACKSELL_ERR_TIMEOUT if a kernel's bounded wait on a shared-memory

@@ -452,6 +452,13 @@ packsell_status packsell_tune_format(int64_t n, int64_t m, int64_t nnz, const in
     return PACKSELL_OK;
 }
 
+packsell_status packsell_set_wait_limit(int64_t polls) {
+    clear_error();
+    set_data_wait_limit(polls < 0 ? kWaitLimit
+                                  : (uint32_t)std::min<int64_t>(polls, (int64_t)UINT32_MAX));
+    return PACKSELL_OK;
+}
+
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream) {
     clear_error();
     if (!A) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_check_status: NULL matrix");

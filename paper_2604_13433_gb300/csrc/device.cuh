@@ -171,10 +171,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false if it ran out.
-constexpr uint32_t kWaitLimit = 1u << 24;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+// Bounded wait for the phase with the given parity: at most `limit` polls;
+// false if it ran out. The kernels' waits for data take the limit set by
+// packsell_set_wait_limit (kWaitLimit by default); the drain of copies
+// already issued, before a kernel that gave up returns, always takes
+// kWaitLimit, so that every copy lands before the block's shared memory is
+// released.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

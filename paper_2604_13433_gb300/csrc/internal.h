@@ -150,6 +150,9 @@ packsell_status launch_stage(const Matrix &A, int v, const void *perm, int pb, c
                              float *y, cudaStream_t s);
 
 // spmv.cu
+constexpr uint32_t kWaitLimit = 1u << 24;  // default polls of a bounded mbarrier wait
+uint32_t data_wait_limit();
+void set_data_wait_limit(uint32_t limit);
 packsell_status plan_spmv(Matrix &A, cudaStream_t s);
 packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_t s);
 packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaStream_t s);

@@ -239,6 +239,89 @@ __global__ void __launch_bounds__(TPB, MINB)
     if (DOT) reduce_publish(red, (double)d1, 0.0);
 }
 
+// The same pipelined structure over FP32 SELL (C = 32, every slice within PF
+// slots) fused with sum_i x_i y_i: the solver's inner product with an FP32
+// SELL matrix, so that the FP32-SELL inner solve is compared with the
+// PackSELL one on kernels of the same form. Each thread loads the next row's
+// values and columns before it gathers the current row; a row multiplies
+// exactly its slice's w slots in stored order (the bits of k_spmv_sell).
+template <int PF, int MINB, bool PERM>
+__global__ void __launch_bounds__(TPB, MINB)
+    k_sell_pipe_dot(int n, int sigma, int sig_shift, const int64_t *__restrict__ offset,
+                    const float *__restrict__ val, const int32_t *__restrict__ col,
+                    const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
+                    float *__restrict__ y, Red red) {
+    float d1 = 0.f;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float cv[PF];
+    int cc[PF], w = 0;
+    int in = i + stride;
+    int64_t sn = 0, en = 0;
+    if (i < n) {
+        const int64_t s = offset[i >> 5];
+        w = (int)((offset[(i >> 5) + 1] - s) >> 5);
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            cv[u] = u < w ? __ldcs(val + s + (i & 31) + u * 32) : 0.f;
+            cc[u] = u < w ? __ldcs(col + s + (i & 31) + u * 32) : 0;
+        }
+        if (in < n) {
+            sn = offset[in >> 5];
+            en = offset[(in >> 5) + 1];
+        }
+    }
+    // the matrix is complete before any solve: its words load before the wait
+    grid_dep_sync();
+    if (red.sc->done) return;  // solver converged: idle (grid-uniform)
+    if (i < n) {
+        while (true) {
+            const int wn = (int)((en - sn) >> 5);
+            float nv[PF];
+            int nc[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const bool ok = in < n && u < wn;
+                nv[u] = ok ? __ldcs(val + sn + (in & 31) + u * 32) : 0.f;
+                nc[u] = ok ? __ldcs(col + sn + (in & 31) + u * 32) : 0;
+            }
+            const int in2 = in + stride;
+            int64_t sn2 = 0, en2 = 0;
+            if (in2 < n) {
+                sn2 = offset[in2 >> 5];
+                en2 = offset[(in2 >> 5) + 1];
+            }
+            float xv[PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) xv[u] = u < w ? __ldg(x + cc[u]) : 0.f;
+            float t = 0.f;
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+                if (u < w) t = fmaf(cv[u], xv[u], t);
+            int io = i;
+            if (PERM) {
+                const int blk = sig_shift >= 0 ? (i >> sig_shift) << sig_shift : (i / sigma) * sigma;
+                io = blk + (perm_bytes == 1 ? (int)((const uint8_t *)perm)[i]
+                                            : (int)((const uint16_t *)perm)[i]);
+            }
+            y[io] = t;
+            d1 = fmaf(x[io], t, d1);
+            if (in >= n) break;
+            i = in;
+            w = wn;
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                cv[u] = nv[u];
+                cc[u] = nc[u];
+            }
+            in = in2;
+            sn = sn2;
+            en = en2;
+        }
+    }
+    reduce_publish(red, (double)d1, 0.0);
+}
+
 // Dual-row persistent SpMV: every thread handles two rows per loop trip, row
 // i (slice k) and row i + stride (another slice), in lockstep: the word loads
 // of both rows are issued before either is decoded, then both rows' gathers,
@@ -519,7 +602,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
                 const void *__restrict__ perm, int perm_bytes, Decode dc,
                 const float *__restrict__ x, float *__restrict__ y,
-                const int32_t *__restrict__ part, DevStatus *st) {
+                const int32_t *__restrict__ part, DevStatus *st, uint32_t wait_limit) {
     using R = BulkRing<NS, SW>;
     extern __shared__ __align__(128) uint32_t ring_all[];
     __shared__ __align__(8) uint64_t bars[NW][NS];
@@ -546,7 +629,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     // wait for chunks up to and including g (in order); false on timeout
     auto wait_upto = [&](int g) -> bool {
         for (; waited <= g; ++waited) {
-            bool ok = mbar_wait(&bar[waited % NS], (uint32_t)((waited / NS) & 1));
+            bool ok = mbar_wait(&bar[waited % NS], (uint32_t)((waited / NS) & 1), wait_limit);
             if (!__all_sync(0xffffffffu, ok)) return false;
         }
         return true;
@@ -675,8 +758,9 @@ packsell_status launch_bulk(const Matrix &A, int v, const void *perm, int pb, co
     int sigma = sg;
     const int64_t *offset = A.offset;
     const uint32_t *pack = A.pack;
+    uint32_t wl = data_wait_limit();
     void *kargs[] = {&n, &sigma, &sig_shift, &kl, (void *)&offset, (void *)&pack, (void *)&perm,
-                     &pb, &dc, (void *)&x, (void *)&y, (void *)&part, (void *)&st};
+                     &pb, &dc, (void *)&x, (void *)&y, (void *)&part, (void *)&st, &wl};
     PS_CUDA(cudaLaunchKernel(bulk_fn<FMT>(v), dim3(A.part_blocks[v]), dim3(cf.nw * 32), kargs,
                              cf.smem(), s));
     return PACKSELL_OK;
@@ -873,6 +957,11 @@ __global__ void __launch_bounds__(TPB)
 }
 
 }  // namespace
+
+// Polls of the staged kernels' waits for data (packsell_set_wait_limit).
+static std::atomic<uint32_t> g_wait_limit{kWaitLimit};
+uint32_t data_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+void set_data_wait_limit(uint32_t limit) { g_wait_limit.store(limit, std::memory_order_relaxed); }
 
 // Launch plan of the bulk-staged kernels: for each configuration a
 // persistent grid of as many blocks as fit on the device, and the per-warp
@@ -1173,6 +1262,23 @@ cudaError_t launch_pipe_dot(const Matrix &A, const float *x, float *y, const Red
                       make_decode(A), x, y, red);
 }
 
+template <int PF, int MINB>
+cudaError_t launch_sell_pipe_dot(const Matrix &A, const float *x, float *y, const Red &red,
+                                 cudaStream_t s) {
+    const int sg = A.p.sigma;
+    const int sh = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
+    if (A.perm_bytes) {
+        auto k = k_sell_pipe_dot<PF, MINB, true>;
+        return launch_pdl(k, (unsigned)dot_grid(k), TPB, s, (int)A.n, sg, sh, (const int64_t *)A.offset,
+                          (const float *)A.val, (const int32_t *)A.col, (const void *)A.perm,
+                          A.perm_bytes, x, y, red);
+    }
+    auto k = k_sell_pipe_dot<PF, MINB, false>;
+    return launch_pdl(k, (unsigned)dot_grid(k), TPB, s, (int)A.n, sg, sh, (const int64_t *)A.offset,
+                      (const float *)A.val, (const int32_t *)A.col, (const void *)A.perm, 0, x, y,
+                      red);
+}
+
 int spmv_dot_blocks(const Matrix &) { return reduce_blocks(); }
 
 packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Red &red,
@@ -1180,7 +1286,15 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
     const int g = device_sms() * 4;
     const void *perm = A.perm;
     const int pb = A.perm_bytes;
-    if (A.p.format == PACKSELL_FMT_SELL_F32) {
+    if (A.p.format == PACKSELL_FMT_SELL_F32 && A.p.C == 32 && A.max_width <= 16) {
+        // short rows: the pipelined form (the PackSELL inner solve's structure)
+        const int pf = round_words(A.max_width);
+        const cudaError_t e = pf == 8    ? launch_sell_pipe_dot<8, 4>(A, x, y, red, s)
+                              : pf == 10 ? launch_sell_pipe_dot<10, 3>(A, x, y, red, s)
+                              : pf == 12 ? launch_sell_pipe_dot<12, 3>(A, x, y, red, s)
+                                         : launch_sell_pipe_dot<16, 2>(A, x, y, red, s);
+        if (e != cudaSuccess) return cuda_fail(e, "spmv_dot_f32 (SELL, pipelined)");
+    } else if (A.p.format == PACKSELL_FMT_SELL_F32) {
         const cudaError_t e = launch_pdl(k_spmv_sell<float, true, true>, (unsigned)g, TPB, s,
                                          (int)A.n, A.p.C, A.p.sigma, (const int64_t *)A.offset,
                                          (const float *)A.val, (const int32_t *)A.col, perm, pb,

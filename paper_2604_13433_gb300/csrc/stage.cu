@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                  const void *__restrict__ perm, int perm_bytes, Decode dc,
                  const float *__restrict__ x, float *__restrict__ y,
                  const int32_t *__restrict__ part, const int64_t *__restrict__ sptr,
-                 const int32_t *__restrict__ sbnd, DevStatus *st) {
+                 const int32_t *__restrict__ sbnd, DevStatus *st, uint32_t wait_limit) {
     static_assert((NS & (NS - 1)) == 0, "NS: power of two");
     extern __shared__ __align__(128) uint32_t ring_all[];
     __shared__ __align__(8) uint64_t bars[NW][NS];
@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(NW * 32, MINB)
             gb = g;
             bl = (gb + lane <= nst) ? B[gb + lane] : 0;
         }
-        if (!__all_sync(0xffffffffu, mbar_wait(&bar[g & (NS - 1)], (uint32_t)((g / NS) & 1)))) {
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait(&bar[g & (NS - 1)], (uint32_t)((g / NS) & 1), wait_limit))) {
             if (lane == 0) dev_fail(st, PACKSELL_ERR_TIMEOUT, gw);
             for (int h = g; h < issued; ++h) mbar_wait(&bar[h & (NS - 1)], (uint32_t)((h / NS) & 1));
             return;
@@ -295,8 +296,10 @@ packsell_status launch_stage(const Matrix &A, int v, const void *perm, int pb, c
     const int32_t *part = P.part, *sb = P.sb;
     const int64_t *sptr = P.sptr;
     DevStatus *st = A.status;
+    uint32_t wl = data_wait_limit();
     void *args[] = {&n, &sg, &sh, &kl, (void *)&offset, (void *)&pack, (void *)&perm, &pb, &dc,
-                    (void *)&x, (void *)&y, (void *)&part, (void *)&sptr, (void *)&sb, (void *)&st};
+                    (void *)&x, (void *)&y, (void *)&part, (void *)&sptr, (void *)&sb, (void *)&st,
+                    &wl};
     void *fn = A.p.format == PACKSELL_FMT_FP16 ? stage_fn<PACKSELL_FMT_FP16>(v)
                                                : stage_fn<PACKSELL_FMT_E8MY>(v);
     PS_CUDA(cudaLaunchKernel(fn, dim3(P.blocks), dim3(cf.nw * 32), args, cf.smem(), s));

@@ -100,6 +100,7 @@ SIGNATURES = {
     "packsell_check_status": (ctypes.c_int, [_P, _P]),
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "packsell_quantize": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P]),
+    "packsell_set_wait_limit": (ctypes.c_int, [_I64]),
     "packsell_tune_format": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, ctypes.c_double,
                                             _P, _P, _I32, _P, _P, _I32, _P, _P]),
     "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
@@ -223,6 +224,12 @@ def packsell_encode(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, 
         _dev(val, val.dtype, "val", nnz) if nnz else None, int(val.dtype == torch.float64),
         _stream(stream), ctypes.byref(h)))
     return PackSELLMatrix(h.value)
+
+
+def packsell_set_wait_limit(polls: int) -> None:
+    """Polls before the TMA-staged SpMV variants give up a wait for data
+    (negative: the default); a diagnostics knob for the timeout path."""
+    _check(lib().packsell_set_wait_limit(int(polls)))
 
 
 def packsell_quantize(val: torch.Tensor, fmt="fp16", D: int = 15, out: torch.Tensor | None = None,

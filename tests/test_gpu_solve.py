@@ -52,9 +52,13 @@ def test_pcg_fp64_matches_oracle(graph):
     assert h[0] == pytest.approx(1.0) and h[-1] < 1e-10
 
 
-@pytest.mark.parametrize("fmt,D,m_in", [("fp16", 15, 20), ("e8my", 8, 20), ("e8my", 11, 50),
-                                        ("sell_f32", 15, 20)])
-def test_iocg_matches_oracle(fmt, D, m_in):
+@pytest.mark.parametrize("fmt,D,m_in,sigma", [("fp16", 15, 20, 256), ("e8my", 8, 20, 256),
+                                              ("e8my", 11, 50, 256), ("sell_f32", 15, 20, 256),
+                                              ("sell_f32", 15, 20, 1), ("fp16", 15, 20, 1)])
+def test_iocg_matches_oracle(fmt, D, m_in, sigma):
+    """IO-CG against the oracle's simulated-precision IO-CG; the inner
+    product runs the pipelined fused SpMV + dot for PackSELL and FP32 SELL
+    alike (7-point rows), with and without the sigma permutation."""
     need_gpu()
     ps = P()
     a = I.poisson7_varcoef(16, seed=3)  # unit diagonal (symmetrically scaled)
@@ -64,9 +68,9 @@ def test_iocg_matches_oracle(fmt, D, m_in):
         deq = a.val.astype(np.float32).astype(np.float64)
     xo, ko, _ = S.iocg(a, b, deq, m_in=m_in, tol=1e-10, max_outer=300)
     A64 = encode(a, "sell_f64")
-    Ain = encode(a, fmt, D=D) if fmt != "sell_f32" else P().packsell_encode_csr(
+    Ain = encode(a, fmt, D=D, sigma=sigma) if fmt != "sell_f32" else P().packsell_encode_csr(
         I.CSR(n=a.n, m=a.m, rowptr=a.rowptr, col=a.col, val=a.val.astype(np.float32)),
-        fmt="sell_f32")
+        fmt="sell_f32", sigma=sigma)
     x, info = ps.packsell_pcg(A64, dev(b), A_inner=Ain, m_in=m_in, rtol=1e-10, max_iters=300)
     assert info["relres_true"] < 1e-10
     assert close_count(info["iters"], ko), (info["iters"], ko)

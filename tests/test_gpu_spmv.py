@@ -518,3 +518,32 @@ def test_transpose_and_pattern_outer(fmt, D):
     row = np.repeat(np.arange(700), csr.row_lengths())
     want = (np.float32(-1.0) * dy[row]) * x[csr.col]
     assert np.array_equal(out.view(np.uint32), want.astype(np.float32).view(np.uint32))
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4, 9, 10])
+def test_bounded_wait_runs_out_and_reports_timeout(variant):
+    """The TMA-staged variants' waits for data are bounded. With the limit
+    at 0 polls every first wait gives up: the kernel records
+    PACKSELL_ERR_TIMEOUT in the matrix's status word, lets the copies it has
+    issued land (the drain keeps the default limit) and returns, and the GPU
+    stays usable; with the default limit restored the next launch gives the
+    twin's bits again and the status word reads clean."""
+    need_gpu()
+    ps = P()
+    csr = I.stencil27(24, seed=2)
+    A = encode_gpu(csr, fmt="fp16", C=32, sigma=256)
+    x = dev(I.uniform(csr.m, seed=3))
+    ps.packsell_set_spmv_variant(A, variant)
+    try:
+        ps.packsell_set_wait_limit(0)
+        ps.packsell_spmv(A, x)
+        with pytest.raises(ps.PackSELLError) as e:
+            ps.packsell_check_status(A)  # reads and clears the word
+        assert e.value.code == 10  # PACKSELL_ERR_TIMEOUT
+    finally:
+        ps.packsell_set_wait_limit(-1)
+    y = ps.packsell_spmv(A, x).cpu().numpy()
+    ps.packsell_check_status(A)
+    enc = O.encode(csr, C=32, sigma=256, D=15, fmt=O.FMT_FP16)
+    twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), x.cpu().numpy())
+    assert np.array_equal(y.view(np.uint32), twin.view(np.uint32))
