@@ -88,13 +88,23 @@ typedef enum packsell_status {
  *         packsell_spmv_host, packsell_get_info, packsell_storage_rows and
  *         packsell_export (2-byte words; packsell_import rejects the blob);
  *         the other calls return PACKSELL_ERR_INVALID_ARG for it.
+ * SELL_F16: plain SELL-C-sigma (§3) with binary16 values (round to nearest
+ *         even, as FP16 PackSELL) in a uint16 array and int32 columns, 48
+ *         bits per stored element: the FP16 SELL the paper compares
+ *         PackSELL with (§5.1.1) and the FP16 operator of FP16-F3R (§5.2.1).
+ *         Padding slots hold column -1 and add nothing, so a row's sum is the
+ *         chain of the FP16 PackSELL kernels over the same values: the same
+ *         bits. Supported by packsell_encode, packsell_spmv (one
+ *         thread-per-row kernel), packsell_get_info, packsell_storage_rows and
+ *         packsell_f3r; the other calls return PACKSELL_ERR_INVALID_ARG.
  */
 typedef enum packsell_format {
     PACKSELL_FMT_FP16 = 1,
     PACKSELL_FMT_E8MY = 2,
     PACKSELL_FMT_SELL_F32 = 3,
     PACKSELL_FMT_SELL_F64 = 4,
-    PACKSELL_FMT_W16_E4M3 = 5
+    PACKSELL_FMT_W16_E4M3 = 5,
+    PACKSELL_FMT_SELL_F16 = 6
 } packsell_format;
 
 typedef struct packsell_params {
@@ -637,6 +647,56 @@ packsell_status packsell_pcg_noalloc(const packsell_matrix *A_outer,
                                      const double *b, double *x,
                                      const packsell_solve_opts *opts, double *h_hist,
                                      packsell_solve_result *result, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* F3R: the nested Krylov solver of §5.2.1                                 */
+/* ---------------------------------------------------------------------- */
+
+typedef struct packsell_f3r_opts {
+    double rtol;        /* stop when ||b - A x||_2 / ||b||_2 < rtol (true residual, FP64) */
+    int32_t m1;         /* restart length of the outer FGMRES (layer 1), 1..60 */
+    int32_t m2;         /* FGMRES steps of layer 2 per application, 1..60 */
+    int32_t m3;         /* FGMRES steps of layer 3 per application, 1..60 */
+    int32_t m4;         /* Richardson steps of layer 4 per application, >= 1 */
+    int32_t max_iters;  /* outer FGMRES steps at most */
+    double omega;       /* Richardson damping, > 0 */
+} packsell_f3r_opts;
+
+/* Defaults: rtol = 1e-9 (the paper's criterion, §5.2), m1 = 30, m2 = 8,
+ * m3 = 4, m4 = 2, max_iters = 300, omega = 1. The paper takes F3R's own
+ * defaults from the work that defines it and does not print them; these are
+ * this library's choices. */
+void packsell_f3r_opts_default(packsell_f3r_opts *o);
+
+/* Solve A x = b with F3R (§5.2.1): FGMRES(m1) in FP64 on A_outer (restarted,
+ * x the initial guess on entry, the solution on exit), preconditioned by
+ * m2 steps of FGMRES on A_mid from zero, preconditioned by m3 steps of FGMRES
+ * on A_low from zero, preconditioned by m4 Richardson steps z <- z + omega
+ * (r - A_low z) from z = 0 (the Jacobi preconditioner is the identity on
+ * the symmetrically scaled matrices of §5.2: scale A beforehand).
+ * Configurations:
+ *  - FP16-F3R: A_mid SELL_F32 (layer 2 in FP32) and A_low a PackSELL FP16
+ *    (or E8MY) or an FP16 SELL matrix (layers 3 and 4: FP32 vectors, the
+ *    FP16 SpMV of the paper);
+ *  - FP64-F3R: A_mid and A_low SELL_F64 (every layer in FP64).
+ * A_outer is SELL_F64; all three square, of the same size, rows in original
+ * order (any C and sigma). Krylov bases by classical Gram-Schmidt with
+ * deterministic FP64 dot products, updates rounded once to the layer's
+ * precision; Hessenberg matrices, Givens rotations and least-squares solves
+ * in FP64 on the device. The outer residual estimate is read after every
+ * outer step; convergence is confirmed on the true FP64 residual (a cycle
+ * restarts from it otherwise). FP16-F3R with a PackSELL FP16 A_low and with
+ * the FP16 SELL copy of the same matrix runs the same arithmetic: the same
+ * iterates, bit for bit.
+ * b, x: double [n], device. result (nullable): iters = outer steps,
+ * inner_iters = layer-3 steps (iters * m2 * m3), relres = the last outer
+ * estimate, relres_true, seconds (device time). Allocates its workspace
+ * (stream-ordered) and SYNCHRONISES. Errors: INVALID_ARG, NO_MEMORY, CUDA,
+ * NOT_CONVERGED (x holds the last iterate), BREAKDOWN (non-finite residual). */
+packsell_status packsell_f3r(const packsell_matrix *A_outer, const packsell_matrix *A_mid,
+                             const packsell_matrix *A_low, const double *b, double *x,
+                             const packsell_f3r_opts *opts, packsell_solve_result *result,
+                             void *stream);
 
 #ifdef __cplusplus
 }

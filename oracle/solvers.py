@@ -180,3 +180,116 @@ def face_grads(faces, dval):
           - dval[faces["pos_vu"]])
     gb = dval[faces["pos_b"]]
     return np.concatenate([gf, gb])
+
+
+# --------------------------------------------------------------------------
+# F3R (§5.2.1): three layers of flexible GMRES and an innermost Richardson
+# --------------------------------------------------------------------------
+# Readings where the paper is silent (it names the layers and which of them
+# use the FP16 SpMV, and takes the rest from the solver's own paper): the
+# outer layer is restarted FGMRES(m1) in double precision; layers 2 and 3 run
+# exactly m2 and m3 FGMRES steps from zero; layer 4 runs m4 Richardson steps
+# z <- z + omega (r - A z) from z = 0; the Jacobi preconditioner is the
+# identity on symmetrically scaled matrices; Krylov bases by classical
+# Gram-Schmidt; in the FP16-enabled form layers 2-4 keep their vectors in
+# float32, layer 2 applies A with float32 values and layers 3-4 with the
+# FP16-quantised values (each product rounded once to float32); dot products,
+# Hessenberg entries and Givens rotations in double.
+
+def _rnd(v, dt):
+    """v rounded to the working precision dt (float32 or float64), as double."""
+    return np.asarray(v, np.float64).astype(dt).astype(np.float64)
+
+
+def fgmres_steps(apply_a, rhs, m, precond, dt=np.float64, stop=None):
+    """Up to m steps of flexible GMRES from zero on A z = rhs (Saad's FGMRES:
+    Arnoldi on the preconditioned directions z_j = M_j(v_j), the small
+    least-squares problem min ||beta e_1 - H y|| by Givens rotations, z =
+    sum_j y_j z_j). Vectors are kept in precision dt. ``stop(est)`` may end the
+    loop early on the residual estimate |g_{j+1}|. Returns (z, estimates)."""
+    rhs = _rnd(rhs, dt)
+    beta = np.sqrt(_dot(rhs, rhs))
+    if beta == 0.0:
+        return np.zeros_like(rhs), [0.0]
+    V = [_rnd(rhs / beta, dt)]
+    Z = []
+    H = np.zeros((m + 1, m))
+    cs, sn = np.zeros(m), np.zeros(m)
+    g = np.zeros(m + 1)
+    g[0] = beta
+    est = [beta]
+    k = 0
+    for j in range(m):
+        Z.append(_rnd(precond(V[j]), dt))
+        w = _rnd(apply_a(Z[j]), dt)
+        h = np.array([_dot(w, V[i]) for i in range(j + 1)])  # classical Gram-Schmidt
+        w = _rnd(w - sum(h[i] * V[i] for i in range(j + 1)), dt)
+        hn = np.sqrt(_dot(w, w))
+        H[:j + 1, j] = h
+        H[j + 1, j] = hn
+        for i in range(j):  # earlier rotations on the new column
+            a, bb = H[i, j], H[i + 1, j]
+            H[i, j], H[i + 1, j] = cs[i] * a + sn[i] * bb, -sn[i] * a + cs[i] * bb
+        r = np.hypot(H[j, j], H[j + 1, j])
+        cs[j], sn[j] = (H[j, j] / r, H[j + 1, j] / r) if r > 0 else (1.0, 0.0)
+        H[j, j], H[j + 1, j] = r, 0.0
+        g[j + 1] = -sn[j] * g[j]
+        g[j] = cs[j] * g[j]
+        V.append(_rnd(w * (1.0 / hn if hn > 0 else 0.0), dt))
+        k = j + 1
+        est.append(abs(g[j + 1]))
+        if stop is not None and stop(abs(g[j + 1])):
+            break
+    y = np.zeros(k)
+    for i in range(k - 1, -1, -1):  # back substitution on the rotated H
+        t = g[i] - H[i, i + 1:k] @ y[i + 1:k]
+        y[i] = t / H[i, i] if H[i, i] != 0 else 0.0
+    z = sum(y[i] * Z[i] for i in range(k))
+    return np.asarray(z, np.float64), est
+
+
+def richardson(apply_a, r, steps, omega=1.0, dt=np.float64):
+    """``steps`` Richardson steps z <- z + omega (r - A z) from z = 0 (the
+    first one gives z = omega r), vectors in precision dt."""
+    r = _rnd(r, dt)
+    z = _rnd(omega * r, dt)
+    for _ in range(steps - 1):
+        z = _rnd(z + omega * (r - _rnd(apply_a(z), dt)), dt)
+    return z
+
+
+def f3r(A, b, val16=None, m1=30, m2=8, m3=4, m4=2, omega=1.0, tol=1e-9, max_iters=300,
+        x0=None, mixed=True):
+    """F3R (§5.2.1). mixed=True: the FP16-enabled form (layer 2 with float32
+    values and vectors, layers 3 and 4 with the FP16-quantised values
+    ``val16`` and float32 vectors); mixed=False: every layer in double with
+    A.val. Layer 1 stops on its residual estimate and confirms on the true
+    residual (restarting from it otherwise). Returns (x, outer steps,
+    estimates)."""
+    b = np.asarray(b, np.float64)
+    dt = np.float32 if mixed else np.float64
+    v64 = np.asarray(A.val, np.float64)
+    v32 = v64.astype(np.float32).astype(np.float64) if mixed else v64
+    v16 = np.asarray(val16, np.float64) if mixed else v64
+    a1 = lambda v: csr_spmv_f64(A, v64, v)
+    a2 = lambda v: csr_spmv_f64(A, v32, v)
+    a3 = lambda v: csr_spmv_f64(A, v16, v)
+    layer4 = lambda r: richardson(a3, r, m4, omega, dt)
+    layer3 = lambda r: _rnd(fgmres_steps(a3, r, m3, layer4, dt)[0], dt)
+    layer2 = lambda r: fgmres_steps(a2, r, m2, layer3, dt)[0]
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    it, hist = 0, []
+    while it < max_iters:
+        r = b - a1(x)
+        if np.linalg.norm(r) / nb < tol:
+            break
+        left = max_iters - it
+        z, est = fgmres_steps(a1, r, min(m1, left), layer2, np.float64,
+                              stop=lambda e: e / nb < tol)
+        x = x + z
+        it += len(est) - 1
+        hist += [e / nb for e in est[1:]]
+    return x, it, hist

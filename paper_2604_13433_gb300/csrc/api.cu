@@ -26,6 +26,7 @@ void clear_error() { g_last_error.clear(); }
 int64_t matrix_bytes(const Matrix &A) {
     int64_t b = 8 * (A.n_slices + 1) + (int64_t)A.perm_bytes * A.n;
     if (is_w16(A.p.format)) b += 2 * A.n_words;
+    else if (is_sell16(A.p.format)) b += 6 * A.n_words;
     else if (is_packed(A.p.format)) b += 4 * A.n_words;
     else b += (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8) * A.n_words;
     if (A.rowptr) b += 8 * (A.n + 1);
@@ -39,10 +40,13 @@ packsell_status spmv_route(const Matrix &A, const float *x, float *y, cudaStream
     return is_w16(A.p.format) ? spmv_w16_impl(A, x, y, s) : spmv_impl(A, x, y, s);
 }
 
-// Calls that do not take 16-bit words.
+// Calls that take neither 16-bit words nor FP16 SELL.
 packsell_status no_w16(const Matrix &A, const char *what) {
-    if (!is_w16(A.p.format)) return PACKSELL_OK;
-    return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for 16-bit words");
+    if (is_w16(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for 16-bit words");
+    if (is_sell16(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for FP16 SELL");
+    return PACKSELL_OK;
 }
 
 }  // namespace packsell
@@ -131,6 +135,8 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     clear_error();
     if (!Ah || !bytes) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: NULL argument");
     const Matrix &A = *M(Ah);
+    if (is_sell16(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: not available for FP16 SELL");
     size_t vb = is_w16(A.p.format) ? 2 : is_packed(A.p.format) ? 4
                 : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
     size_t need = sizeof(BlobHeader) + 8 * (A.n_slices + 1) + (size_t)A.perm_bytes * A.n +
@@ -687,3 +693,24 @@ packsell_status packsell_pcg_noalloc(const packsell_matrix *A_outer,
 }
 
 }  // extern "C"
+
+void packsell_f3r_opts_default(packsell_f3r_opts *o) {
+    if (!o) return;
+    o->rtol = 1e-9;
+    o->m1 = 30;
+    o->m2 = 8;
+    o->m3 = 4;
+    o->m4 = 2;
+    o->max_iters = 300;
+    o->omega = 1.0;
+}
+
+packsell_status packsell_f3r(const packsell_matrix *A_outer, const packsell_matrix *A_mid,
+                             const packsell_matrix *A_low, const double *b, double *x,
+                             const packsell_f3r_opts *opts, packsell_solve_result *result,
+                             void *stream) {
+    clear_error();
+    if (!A_outer || !A_mid || !A_low || !opts)
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_f3r: NULL argument");
+    return f3r_impl(M(A_outer), M(A_mid), M(A_low), b, x, *opts, result, as_stream(stream));
+}

@@ -429,6 +429,34 @@ __global__ void k_scatter_sell(int n, int64_t rows_total, int C, int sigma,
     }
 }
 
+// FP16 SELL (§3 layout, binary16 values): the value of each stored nonzero is
+// the upper half of its FP16 field; padding slots hold column -1.
+__global__ void k_scatter_sell16(int n, int64_t rows_total, int C, int sigma,
+                                 const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                 const uint32_t *__restrict__ field, const void *perm, int perm_bytes,
+                                 const int64_t *__restrict__ offset, uint16_t *__restrict__ val,
+                                 int32_t *__restrict__ colo) {
+    int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ii >= rows_total) return;
+    int i = (int)ii;
+    int64_t k = ii / C;
+    int l = (int)(ii - k * C);
+    int64_t s = offset[k];
+    int64_t w = (offset[k + 1] - s) / C;
+    int64_t j = 0;
+    if (i < n) {
+        int r = orig_row(i, sigma, perm, perm_bytes);
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p, ++j) {
+            val[s + j * C + l] = (uint16_t)(field[p] >> 16);
+            colo[s + j * C + l] = col[p];
+        }
+    }
+    for (; j < w; ++j) {
+        val[s + j * C + l] = 0;
+        colo[s + j * C + l] = -1;
+    }
+}
+
 const char *status_text(int code) {
     switch (code) {
         case PACKSELL_ERR_INVALID_ARG: return "invalid row pointer or k_left below the bandwidth";
@@ -479,7 +507,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
     const int fmt = p.format;
     if (!out) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: out is NULL");
     *out = nullptr;
-    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt))
+    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt) && !is_sell16(fmt))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: unknown format");
     if (p.C < 1 || p.C > 1024) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: C must be in [1, 1024]");
     if (p.sigma < 1 || p.sigma > 65536)
@@ -528,7 +556,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         if ((e = T.get(&st, sizeof(DevStatus))) || (e = T.get(&kl, 8)) || (e = T.get(&total, 8)) ||
             (e = T.get(&maxw, 4)) || (e = T.get(&words, 4 * (size_t)n)) ||
             (e = T.get(&words_st, 4 * (size_t)n)) || (e = T.get(&slice_words, 8 * (size_t)S)) ||
-            (packed && (e = T.get(&field, 4 * (size_t)nnz))))
+            ((packed || is_sell16(fmt)) && (e = T.get(&field, 4 * (size_t)nnz))))
             return bail(e == cudaErrorMemoryAllocation
                             ? fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: temporaries")
                             : cuda_fail(e, "cudaMallocAsync"));
@@ -541,13 +569,15 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: matrix arrays"));
 
         k_check_rows<<<blocks_for(n), TPB, 0, s>>>((int)n, m, nnz, rowptr, col, kl, st);
-        if (packed && nnz > 0) {
+        if ((packed || is_sell16(fmt)) && nnz > 0) {
             int qb = blocks_for(nnz);
             qb = std::min(qb, 152 * 64);
+            // FP16 SELL takes the FP16 quantiser of the packed format
+            const int qf = is_sell16(fmt) ? PACKSELL_FMT_FP16 : fmt, qd = is_sell16(fmt) ? 15 : D;
             if (val_is_f64)
-                k_quantize<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, fmt, D, field, st);
+                k_quantize<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, qf, qd, field, st);
             else
-                k_quantize<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, fmt, D, field, st);
+                k_quantize<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, qf, qd, field, st);
         }
         if (n > 0) {
             k_count_words<<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, col, p.sigma, p.k_left, kl,
@@ -610,6 +640,15 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
                 k_scatter_packed<<<blocks_for(rows_total), TPB, 0, s>>>(
                     (int)n, rows_total, p.C, p.sigma, A->p.k_left, kl, D, rowptr, col, field,
                     A->perm, perm_bytes, A->offset, A->pack);
+        } else if (is_sell16(fmt)) {
+            if (cudaMalloc(&A->val, 2 * std::max<int64_t>(nw, 1)) != cudaSuccess ||
+                cudaMalloc(&A->col, 4 * std::max<int64_t>(nw, 1)) != cudaSuccess)
+                return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: value arrays"));
+            int64_t rows_total = S * p.C;
+            if (rows_total > 0)
+                k_scatter_sell16<<<blocks_for(rows_total), TPB, 0, s>>>(
+                    (int)n, rows_total, p.C, p.sigma, rowptr, col, field, A->perm, perm_bytes,
+                    A->offset, (uint16_t *)A->val, A->col);
         } else {
             size_t vb = fmt == PACKSELL_FMT_SELL_F64 ? 8 : 4;
             if (cudaMalloc(&A->val, vb * std::max<int64_t>(nw, 1)) != cudaSuccess ||

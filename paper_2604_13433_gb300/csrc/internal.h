@@ -72,6 +72,7 @@ constexpr int64_t kWordTail = 4;
 inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKSELL_FMT_E8MY; }
 inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PACKSELL_FMT_SELL_F64; }
 inline bool is_w16(int fmt) { return fmt == PACKSELL_FMT_W16_E4M3; }
+inline bool is_sell16(int fmt) { return fmt == PACKSELL_FMT_SELL_F16; }
 
 // thread-local error message
 packsell_status fail(packsell_status st, const std::string &msg);
@@ -188,6 +189,11 @@ packsell_status solve_noalloc(const Matrix *A64, const Matrix *Ain, const double
                               const double *b, double *x, const packsell_solve_opts &o,
                               double *h_hist, packsell_solve_result *res, cudaStream_t s);
 size_t noalloc_capacity();
+
+// f3r.cu
+packsell_status f3r_impl(const Matrix *A1, const Matrix *A2, const Matrix *A3, const double *b,
+                         double *x, const packsell_f3r_opts &o, packsell_solve_result *res,
+                         cudaStream_t s);
 
 // solver support (spmv.cu): SpMV fused with a deterministic dot reduction
 struct Red;

@@ -842,6 +842,30 @@ __global__ void __launch_bounds__(TPB, 4)
     sell_rows<double, true, true>(n, C, sigma, offset, val, col, perm, perm_bytes, x, y, b, red);
 }
 
+// FP16 SELL (binary16 values, int32 columns, padding at column -1): one
+// thread per row, each nonzero one fused multiply-add in stored order; the
+// padding slots, trailing each row, add nothing. The chain of the FP16
+// PackSELL kernels over the same values.
+__global__ void __launch_bounds__(TPB)
+    k_spmv_sell16(int n, int C, int sigma, const int64_t *__restrict__ offset,
+                  const uint16_t *__restrict__ val, const int32_t *__restrict__ col,
+                  const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
+                  float *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = i / C, l = i - k * C;
+    const int64_t s = offset[k];
+    const int w = (int)((offset[k + 1] - s) / C);
+    float t = 0.f;
+    for (int j = 0; j < w; ++j) {
+        const int c = __ldcs(col + s + (int64_t)j * C + l);
+        if (c < 0) break;
+        const float v = __half2float(__ushort_as_half(__ldcs(val + s + (int64_t)j * C + l)));
+        t = fmaf(v, __ldg(x + c), t);
+    }
+    y[orig_row(i, sigma, perm, perm_bytes)] = t;
+}
+
 // Thread-per-row PackSELL SpMV fused with sum_i x_i y_i (solver use, any C),
 // on a fixed grid striding over rows.
 template <int FMT>
@@ -1126,6 +1150,10 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
             if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (SELL)");
             break;
         }
+        case PACKSELL_FMT_SELL_F16:
+            k_spmv_sell16<<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
+                                            (const uint16_t *)A.val, A.col, perm, pb, x, y);
+            break;
         default:
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: SELL_F64 needs packsell_spmv_f64");
     }

@@ -20,9 +20,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpacksell.so")
 
-FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3 = 1, 2, 3, 4, 5
+FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3, FMT_SELL_F16 = 1, 2, 3, 4, 5, 6
 _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
-            "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3}
+            "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3, "sell_f16": FMT_SELL_F16}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
           6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
@@ -66,6 +66,12 @@ class FormatTrial(ctypes.Structure):
                 ("ms", ctypes.c_double)]
 
 
+class F3ROpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("m1", ctypes.c_int32), ("m2", ctypes.c_int32),
+                ("m3", ctypes.c_int32), ("m4", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("omega", ctypes.c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("m_in", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
@@ -101,6 +107,8 @@ SIGNATURES = {
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "packsell_quantize": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P]),
     "packsell_set_wait_limit": (ctypes.c_int, [_I64]),
+    "packsell_f3r_opts_default": (None, [_P]),
+    "packsell_f3r": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "packsell_tune_format": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, ctypes.c_double,
                                             _P, _P, _I32, _P, _P, _I32, _P, _P]),
     "packsell_pcg_workspace_bytes": (ctypes.c_size_t, [_I64, _I32, _I32, _I32]),
@@ -727,3 +735,31 @@ def packsell_batch_spmm(B: PackSELLBatchMM, stream=None) -> None:
 
 def packsell_batch_spmv(B: PackSELLBatch, stream=None) -> None:
     B.spmv(stream)
+
+
+def packsell_f3r(A_outer: PackSELLMatrix, A_mid: PackSELLMatrix, A_low: PackSELLMatrix,
+                 b: torch.Tensor, x: torch.Tensor | None = None, *, rtol: float | None = None,
+                 m1: int | None = None, m2: int | None = None, m3: int | None = None,
+                 m4: int | None = None, max_iters: int | None = None, omega: float | None = None,
+                 check: bool = True, stream=None):
+    """F3R (§5.2.1): FGMRES(m1) in FP64 on A_outer, preconditioned by m2 FGMRES
+    steps on A_mid, by m3 FGMRES steps on A_low, by m4 Richardson steps on
+    A_low. Returns (x, info). Unset options take packsell_f3r_opts_default."""
+    o = F3ROpts()
+    lib().packsell_f3r_opts_default(ctypes.byref(o))
+    for k, v in (("rtol", rtol), ("m1", m1), ("m2", m2), ("m3", m3), ("m4", m4),
+                 ("max_iters", max_iters), ("omega", omega)):
+        if v is not None:
+            setattr(o, k, v)
+    n = A_outer.n
+    if x is None:
+        x = torch.zeros(n, dtype=torch.float64, device=b.device)
+    res = SolveResult()
+    code = lib().packsell_f3r(A_outer.handle, A_mid.handle, A_low.handle,
+                              _dev(b, torch.float64, "b", n), _dev(x, torch.float64, "x", n),
+                              ctypes.byref(o), ctypes.byref(res), _stream(stream))
+    info = {"iters": res.iters, "inner_iters": res.inner_iters, "relres": res.relres,
+            "relres_true": res.relres_true, "seconds": res.seconds, "status": STATUS.get(code, code)}
+    if check:
+        _check(code)
+    return x, info
