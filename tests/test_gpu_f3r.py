@@ -58,8 +58,8 @@ def test_sell_f16_spmv_equals_packsell_fp16(C, sigma):
     deq = O.quantize(csr.val, O.FMT_FP16, 15)[1].astype(np.float32)
     twin = O.csr_spmv_fma_f32(csr, deq, x.cpu().numpy())
     assert np.array_equal(ys.view(np.uint32), twin.view(np.uint32))
-    assert S16.n_words == O.encode(csr, C=C, sigma=sigma, D=31, fmt=O.FMT_E8MY).n_words - \
-        O.encode(csr, C=C, sigma=sigma, D=31, fmt=O.FMT_E8MY).n_dummies
+    # the layout of FP32 SELL: same slots, 6 bytes each instead of 8
+    assert S16.n_words == ps.packsell_encode_csr(csr, fmt="sell_f32", C=C, sigma=sigma).n_words
 
 
 def _f3r_inputs(ps, csr, low_fmt):
