@@ -15,6 +15,8 @@ of the measured HBM peak and dominant kernel:
   batch_256           256 irregular matrices per launch (SELL and CSR order),
                       batched SpMM k = 1, 4, 16
   diff_solve_512      512 differentiable 5-point solves, forward and backward
+  f3r                 the nested F3R solver (FP64, FP16 SELL and PackSELL inner
+                      layers) on the scaled 27-point matrix
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
 
@@ -450,6 +452,36 @@ def batch_section(ps, torch, dev, K, W, peak):
     return out
 
 
+def f3r_section(ps, torch, dev):
+    """F3R (§5.2.1) to ||b - A x|| / ||b|| < 1e-9 (the paper's criterion) on
+    the 27-point 128^3 matrix (the HPCG_7_7_7 pattern) after the symmetric
+    scaling of §5.2, b ~ U[0, 1), x0 = 0: FP64-F3R, FP16-F3R with FP16 SELL
+    inner operators and with PackSELL FP16 inner operators (implicit
+    permutation, sigma = 256, as in the paper). One untimed run of each
+    first; seconds are device time."""
+    csr = I.diag_scaled(I.stencil27(128, seed=0))
+    rp, cl = torch.from_numpy(csr.rowptr).to(dev), torch.from_numpy(csr.col).to(dev)
+    vl = torch.from_numpy(csr.val).to(dev)
+    b = torch.from_numpy(I.uniform(csr.n, seed=9, lo=0.0, hi=1.0).astype(np.float64)).to(dev)
+    A1 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f64")
+    A2 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="sell_f32")
+    opts = dict(m1=30, m2=8, m3=4, m4=2, rtol=1e-9, max_iters=300)
+    out = {"workload": "stencil27_128^3 (scaled)", "n": csr.n, "nnz": csr.nnz, "opts": opts}
+    for name, low in (("fp64_f3r", None), ("sell_fp16_f3r", "sell_f16"), ("packsell_f3r", "fp16")):
+        A3 = A1 if low is None else ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=low, D=15)
+        Am = A1 if low is None else A2
+        ps.packsell_f3r(A1, Am, A3, b, **opts)  # untimed
+        x, info = ps.packsell_f3r(A1, Am, A3, b, **opts)
+        out[name] = {k: info[k] for k in ("seconds", "iters", "inner_iters", "relres_true")}
+        if low is not None:
+            del A3
+    base = out["fp64_f3r"]["seconds"]
+    for k in ("sell_fp16_f3r", "packsell_f3r"):
+        out[k]["speedup_vs_fp64_f3r"] = base / out[k]["seconds"]
+    out["packsell_vs_sell_fp16"] = out["sell_fp16_f3r"]["seconds"] / out["packsell_f3r"]["seconds"]
+    return out
+
+
 def diff_solve_section(ps, torch, dev):
     """512 SPD 5-point systems (face coefficients exp(N(0, 0.5)), grids 32^2 to
     256^2) assembled block-diagonally; loss ||x - x_t||^2; forward solve and
@@ -760,6 +792,7 @@ def run_ours(args):
         line["stencil27_128_spmm"] = stencil_spmm_section(ps, torch, dev, K, peak)
         line["batch_256"] = batch_section(ps, torch, dev, K, W, peak)
         line["diff_solve_512"] = diff_solve_section(ps, torch, dev)
+        line["f3r"] = f3r_section(ps, torch, dev)
     if rank == 0 and not args.no_cpu:
         import oracle as O
 

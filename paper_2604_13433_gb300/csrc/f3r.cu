@@ -366,6 +366,8 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
     cudaStream_t s = nullptr;
     PS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     void *mem = nullptr;
     packsell_status st = PACKSELL_OK;
     int iters = 0, steps = 0;
@@ -384,12 +386,12 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
         cudaEventCreate(&ev1);
     }
     const size_t need =
-        sizeof(double) * ((size_t)(2 * o.m1 + 1) * n + 3 * (size_t)n + 64 * (size_t)G +
+        sizeof(double) * ((size_t)(2 * o.m1 + 1) * n + 5 * (size_t)n + 64 * (size_t)G +
                           (size_t)(o.m1 + 1) * o.m1 + 8 * (size_t)o.m1 + 16) +
         sizeof(TI) * ((size_t)(2 * o.m2 + 1) * n + (size_t)(2 * o.m3 + 1) * n + 2 * (size_t)n) +
         sizeof(double) * ((size_t)(o.m2 + 1) * o.m2 + (size_t)(o.m3 + 1) * o.m3 + 8 * (size_t)(o.m2 + o.m3) + 32) +
         256 * 32;
-    double *r = nullptr, *ax = nullptr, *zt = nullptr;
+    double *r = nullptr, *ax = nullptr, *zt = nullptr, *prhs = nullptr, *pout = nullptr;
     double nb = 0.0;
     if (cudaMallocAsync(&mem, need, s) != cudaSuccess) {
         st = fail(PACKSELL_ERR_NO_MEMORY, "packsell_f3r: workspace allocation");
@@ -409,8 +411,10 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
     r = P.take<double>(n);
     ax = P.take<double>(n);
     zt = P.take<double>(n);
+    prhs = P.take<double>(n);
+    pout = P.take<double>(n);
     F.rt = P.take<TI>(n);
-    if (!F.part || !r || !ax || !zt || !F.rt || !make_layer(P, F.L1, o.m1, n) ||
+    if (!F.part || !r || !ax || !zt || !prhs || !pout || !F.rt || !make_layer(P, F.L1, o.m1, n) ||
         !make_layer(P, F.L2, o.m2, n) || !make_layer(P, F.L3, o.m3, n)) {
         st = fail(PACKSELL_ERR_NO_MEMORY, "packsell_f3r: workspace carving");
         goto out;
@@ -441,6 +445,25 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
             !ck(cudaStreamSynchronize(s)))
             goto out;
         nb = sc[0];
+        // layers 2-4 (the preconditioner of an outer step) as one CUDA graph:
+        // a fixed sequence of some hundreds of kernels with no host step,
+        // replayed on the fixed buffers prhs -> pout
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = fail(PACKSELL_ERR_CUDA, "packsell_f3r: stream capture failed to start");
+            goto out;
+        }
+        {
+            const packsell_status cst = F.layer2(prhs, pout);
+            const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (cst != PACKSELL_OK) {
+                st = cst;
+                goto out;
+            }
+            if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                st = fail(PACKSELL_ERR_CUDA, "packsell_f3r: graph capture failed");
+                goto out;
+            }
+        }
         if (nb == 0.0) {
             if (!ck(cudaMemsetAsync(x, 0, sizeof(double) * n, s))) goto out;
             relres = relres_true = 0.0;
@@ -462,8 +485,13 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
             k_scale<double, double><<<G, FT, 0, s>>>(n, r, F.L1.V, F.L1.h.scal + 1);
             int k = 0;
             for (; k < o.m1 && iters < o.max_iters; ++k) {
-                st = F.layer2(F.L1.V + (int64_t)k * n, F.L1.Z + (int64_t)k * n);
-                if (st == PACKSELL_OK) st = F.arnoldi(F.L1, A1, k);
+                if (!ck(cudaMemcpyAsync(prhs, F.L1.V + (int64_t)k * n, sizeof(double) * n,
+                                        cudaMemcpyDeviceToDevice, s)) ||
+                    !ck(cudaGraphLaunch(exec, s)) ||
+                    !ck(cudaMemcpyAsync(F.L1.Z + (int64_t)k * n, pout, sizeof(double) * n,
+                                        cudaMemcpyDeviceToDevice, s)))
+                    goto out;
+                st = F.arnoldi(F.L1, A1, k);
                 if (st != PACKSELL_OK) goto out;
                 ++iters;
                 if (!ck(cudaMemcpyAsync(sc, F.L1.h.scal, sizeof(sc), cudaMemcpyDeviceToHost, s)) ||
@@ -516,6 +544,8 @@ done:
         st = fail(PACKSELL_ERR_NOT_CONVERGED,
                   "packsell_f3r: no convergence in " + std::to_string(o.max_iters) + " outer iterations");
 out:
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
     if (mem) cudaFreeAsync(mem, s);
     cudaStreamSynchronize(s);
     if (ev0) cudaEventDestroy(ev0);

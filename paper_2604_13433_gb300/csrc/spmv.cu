@@ -844,25 +844,51 @@ __global__ void __launch_bounds__(TPB, 4)
 
 // FP16 SELL (binary16 values, int32 columns, padding at column -1): one
 // thread per row, each nonzero one fused multiply-add in stored order; the
-// padding slots, trailing each row, add nothing. The chain of the FP16
-// PackSELL kernels over the same values.
+// padding slots, trailing each row, add nothing, so a row's sum is the chain
+// of the FP16 PackSELL kernels over the same values. The loads of a round of
+// UNROLL slots go out before any is used, as in the FP32 SELL kernel, and the
+// launch is programmatic (values and columns load before the wait on the
+// previous kernel of the stream; x and y after it).
 __global__ void __launch_bounds__(TPB)
     k_spmv_sell16(int n, int C, int sigma, const int64_t *__restrict__ offset,
                   const uint16_t *__restrict__ val, const int32_t *__restrict__ col,
                   const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
                   float *__restrict__ y) {
+    grid_dep_launch();  // one pass over the rows: signal at block start
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n) {
+        grid_dep_wait();
+        return;
+    }
     const int k = i / C, l = i - k * C;
     const int64_t s = offset[k];
     const int w = (int)((offset[k + 1] - s) / C);
+    const uint16_t *vp = val + s + l;
+    const int32_t *cp = col + s + l;
     float t = 0.f;
-    for (int j = 0; j < w; ++j) {
-        const int c = __ldcs(col + s + (int64_t)j * C + l);
-        if (c < 0) break;
-        const float v = __half2float(__ushort_as_half(__ldcs(val + s + (int64_t)j * C + l)));
-        t = fmaf(v, __ldg(x + c), t);
+    bool waited = false;
+    for (int j = 0; j < w; j += UNROLL) {
+        uint16_t v[UNROLL];
+        int cc[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const bool ok = j + u < w;
+            v[u] = ok ? __ldcs(vp + (int64_t)(j + u) * C) : (uint16_t)0;
+            cc[u] = ok ? __ldcs(cp + (int64_t)(j + u) * C) : -1;
+        }
+        if (!waited) {
+            grid_dep_wait();
+            waited = true;
+        }
+        float xv[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.f;
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            if (cc[u] >= 0) t = fmaf(__half2float(__ushort_as_half(v[u])), xv[u], t);
+        if (cc[UNROLL - 1] < 0) break;  // padding: the row has ended
     }
+    if (!waited) grid_dep_wait();
     y[orig_row(i, sigma, perm, perm_bytes)] = t;
 }
 
@@ -1150,10 +1176,14 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
             if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (SELL)");
             break;
         }
-        case PACKSELL_FMT_SELL_F16:
-            k_spmv_sell16<<<g, TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
-                                            (const uint16_t *)A.val, A.col, perm, pb, x, y);
+        case PACKSELL_FMT_SELL_F16: {
+            const cudaError_t e = launch_pdl(k_spmv_sell16, (unsigned)g, TPB, s, (int)A.n, A.p.C,
+                                             A.p.sigma, (const int64_t *)A.offset,
+                                             (const uint16_t *)A.val, (const int32_t *)A.col, perm,
+                                             pb, x, y);
+            if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (FP16 SELL)");
             break;
+        }
         default:
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: SELL_F64 needs packsell_spmv_f64");
     }

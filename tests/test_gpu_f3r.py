@@ -18,15 +18,7 @@ from _gpu import P, dev, need_gpu, torch
 pytestmark = pytest.mark.gpu
 
 
-def scaled(csr):
-    """The symmetric diagonal scaling of §5.2: G^-1 A G^-1, g_i = sqrt(|a_ii|)."""
-    row = np.repeat(np.arange(csr.n), csr.row_lengths())
-    val = csr.val.astype(np.float64)
-    d = np.ones(csr.n)
-    on = csr.col == row
-    d[row[on]] = np.abs(val[on])
-    g = 1.0 / np.sqrt(d)
-    return I.CSR(n=csr.n, m=csr.m, rowptr=csr.rowptr, col=csr.col, val=val * g[row] * g[csr.col])
+scaled = I.diag_scaled  # the symmetric diagonal scaling of §5.2
 
 
 def nonsym(n, seed):
