@@ -19,6 +19,7 @@ of the measured HBM peak and dominant kernel:
                       layers) on the scaled 27-point matrix
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+                  [--sections irregular,spmm,batch,diff,f3r]
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the workload has no exchange step); value sums over ranks, time is the max.
@@ -65,8 +66,11 @@ def parse():
     ap.add_argument("--variant", type=int, default=0,
                     help="SpMV variant of the headline matrix (0: autotune)")
     ap.add_argument("--quick", action="store_true",
-                    help="skip the irregular-matrix, SpMM, batch and batched "
-                         "differentiable-solve sections")
+                    help="skip the irregular-matrix, SpMM, batch, batched "
+                         "differentiable-solve and F3R sections")
+    ap.add_argument("--sections", default="irregular,spmm,batch,diff,f3r",
+                    help="comma list of the sections after the solver one to run "
+                         "(irregular, spmm, batch, diff, f3r)")
     ap.add_argument("--formats", default="all",
                     help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
                          "e8m15), 'all' or 'none'")
@@ -787,11 +791,16 @@ def run_ours(args):
     if not args.no_pcg:
         line["pcg"] = pcg_section(ps, torch, dev, args.pcg_grid,
                                   [int(v) for v in str(args.pcg_min).split(",")])
-    if not args.quick:
+    secs = set() if args.quick else set(args.sections.split(","))
+    if "irregular" in secs:
         line["irregular_4M"] = irregular_section(ps, torch, dev, K, W, peak)
+    if "spmm" in secs:
         line["stencil27_128_spmm"] = stencil_spmm_section(ps, torch, dev, K, peak)
+    if "batch" in secs:
         line["batch_256"] = batch_section(ps, torch, dev, K, W, peak)
+    if "diff" in secs:
         line["diff_solve_512"] = diff_solve_section(ps, torch, dev)
+    if "f3r" in secs:
         line["f3r"] = f3r_section(ps, torch, dev)
     if rank == 0 and not args.no_cpu:
         import oracle as O
