@@ -32,6 +32,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FMT_FP16 = 1
 FMT_E8MY = 2
+FMT_FIXED = 7  # fixed point: a V-bit two's-complement integer times 2^s (one s per matrix)
 
 OK, ERR_ARG, ERR_UNSORTED, ERR_NONFINITE, ERR_RANGE = 0, 1, 2, 3, 4
 
@@ -91,9 +92,15 @@ def lib():
         L.orc_csr_spmv_t_f64.argtypes = [i64, i64, P, P, P, P, P]
         L.orc_csr_spmm_f64.argtypes = [i64, i64, P, P, P, P, i64, P, i64]
         L.orc_packsell_spmv_f64.argtypes = [i64, i32, i32, i32, i32, i64, P, P, P, P, P,
-                                            ctypes.c_int]
+                                            ctypes.c_int, i32]
         L.orc_quantize.argtypes = [i64, P, i32, i32, P, P, P]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_fixed_exponent.argtypes = [ctypes.c_double, ctypes.c_int]
+        L.orc_fixed_exponent.restype = ctypes.c_int
+        L.orc_fixed_bits.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
+        L.orc_fixed_value.argtypes = [u32, ctypes.c_int, ctypes.c_int]
+        L.orc_fixed_value.restype = ctypes.c_double
+        L.orc_quantize_fixed.argtypes = [i64, P, i32, P, P, P, P]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
         _lib = L
@@ -143,10 +150,31 @@ def e8my_bits(v: float, D: int) -> int:
     return out.value
 
 
+def fixed_exponent(M: float, D: int) -> int:
+    """The fixed-point exponent s for the largest magnitude M (V = 31 - D)."""
+    return int(lib().orc_fixed_exponent(float(M), int(D)))
+
+
+def fixed_bits(v: float, D: int, s: int) -> int:
+    out = ctypes.c_uint32()
+    st = lib().orc_fixed_bits(float(v), int(D), int(s), ctypes.byref(out))
+    if st:
+        raise OracleError(st, "fixed_bits")
+    return out.value
+
+
+def fixed_value(field: int, D: int, s: int) -> float:
+    return float(lib().orc_fixed_value(int(field), int(D), int(s)))
+
+
 def quantize(val: np.ndarray, fmt: int, D: int):
     """Value fields (uint32, the upper V bits of a word) and the values they
     stand for (float64) for an array of real values. Raises on overflow or a
-    non-finite input, reporting the first offending index."""
+    non-finite input, reporting the first offending index. Fixed point takes
+    its exponent from the largest magnitude (see quantize_fixed)."""
+    if fmt == FMT_FIXED:
+        field, deq, _ = quantize_fixed(val, D)
+        return field, deq
     v = _c(val, np.float64)
     field = np.empty(v.size, np.uint32)
     deq = np.empty(v.size, np.float64)
@@ -157,6 +185,22 @@ def quantize(val: np.ndarray, fmt: int, D: int):
         e.index = bad.value
         raise e
     return field, deq
+
+
+def quantize_fixed(val: np.ndarray, D: int):
+    """Fixed-point fields, values and the matrix exponent s."""
+    v = _c(val, np.float64)
+    field = np.empty(v.size, np.uint32)
+    deq = np.empty(v.size, np.float64)
+    s = ctypes.c_int32()
+    bad = ctypes.c_int64()
+    st = lib().orc_quantize_fixed(v.size, _p(v), D, _p(field), _p(deq), ctypes.byref(s),
+                                  ctypes.byref(bad))
+    if st:
+        e = OracleError(st, f"quantize_fixed (index {bad.value})")
+        e.index = bad.value
+        raise e
+    return field, deq, s.value
 
 
 # --------------------------------------------------------------------------
@@ -198,6 +242,7 @@ class Encoded:
     n_words: int
     n_dummies: int
     n_pad: int
+    value_exp: int = 0  # fixed point: the matrix exponent s (value = q * 2^s)
 
     @property
     def n_slices(self) -> int:
@@ -219,7 +264,11 @@ def encode(csr, C: int = 32, sigma: int = 256, D: int = 15, fmt: int = FMT_FP16,
     """The PackSELL encoding of a CSR matrix (§4.1-§4.3). Parity: bit-exact."""
     L = lib()
     rowptr, col = _c(csr.rowptr, np.int64), _c(csr.col, np.int32)
-    field, deq = quantize(csr.val, fmt, D)
+    vexp = 0
+    if fmt == FMT_FIXED:
+        field, deq, vexp = quantize_fixed(csr.val, D)
+    else:
+        field, deq = quantize(csr.val, fmt, D)
     n, m = csr.n, csr.m
     S = (n + C - 1) // C
     words = np.empty(n, np.int64)
@@ -237,7 +286,8 @@ def encode(csr, C: int = 32, sigma: int = 256, D: int = 15, fmt: int = FMT_FP16,
         raise OracleError(st, "encode_fill")
     return Encoded(n=n, m=m, C=C, sigma=sigma, D=D, fmt=fmt, k_left=int(stats[0]),
                    words=words, perm=perm, offset=offset, pack=pack, field=field, deq=deq,
-                   n_words=int(stats[1]), n_dummies=int(stats[2]), n_pad=int(stats[3]))
+                   n_words=int(stats[1]), n_dummies=int(stats[2]), n_pad=int(stats[3]),
+                   value_exp=vexp)
 
 
 def e4m3_bits(v: float) -> int:
@@ -388,7 +438,7 @@ def packsell_spmv_f64(enc: Encoded, x: np.ndarray, explicit: bool = False) -> np
     y = np.zeros(enc.n, np.float64)
     lib().orc_packsell_spmv_f64(enc.n, enc.C, enc.sigma, enc.D, enc.fmt, enc.k_left,
                                 _p(enc.perm), _p(enc.offset), _p(enc.pack),
-                                _p(_c(x, np.float64)), _p(y), int(explicit))
+                                _p(_c(x, np.float64)), _p(y), int(explicit), int(enc.value_exp))
     return y
 
 

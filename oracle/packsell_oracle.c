@@ -29,7 +29,7 @@
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_UNSORTED = 2, ORC_ERR_NONFINITE = 3,
        ORC_ERR_RANGE = 4 };
-enum { ORC_FMT_FP16 = 1, ORC_FMT_E8MY = 2 };
+enum { ORC_FMT_FP16 = 1, ORC_FMT_E8MY = 2, ORC_FMT_FIXED = 7 };
 
 /* ------------------------------------------------------------------------ */
 /* Value formats (§4.2.2)                                                     */
@@ -108,6 +108,73 @@ int orc_e8my_bits(double v, int D, uint32_t *out)
     uint32_t b = f32_bits(rf);
     b = (b >> (D + 1)) << (D + 1);
     *out = b;
+    return ORC_OK;
+}
+
+/* Fixed point, an integer value format (§4.2.1 allows any V-bit format,
+ * integer formats included): the V = 31 - D value bits hold a two's-
+ * complement integer q and the value is q * 2^s, with one exponent s for the
+ * whole matrix. s is the smallest integer with (2^(V-1) - 1) * 2^s >= M, M the
+ * largest |a_ij| (s = 0 when M = 0), so every value rounds to an integer of at
+ * most 2^(V-1) - 1 in magnitude. Written from that definition with exact
+ * power-of-two scaling in double. */
+int orc_fixed_exponent(double M, int D)
+{
+    const int V = 31 - D;
+    if (D < 1 || D > 22) return 0;
+    if (!(M > 0.0)) return 0;
+    const double top = ldexp(1.0, V - 1) - 1.0;  /* largest magnitude of q */
+    int s = ilogb(M) - (V - 1);
+    while (ldexp(top, s) < M) ++s;
+    while (ldexp(top, s - 1) >= M) --s;
+    return s;
+}
+
+/* Value field of v in fixed point with exponent s: q = v / 2^s rounded half
+ * away from zero (round()), placed as a V-bit two's-complement integer in
+ * bits D+1..31. Returns ORC_OK, ORC_ERR_NONFINITE, or ORC_ERR_RANGE when |q|
+ * exceeds 2^(V-1) - 1. */
+int orc_fixed_bits(double v, int D, int s, uint32_t *out)
+{
+    if (D < 1 || D > 22) return ORC_ERR_ARG;
+    if (isnan(v) || isinf(v)) return ORC_ERR_NONFINITE;
+    const int V = 31 - D;
+    const double q = round(ldexp(v, -s));
+    if (fabs(q) > ldexp(1.0, V - 1) - 1.0) return ORC_ERR_RANGE;
+    const int64_t qi = (int64_t)q;
+    const uint32_t bits = (uint32_t)((uint64_t)qi & ((1ull << V) - 1ull));
+    *out = bits << (D + 1);
+    return ORC_OK;
+}
+
+/* The value of a fixed-point field: the sign-extended V-bit integer times 2^s. */
+double orc_fixed_value(uint32_t field, int D, int s)
+{
+    const int V = 31 - D;
+    int64_t q = (int64_t)(field >> (D + 1));
+    if (q >= (1ll << (V - 1))) q -= (1ll << V);
+    return ldexp((double)q, s);
+}
+
+/* Fixed-point quantisation of nnz values: the exponent from the largest
+ * magnitude, then every field and its value. Returns the first error with its
+ * index in *bad. */
+int orc_quantize_fixed(int64_t nnz, const double *val, int32_t D, uint32_t *field, double *deq,
+                       int32_t *s_out, int64_t *bad)
+{
+    *bad = -1;
+    double M = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) {
+        if (isnan(val[p]) || isinf(val[p])) { *bad = p; return ORC_ERR_NONFINITE; }
+        if (fabs(val[p]) > M) M = fabs(val[p]);
+    }
+    const int s = orc_fixed_exponent(M, D);
+    *s_out = s;
+    for (int64_t p = 0; p < nnz; ++p) {
+        int st = orc_fixed_bits(val[p], D, s, &field[p]);
+        if (st) { *bad = p; return st; }
+        deq[p] = orc_fixed_value(field[p], D, s);
+    }
     return ORC_OK;
 }
 
@@ -501,7 +568,8 @@ void orc_csr_spmm_f64(int64_t n, int64_t k, const int64_t *rowptr, const int32_t
  * explicit_order != 0 writes y in storage order, else in original order. */
 void orc_packsell_spmv_f64(int64_t n, int32_t C, int32_t sigma, int32_t D, int32_t fmt,
                            int64_t k_left, const int32_t *perm, const int64_t *offset,
-                           const uint32_t *pack, const double *x, double *y, int explicit_order)
+                           const uint32_t *pack, const double *x, double *y, int explicit_order,
+                           int32_t value_exp)
 {
     for (int64_t i = 0; i < n; ++i) {
         int64_t k = i / C, l = i % C;
@@ -513,7 +581,9 @@ void orc_packsell_spmv_f64(int64_t n, int32_t C, int32_t sigma, int32_t D, int32
             uint32_t flag, delta, fld;
             orc_unpack(pack[s + j * C + l], D, &flag, &delta, &fld);
             c += delta;
-            if (flag) t += orc_field_value(fld, fmt) * x[c];
+            if (flag)
+                t += (fmt == ORC_FMT_FIXED ? orc_fixed_value(fld, D, value_exp)
+                                           : orc_field_value(fld, fmt)) * x[c];
         }
         y[iout] = t;
     }
