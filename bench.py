@@ -186,7 +186,9 @@ class Clocks:
 
 
 def spmv_bytes(A, fmt_is_sell: bool):
-    per = 8 if fmt_is_sell else (2 if A.format == 5 else 4)  # 5: 16-bit words
+    # bytes per stored slot: FP32 SELL 8, FP16 SELL (format 6) 6, 16-bit words
+    # (format 5) 2, 32-bit PackSELL words 4
+    per = 8 if fmt_is_sell else (6 if A.format == 6 else 2 if A.format == 5 else 4)
     perm = 0 if A.explicit_perm else A.n * A.perm_bytes
     return per * A.n_words + 8 * (A.n_slices + 1) + perm + 4 * A.m + 4 * A.n
 
@@ -693,7 +695,8 @@ def run_ours(args):
                  ("fp16_v8", "fp16", 15), ("fp16_v9", "fp16", 15), ("fp16_v10", "fp16", 15),
                  ("fp16_v13", "fp16", 15),
                  ("e8m7", "e8my", 15),
-                 ("e8m11", "e8my", 11), ("e8m15", "e8my", 7), ("w16_e4m3", "w16_e4m3", 7))
+                 ("e8m11", "e8my", 11), ("e8m15", "e8my", 7), ("w16_e4m3", "w16_e4m3", 7),
+                 ("sell_f16", "sell_f16", 15), ("fixed_d15", "fixed", 15))
         if args.formats != "all":
             keep = set(args.formats.split(",")) if args.formats != "none" else set()
             sweep = tuple(f for f in sweep if f[0] in keep)
@@ -701,7 +704,7 @@ def run_ours(args):
             A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D, **common)
             if name.startswith("fp16_v"):
                 ps.packsell_set_spmv_variant(A, int(name.split("_v")[1]))
-            elif fmt != "sell_f32":
+            elif fmt not in ("sell_f32", "sell_f16", "fixed"):
                 ps.packsell_tune_spmv(A, x, y, reps=20)
             nb = spmv_bytes(A, fmt == "sell_f32")
             ms, _ = time_launches(torch, lambda: ps.packsell_spmv(A, x, y), K, W)
@@ -773,6 +776,8 @@ def run_ours(args):
                    "timing": "K back-to-back launches between two CUDA events on the launching stream",
                    "parallelism": f"replicas x{world}"},
         "speedup_vs_sell_f32": sell["us"] / formats["fp16"]["us"] if sell else None,
+        "speedup_vs_sell_f16": (formats["sell_f16"]["us"] / formats["fp16"]["us"]
+                                if "sell_f16" in formats else None),
         "formats": formats,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,

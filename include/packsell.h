@@ -88,6 +88,19 @@ typedef enum packsell_status {
  *         packsell_spmv_host, packsell_get_info, packsell_storage_rows and
  *         packsell_export (2-byte words; packsell_import rejects the blob);
  *         the other calls return PACKSELL_ERR_INVALID_ARG for it.
+ * FIXED : fixed point, an integer value format (§4.2.1 allows any V-bit
+ *         format, integer ones included): bits D+1..31 hold a two's-
+ *         complement integer q of V = 31 - D bits and the value is q * 2^s,
+ *         with one exponent s for the matrix (packsell_info.value_exp): the
+ *         smallest s with (2^(V-1) - 1) * 2^s >= max |a_ij|; q = a_ij / 2^s
+ *         rounded half away from zero. Integer-valued matrices (stencils with
+ *         integer coefficients) are exact. D in [6, 22] (V <= 25 bits, so
+ *         every q converts to FP32 exactly). Supported by
+ *         packsell_encode, packsell_spmv (the thread-per-row variant 1, which
+ *         sums the decoded values q * 2^s in stored order: the bits of the FP32
+ *         twin of the decoded matrix), packsell_spmv_host, packsell_get_info,
+ *         packsell_storage_rows; the other calls return
+ *         PACKSELL_ERR_INVALID_ARG.
  * SELL_F16: plain SELL-C-sigma (§3) with binary16 values (round to nearest
  *         even, as FP16 PackSELL) in a uint16 array and int32 columns, 48
  *         bits per stored element: the FP16 SELL the paper compares
@@ -104,7 +117,8 @@ typedef enum packsell_format {
     PACKSELL_FMT_SELL_F32 = 3,
     PACKSELL_FMT_SELL_F64 = 4,
     PACKSELL_FMT_W16_E4M3 = 5,
-    PACKSELL_FMT_SELL_F16 = 6
+    PACKSELL_FMT_SELL_F16 = 6,
+    PACKSELL_FMT_FIXED = 7
 } packsell_format;
 
 typedef struct packsell_params {
@@ -143,6 +157,7 @@ typedef struct packsell_info {
     const int32_t *col;     /* SELL columns, NULL for PackSELL */
     const int64_t *offset;  /* n_slices + 1 word offsets of the slices */
     const void *perm;       /* n entries of perm_bytes, NULL when sigma = 1 */
+    int32_t value_exp;      /* FIXED: the matrix exponent s (value = q * 2^s); 0 otherwise */
 } packsell_info;
 
 const char *packsell_version(void);

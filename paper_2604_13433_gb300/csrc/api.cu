@@ -27,7 +27,7 @@ int64_t matrix_bytes(const Matrix &A) {
     int64_t b = 8 * (A.n_slices + 1) + (int64_t)A.perm_bytes * A.n;
     if (is_w16(A.p.format)) b += 2 * A.n_words;
     else if (is_sell16(A.p.format)) b += 6 * A.n_words;
-    else if (is_packed(A.p.format)) b += 4 * A.n_words;
+    else if (is_packed(A.p.format) || is_fixed(A.p.format)) b += 4 * A.n_words;
     else b += (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8) * A.n_words;
     if (A.rowptr) b += 8 * (A.n + 1);
     return b;
@@ -46,6 +46,8 @@ packsell_status no_w16(const Matrix &A, const char *what) {
         return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for 16-bit words");
     if (is_sell16(A.p.format))
         return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for FP16 SELL");
+    if (is_fixed(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for fixed point");
     return PACKSELL_OK;
 }
 
@@ -127,6 +129,7 @@ packsell_status packsell_get_info(const packsell_matrix *Ah, packsell_info *info
     info->col = A.col;
     info->offset = A.offset;
     info->perm = A.perm;
+    info->value_exp = A.value_exp;
     return PACKSELL_OK;
 }
 
@@ -135,8 +138,9 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     clear_error();
     if (!Ah || !bytes) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: NULL argument");
     const Matrix &A = *M(Ah);
-    if (is_sell16(A.p.format))
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: not available for FP16 SELL");
+    if (is_sell16(A.p.format) || is_fixed(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_export: not available for FP16 SELL and fixed point");
     size_t vb = is_w16(A.p.format) ? 2 : is_packed(A.p.format) ? 4
                 : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
     size_t need = sizeof(BlobHeader) + 8 * (A.n_slices + 1) + (size_t)A.perm_bytes * A.n +

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <utility>
@@ -33,29 +34,39 @@ __device__ __forceinline__ int orig_row(int i, int sigma, const void *perm, int 
 // Decoded word: flag, delta and value. The delta field is D bits wide when the
 // flag is set and 31 bits wide otherwise (§4.2.1); the value is the upper
 // 31 - D bits read as FP16 (bits 16..31) or as an FP32 pattern (E8MY).
+// Fixed point: the V-bit two's-complement field (an arithmetic shift
+// sign-extends it) times the matrix's 2^s; exact, since |q| < 2^24.
 template <int FMT>
 struct Word {
     __device__ __forceinline__ static void decode(uint32_t w, uint32_t dmask, uint32_t vmask,
-                                                  uint32_t &flag, uint32_t &delta, float &v) {
+                                                  uint32_t &flag, uint32_t &delta, float &v,
+                                                  int vshift = 0, float vscale = 1.f) {
         flag = w & 1u;
         delta = (w >> 1) & (flag ? dmask : 0x7fffffffu);
         if (FMT == PACKSELL_FMT_FP16) {
             v = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+        } else if (FMT == PACKSELL_FMT_FIXED) {
+            v = (float)((int32_t)w >> vshift) * vscale;
         } else {
             v = __uint_as_float(w & vmask);
         }
     }
 };
 
-// Masks of a matrix's word layout: delta bits (flag 1) and value bits.
+// Masks of a matrix's word layout: delta bits (flag 1) and value bits; for
+// fixed point the shift of the value field and the matrix's scale 2^s.
 struct Decode {
     uint32_t dmask, vmask;
+    int vshift;
+    float vscale;
 };
 
 inline Decode make_decode(const Matrix &A) {
     Decode d;
     d.dmask = (1u << A.p.D) - 1u;
     d.vmask = ~((2u << A.p.D) - 1u);
+    d.vshift = A.p.D + 1;
+    d.vscale = ldexpf(1.0f, A.value_exp);
     return d;
 }
 
@@ -72,6 +83,7 @@ __device__ __forceinline__ void word_gather(uint32_t wd, Decode dc, const float 
 template <int FMT>
 __device__ __forceinline__ float word_value(uint32_t wd, Decode dc) {
     if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
+    if (FMT == PACKSELL_FMT_FIXED) return (float)((int32_t)wd >> dc.vshift) * dc.vscale;
     return __uint_as_float(wd & dc.vmask);
 }
 

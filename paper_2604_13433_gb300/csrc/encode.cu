@@ -127,14 +127,44 @@ __device__ __forceinline__ int field_e4m3(T v, uint32_t &field) {
     return 0;
 }
 
+// Fixed-point value field: q = v / 2^s rounded half away from zero (exact
+// scaling and rounding in double), as a V = 31 - D bit two's-complement
+// integer in bits D+1..31; |q| above 2^(V-1) - 1 is out of range.
+template <typename T>
+__device__ __forceinline__ int field_fixed(T v, int D, int s, uint32_t &field) {
+    if (!isfinite(v)) return PACKSELL_ERR_NONFINITE;
+    const int V = 31 - D;
+    const double q = round(ldexp((double)v, -s));
+    if (fabs(q) > ldexp(1.0, V - 1) - 1.0) return PACKSELL_ERR_RANGE;
+    const uint32_t bits = (uint32_t)((unsigned long long)(long long)q & ((1ull << V) - 1ull));
+    field = bits << (D + 1);
+    return 0;
+}
+
+// the largest finite |v| (as the bits of a non-negative double, which order
+// as integers)
+template <typename T>
+__global__ void k_absmax(int64_t nnz, const T *__restrict__ val, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs((double)val[p]);
+        if (isfinite(a)) m = max(m, (unsigned long long)__double_as_longlong(a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 template <typename T>
 __global__ void k_quantize(int64_t nnz, const T *__restrict__ val, int fmt, int D,
-                           uint32_t *__restrict__ field, DevStatus *st) {
+                           uint32_t *__restrict__ field, DevStatus *st, int s = 0) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
         uint32_t f = 0;
         int err = (fmt == PACKSELL_FMT_FP16) ? field_fp16(val[p], f)
                   : (fmt == PACKSELL_FMT_W16_E4M3) ? field_e4m3(val[p], f)
+                  : (fmt == PACKSELL_FMT_FIXED)    ? field_fixed(val[p], D, s, f)
                                                    : field_e8my(val[p], D, f);
         if (err) dev_fail(st, err, p);
         field[p] = f;
@@ -457,6 +487,18 @@ __global__ void k_scatter_sell16(int n, int64_t rows_total, int C, int sigma,
     }
 }
 
+// The fixed-point exponent: the smallest s with (2^(V-1) - 1) * 2^s >= M
+// (0 for M = 0), V = 31 - D.
+int fixed_exponent(double M, int D) {
+    const int V = 31 - D;
+    if (!(M > 0.0)) return 0;
+    const double top = ldexp(1.0, V - 1) - 1.0;
+    int sx = ilogb(M) - (V - 1);
+    while (ldexp(top, sx) < M) ++sx;
+    while (ldexp(top, sx - 1) >= M) --sx;
+    return sx;
+}
+
 const char *status_text(int code) {
     switch (code) {
         case PACKSELL_ERR_INVALID_ARG: return "invalid row pointer or k_left below the bandwidth";
@@ -507,7 +549,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
     const int fmt = p.format;
     if (!out) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: out is NULL");
     *out = nullptr;
-    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt) && !is_sell16(fmt))
+    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt) && !is_sell16(fmt) && !is_fixed(fmt))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: unknown format");
     if (p.C < 1 || p.C > 1024) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: C must be in [1, 1024]");
     if (p.sigma < 1 || p.sigma > 65536)
@@ -516,6 +558,9 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: FP16 needs D = 15");
     if (fmt == PACKSELL_FMT_E8MY && (p.D < 1 || p.D > 22))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: E8MY needs D in [1, 22]");
+    // fixed point: V = 31 - D <= 25 bits, so every q converts to FP32 exactly
+    if (is_fixed(fmt) && (p.D < 6 || p.D > 22))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: FIXED needs D in [6, 22]");
     if (is_w16(fmt) && p.D != 7)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: W16_E4M3 needs D = 7");
     if (n < 0 || m < 0 || nnz < 0 || n >= (1ll << 31) || m >= (1ll << 31))
@@ -524,7 +569,7 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: NULL array");
     if (p.k_left < -1) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: k_left < -1");
 
-    const bool packed = is_packed(fmt) || is_w16(fmt);  // delta-value words
+    const bool packed = is_packed(fmt) || is_w16(fmt) || is_fixed(fmt);  // delta-value words
     const int D = packed ? p.D : 31;
     const int W = is_w16(fmt) ? 16 : 32;
     const int64_t S = (n + p.C - 1) / p.C;
@@ -569,15 +614,32 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: matrix arrays"));
 
         k_check_rows<<<blocks_for(n), TPB, 0, s>>>((int)n, m, nnz, rowptr, col, kl, st);
+        if (is_fixed(fmt) && nnz > 0) {
+            // fixed point: the exponent from the largest magnitude first
+            unsigned long long *amax = nullptr, hmax = 0;
+            if ((e = T.get(&amax, 8)) || (e = cudaMemsetAsync(amax, 0, 8, s)))
+                return bail(cuda_fail(e, "packsell_encode: fixed-point scale"));
+            const int qb0 = std::min(blocks_for(nnz), 152 * 64);
+            if (val_is_f64) k_absmax<double><<<qb0, TPB, 0, s>>>(nnz, (const double *)val, amax);
+            else k_absmax<float><<<qb0, TPB, 0, s>>>(nnz, (const float *)val, amax);
+            if ((e = cudaMemcpyAsync(&hmax, amax, 8, cudaMemcpyDeviceToHost, s)) ||
+                (e = cudaStreamSynchronize(s)))
+                return bail(cuda_fail(e, "packsell_encode: fixed-point scale"));
+            double M;
+            memcpy(&M, &hmax, sizeof M);
+            A->value_exp = fixed_exponent(M, p.D);
+        }
         if ((packed || is_sell16(fmt)) && nnz > 0) {
             int qb = blocks_for(nnz);
             qb = std::min(qb, 152 * 64);
             // FP16 SELL takes the FP16 quantiser of the packed format
             const int qf = is_sell16(fmt) ? PACKSELL_FMT_FP16 : fmt, qd = is_sell16(fmt) ? 15 : D;
             if (val_is_f64)
-                k_quantize<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, qf, qd, field, st);
+                k_quantize<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, qf, qd, field, st,
+                                                      A->value_exp);
             else
-                k_quantize<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, qf, qd, field, st);
+                k_quantize<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, qf, qd, field, st,
+                                                     A->value_exp);
         }
         if (n > 0) {
             k_count_words<<<blocks_for(n), TPB, 0, s>>>((int)n, rowptr, col, p.sigma, p.k_left, kl,

@@ -33,6 +33,7 @@ struct Matrix {
     int64_t n_slices = 0, n_words = 0, n_dummies = 0, n_pad = 0;
     int32_t max_width = 0;
     int32_t perm_bytes = 0;
+    int32_t value_exp = 0;  // FIXED: value = q * 2^value_exp
     int device = 0;
     // device arrays
     uint32_t *pack = nullptr;  // PackSELL words
@@ -73,6 +74,7 @@ inline bool is_packed(int fmt) { return fmt == PACKSELL_FMT_FP16 || fmt == PACKS
 inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PACKSELL_FMT_SELL_F64; }
 inline bool is_w16(int fmt) { return fmt == PACKSELL_FMT_W16_E4M3; }
 inline bool is_sell16(int fmt) { return fmt == PACKSELL_FMT_SELL_F16; }
+inline bool is_fixed(int fmt) { return fmt == PACKSELL_FMT_FIXED; }
 
 // thread-local error message
 packsell_status fail(packsell_status st, const std::string &msg);

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(TPB)
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
             uint32_t d;
-            Word<FMT>::decode(wd[u], dc.dmask, dc.vmask, fl[u], d, vv[u]);
+            Word<FMT>::decode(wd[u], dc.dmask, dc.vmask, fl[u], d, vv[u], dc.vshift, dc.vscale);
             c += (int)d;
             xv[u] = fl[u] ? __ldg(x + c) : 0.f;
         }
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(TPB)
         float v;
         const uint32_t wj = ldg_stream(pp + (int64_t)j * C);
         if (wj == 0u) break;
-        Word<FMT>::decode(wj, dc.dmask, dc.vmask, f, d, v);
+        Word<FMT>::decode(wj, dc.dmask, dc.vmask, f, d, v, dc.vshift, dc.vscale);
         c += (int)d;
         if (f) t = fmaf(v, __ldg(x + c), t);
     }
@@ -1176,6 +1176,10 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
             if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv (SELL)");
             break;
         }
+        case PACKSELL_FMT_FIXED:
+            k_spmv_packed<PACKSELL_FMT_FIXED><<<g, TPB, 0, s>>>(
+                (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
+            break;
         case PACKSELL_FMT_SELL_F16: {
             const cudaError_t e = launch_pdl(k_spmv_sell16, (unsigned)g, TPB, s, (int)A.n, A.p.C,
                                              A.p.sigma, (const int64_t *)A.offset,

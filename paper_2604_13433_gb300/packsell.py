@@ -21,8 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpacksell.so")
 
 FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3, FMT_SELL_F16 = 1, 2, 3, 4, 5, 6
+FMT_FIXED = 7
 _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
-            "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3, "sell_f16": FMT_SELL_F16}
+            "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3, "sell_f16": FMT_SELL_F16,
+            "fixed": FMT_FIXED}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
           6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
@@ -57,7 +59,8 @@ class Info(ctypes.Structure):
                 ("n_dummies", ctypes.c_int64), ("n_pad", ctypes.c_int64),
                 ("max_width", ctypes.c_int32), ("perm_bytes", ctypes.c_int32),
                 ("bytes", ctypes.c_int64), ("pack", ctypes.c_void_p), ("val", ctypes.c_void_p),
-                ("col", ctypes.c_void_p), ("offset", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
+                ("col", ctypes.c_void_p), ("offset", ctypes.c_void_p), ("perm", ctypes.c_void_p),
+                ("value_exp", ctypes.c_int32)]
 
 
 class FormatTrial(ctypes.Structure):
@@ -189,6 +192,7 @@ class PackSELLMatrix:
         self.n_slices, self.n_words = info.n_slices, info.n_words
         self.n_dummies, self.n_pad = info.n_dummies, info.n_pad
         self.max_width, self.perm_bytes, self.bytes = info.max_width, info.perm_bytes, info.bytes
+        self.value_exp = info.value_exp
 
     @property
     def handle(self):

@@ -36,7 +36,7 @@ def test_binding_covers_declared_symbols():
 def test_struct_layouts():
     # packsell_params: 6 int32 + int64; packsell_info as declared
     assert ctypes.sizeof(packsell.Params) == 32
-    assert ctypes.sizeof(packsell.Info) == 144
+    assert ctypes.sizeof(packsell.Info) == 152
 
 
 def test_version_and_defaults_without_gpu():
