@@ -395,6 +395,7 @@ def irregular_section(ps, torch, dev, K, W, peak):
     sec["sell_f32"] = _rate(spmv_bytes(S, True), ms, peak, "k_spmv_sell", words=S.n_words)
     del S
     sec["cusparse_csr_f32"] = cusparse_csr_gbps(torch, rp, cl, vl, csr.n, csr.m, x, K, W)
+    sec["reordered_rcm"] = reordered_irregular(ps, torch, dev, csr, x, y, K, W, peak)
     for name, M in (("spmm_c32", A), ("spmm_csr_order", Acsr)):
         rows = {}
         for k in (1, 4, 16, 64):
@@ -409,6 +410,33 @@ def irregular_section(ps, torch, dev, K, W, peak):
         sec[name] = rows
     del A, Acsr, rp, cl, vl
     return sec
+
+
+def reordered_irregular(ps, torch, dev, csr, x, y, K, W, peak):
+    """The same matrix after reverse Cuthill-McKee reordering (host code in the
+    library, §7's future work): P A P^T encoded in SELL slices (C = 32, sigma =
+    256, tuned) and in CSR order (variant 14); x is permuted alike (the product
+    of the reordered matrix is P y)."""
+    t0 = time.perf_counter()
+    perm = ps.packsell_reorder_rcm(csr.rowptr, csr.col)
+    t1 = time.perf_counter()
+    rp, cl, vl = ps.packsell_permute_csr(csr.rowptr, csr.col, csr.val, perm)
+    t2 = time.perf_counter()
+    rpd, cld, vld = (torch.from_numpy(a).to(dev) for a in (rp, cl, vl))
+    xp = x[torch.from_numpy(perm).to(dev).long()].contiguous()
+    out = {"rcm_s": t1 - t0, "permute_s": t2 - t1}
+    R = ps.packsell_encode(rpd, cld, vld, csr.n, csr.m, fmt="fp16", D=15, explicit_perm=True)
+    tuned = ps.packsell_tune_spmv(R, xp, y, reps=10)
+    v = min(tuned, key=tuned.get)
+    ms, _ = time_launches(torch, lambda: ps.packsell_spmv(R, xp, y), K, W)
+    out["sell_c32_fp16"] = _rate(spmv_bytes(R, False), ms, peak, KERNEL_NAMES.get(v, "k_spmv"),
+                                 variant=v, words=R.n_words, words_per_nnz=R.n_words / csr.nnz)
+    del R
+    R = ps.packsell_encode(rpd, cld, vld, csr.n, csr.m, fmt="fp16", D=15, C=1, sigma=1)
+    ms, _ = time_launches(torch, lambda: ps.packsell_spmv(R, xp, y), K, W)
+    out["csr_order_fp16"] = _rate(spmv_bytes(R, False), ms, peak, "k_spmv_split",
+                                  words=R.n_words, words_per_nnz=R.n_words / csr.nnz)
+    return out
 
 
 def stencil_spmm_section(ps, torch, dev, K, peak):
@@ -599,6 +627,30 @@ def pcg_section(ps, torch, dev, grid, m_in):
                 sec[key]["inner_words"] = Ain.n_words
             del Ain
         del A64
+    out["reordered_rcm"] = reordered_iocg(ps, torch, dev, csr, b_h, m_in[-1])
+    return out
+
+
+def reordered_iocg(ps, torch, dev, csr, b_h, m_in):
+    """IO-CG (FP16 PackSELL inner, sigma = 256 implicit) on the reverse
+    Cuthill-McKee reordering P A P^T of the same system (b permuted alike),
+    beside the same solve on the original order. A permutation keeps 2-norms,
+    so the reordered system's true relative residual is the original's."""
+    t0 = time.perf_counter()
+    perm = ps.packsell_reorder_rcm(csr.rowptr, csr.col)
+    t1 = time.perf_counter()
+    rp, cl, vl = ps.packsell_permute_csr(csr.rowptr, csr.col, csr.val, perm)
+    t2 = time.perf_counter()
+    rpd, cld, vld = (torch.from_numpy(a).to(dev) for a in (rp, cl, vl))
+    bp = torch.from_numpy(np.ascontiguousarray(b_h[perm])).to(dev)
+    A64 = ps.packsell_encode(rpd, cld, vld, csr.n, csr.m, fmt="sell_f64")
+    Ain = ps.packsell_encode(rpd, cld, vld, csr.n, csr.m, fmt="fp16", D=15)
+    x = torch.zeros(csr.n, dtype=torch.float64, device=dev)
+    _, info = ps.packsell_pcg(A64, bp, x, A_inner=Ain, m_in=m_in, rtol=1e-10, max_iters=5000,
+                              check=False)
+    out = {"rcm_s": t1 - t0, "permute_s": t2 - t1, "inner_words": Ain.n_words, "m_in": m_in}
+    out["iocg_fp16"] = {k: info[k] for k in ("seconds", "iters", "inner_iters", "relres_true",
+                                              "status")}
     return out
 
 
