@@ -86,7 +86,7 @@ typedef enum packsell_status {
  *         Supported by packsell_encode, packsell_spmv (one thread-per-row
  *         kernel; packsell_set_spmv_variant/tune_spmv see variant 1 only),
  *         packsell_spmv_host, packsell_get_info, packsell_storage_rows and
- *         packsell_export (2-byte words; packsell_import rejects the blob);
+ *         packsell_export and packsell_import (2-byte words);
  *         the other calls return PACKSELL_ERR_INVALID_ARG for it.
  * FIXED : fixed point, an integer value format (§4.2.1 allows any V-bit
  *         format, integer ones included): bits D+1..31 hold a two's-
@@ -99,8 +99,8 @@ typedef enum packsell_status {
  *         packsell_encode, packsell_spmv (the thread-per-row variant 1, which
  *         sums the decoded values q * 2^s in stored order: the bits of the FP32
  *         twin of the decoded matrix), packsell_spmv_host, packsell_get_info,
- *         packsell_storage_rows; the other calls return
- *         PACKSELL_ERR_INVALID_ARG.
+ *         packsell_storage_rows, packsell_export and packsell_import (the
+ *         blob carries s); the other calls return PACKSELL_ERR_INVALID_ARG.
  * SELL_F16: plain SELL-C-sigma (§3) with binary16 values (round to nearest
  *         even, as FP16 PackSELL) in a uint16 array and int32 columns, 48
  *         bits per stored element: the FP16 SELL the paper compares
@@ -108,8 +108,9 @@ typedef enum packsell_status {
  *         Padding slots hold column -1 and add nothing, so a row's sum is the
  *         chain of the FP16 PackSELL kernels over the same values: the same
  *         bits. Supported by packsell_encode, packsell_spmv (one
- *         thread-per-row kernel), packsell_get_info, packsell_storage_rows and
- *         packsell_f3r; the other calls return PACKSELL_ERR_INVALID_ARG.
+ *         thread-per-row kernel), packsell_get_info, packsell_storage_rows,
+ *         packsell_export, packsell_import and packsell_f3r; the other calls
+ *         return PACKSELL_ERR_INVALID_ARG.
  */
 typedef enum packsell_format {
     PACKSELL_FMT_FP16 = 1,
@@ -226,15 +227,19 @@ packsell_status packsell_destroy(packsell_matrix *A);
 packsell_status packsell_get_info(const packsell_matrix *A, packsell_info *info);
 
 /* Serialise the stored arrays of §4.3 (no counterpart in the paper) to a
- * host blob: header, offset, perm, then pack (or val, col).
+ * host blob, for every format: a 112-byte header (magic "PKCSELL2"; n, m,
+ * nnz; packsell_params; n_slices, n_words, n_dummies, n_pad; max_width,
+ * perm_bytes, value_exp, 0), the n_slices + 1 offsets (int64), perm
+ * (perm_bytes per row), then the words (uint32, or uint16 for W16_E4M3) or
+ * the values (float, double or binary16) followed by the columns (int32).
  * With h_blob == NULL only *bytes is set. Synchronises `stream`. */
 packsell_status packsell_export(const packsell_matrix *A, void *h_blob, size_t *bytes,
                                 void *stream);
 
 /* Rebuild a matrix (§4.3's arrays) from packsell_export's blob. The blob is validated on the
- * device (every row decoded, columns checked against m, value words counted
- * against nnz) before the call returns; a bad blob gives CORRUPT and no
- * matrix. Synchronises `stream`. */
+ * device (every row decoded, columns checked against m, value words, or the
+ * FP16 SELL slots that are not padding, counted against nnz) before the call
+ * returns; a bad blob gives CORRUPT and no matrix. Synchronises `stream`. */
 packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
                                 packsell_matrix **out);
 
@@ -650,8 +655,7 @@ packsell_status packsell_pcg_backward(const packsell_matrix *A_outer,
  *   (result->seconds is host wall time).
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current and keeps it for later
- *   calls on that device; make that first call before any stream capture
- *   begins. A cudaDeviceReset invalidates the kept address, as it does every
+ *   calls on that device. A cudaDeviceReset invalidates the kept address, as it does every
  *   matrix of the library: do not call the library on a device after
  *   resetting it.
  * - All calls share the array and every call re-initialises what must start

@@ -56,7 +56,7 @@ packsell_status no_w16(const Matrix &A, const char *what) {
 using namespace packsell;
 
 namespace {
-constexpr uint64_t kMagic = 0x314C4C4553434B50ull;  // "PKCSELL1"
+constexpr uint64_t kMagic = 0x324C4C4553434B50ull;  // "PKCSELL2"
 
 struct BlobHeader {
     uint64_t magic;
@@ -64,7 +64,17 @@ struct BlobHeader {
     packsell_params p;
     int64_t n_slices, n_words, n_dummies, n_pad;
     int32_t max_width, perm_bytes;
+    int32_t value_exp, reserved;  // fixed point's 2^s; 0
 };
+
+// Bytes per stored word of each format in the blob: the word, or value and
+// column of plain SELL.
+inline size_t blob_word_bytes(int fmt) {
+    if (is_w16(fmt)) return 2;
+    if (is_packed(fmt) || is_fixed(fmt)) return 4;
+    if (is_sell16(fmt)) return 6;
+    return fmt == PACKSELL_FMT_SELL_F64 ? 12 : 8;
+}
 
 inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
@@ -138,11 +148,7 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     clear_error();
     if (!Ah || !bytes) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_export: NULL argument");
     const Matrix &A = *M(Ah);
-    if (is_sell16(A.p.format) || is_fixed(A.p.format))
-        return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_export: not available for FP16 SELL and fixed point");
-    size_t vb = is_w16(A.p.format) ? 2 : is_packed(A.p.format) ? 4
-                : (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
+    const size_t vb = blob_word_bytes(A.p.format);
     size_t need = sizeof(BlobHeader) + 8 * (A.n_slices + 1) + (size_t)A.perm_bytes * A.n +
                   vb * (size_t)A.n_words;
     if (!h_blob) {
@@ -163,6 +169,7 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     h.n_pad = A.n_pad;
     h.max_width = A.max_width;
     h.perm_bytes = A.perm_bytes;
+    h.value_exp = A.value_exp;
     char *dst = (char *)h_blob;
     memcpy(dst, &h, sizeof(h));
     dst += sizeof(h);
@@ -175,10 +182,10 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     }
     if (is_w16(A.p.format)) {
         PS_CUDA(cudaMemcpyAsync(dst, A.pack16, 2 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
-    } else if (is_packed(A.p.format)) {
+    } else if (is_packed(A.p.format) || is_fixed(A.p.format)) {
         PS_CUDA(cudaMemcpyAsync(dst, A.pack, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
     } else {
-        size_t eb = A.p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
+        const size_t eb = vb - 4;
         PS_CUDA(cudaMemcpyAsync(dst, A.val, eb * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
         dst += eb * (size_t)A.n_words;
         PS_CUDA(cudaMemcpyAsync(dst, A.col, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
@@ -197,14 +204,20 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     BlobHeader h;
     memcpy(&h, h_blob, sizeof(h));
     const packsell_params &p = h.p;
-    bool fmt_ok = is_packed(p.format) || is_sell(p.format);
-    if (h.magic != kMagic || !fmt_ok || h.n < 0 || h.n >= (1ll << 31) || h.m < 0 ||
+    const bool fmt_ok = is_packed(p.format) || is_sell(p.format) || is_w16(p.format) ||
+                        is_sell16(p.format) || is_fixed(p.format);
+    // delta bits each word format accepts (packsell_encode's own ranges)
+    const bool d_ok = is_packed(p.format)  ? (p.D >= 1 && p.D <= 22)
+                      : is_fixed(p.format) ? (p.D >= 6 && p.D <= 22)
+                      : is_w16(p.format)   ? p.D == 7
+                                           : true;
+    if (h.magic != kMagic || !fmt_ok || !d_ok || h.n < 0 || h.n >= (1ll << 31) || h.m < 0 ||
         h.m >= (1ll << 31) || p.C < 1 || p.C > 1024 || p.sigma < 1 || p.sigma > 65536 ||
-        (is_packed(p.format) && (p.D < 1 || p.D > 22)) || h.n_slices != (h.n + p.C - 1) / p.C ||
-        h.n_words < 0 || h.perm_bytes != (p.sigma == 1 ? 0 : (p.sigma <= 256 ? 1 : 2)) ||
-        p.k_left < 0)
+        h.n_slices != (h.n + p.C - 1) / p.C || h.n_words < 0 ||
+        h.perm_bytes != (p.sigma == 1 ? 0 : (p.sigma <= 256 ? 1 : 2)) || p.k_left < 0 ||
+        (is_fixed(p.format) ? (h.value_exp < -1100 || h.value_exp > 1100) : h.value_exp != 0))
         return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad header");
-    size_t vb = is_packed(p.format) ? 4 : (p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8);
+    const size_t vb = blob_word_bytes(p.format);
     size_t need = sizeof(BlobHeader) + 8 * (h.n_slices + 1) + (size_t)h.perm_bytes * h.n +
                   vb * (size_t)h.n_words;
     if (bytes < need) return fail(PACKSELL_ERR_CORRUPT, "packsell_import: blob truncated");
@@ -234,6 +247,7 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     A->n_pad = h.n_pad;
     A->max_width = h.max_width;
     A->perm_bytes = h.perm_bytes;
+    A->value_exp = h.value_exp;
     cudaGetDevice(&A->device);
     cudaStream_t s = as_stream(stream);
     auto bail = [&](packsell_status st) {
@@ -253,14 +267,20 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
         src += (size_t)h.perm_bytes * h.n;
     }
     size_t nw = (size_t)std::max<int64_t>(h.n_words, 1);
-    if (is_packed(p.format)) {
+    if (is_w16(p.format)) {
+        if (cudaMalloc(&A->pack16, 2 * nw) != cudaSuccess)
+            return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
+        if (cudaMemcpyAsync(A->pack16, src, 2 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
+    } else if (is_packed(p.format) || is_fixed(p.format)) {
         if (cudaMalloc(&A->pack, 4 * (nw + kWordTail)) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
         if (cudaMemcpyAsync(A->pack, src, 4 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
             return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
     } else {
-        size_t eb = p.format == PACKSELL_FMT_SELL_F64 ? 8 : 4;
+        const size_t eb = vb - 4;
         if (cudaMalloc(&A->val, eb * nw) != cudaSuccess || cudaMalloc(&A->col, 4 * nw) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
         if (cudaMemcpyAsync(A->val, src, eb * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=

@@ -765,9 +765,13 @@ void destroy_matrix(Matrix *A) {
 
 // ---- validation of imported matrices ----
 namespace {
-template <bool PACKED>
+// What k_validate decodes: 32-bit words (FP16, E8MY, fixed point), 16-bit
+// words, or the column array of plain SELL (FP16 SELL pads with column -1).
+enum ValidateKind { kValWords32 = 0, kValWords16 = 1, kValCols = 2, kValCols16 = 3 };
+
+template <int KIND>
 __global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left, int D,
-                           const int64_t *__restrict__ offset, const uint32_t *__restrict__ pack,
+                           const int64_t *__restrict__ offset, const void *__restrict__ words,
                            const int32_t *__restrict__ colv, const void *perm, int perm_bytes,
                            unsigned long long *count, DevStatus *st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -789,26 +793,38 @@ __global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left,
     }
     int64_t w = (e - s) / C;
     unsigned long long cnt = 0;
-    if (PACKED) {
+    if (KIND == kValWords32 || KIND == kValWords16) {
+        // flag 1: D delta bits; flag 0 (dummy, padding): the rest of the word
+        const uint32_t dmask = (1u << D) - 1u;
+        const uint32_t wide = KIND == kValWords32 ? 0x7fffffffu : 0x7fffu;
         long long c = left_offset(i, sigma, k_left);
-        uint32_t dmask = (1u << D) - 1u;
         for (int64_t j = 0; j < w; ++j) {
-            uint32_t wd = pack[s + j * C + l];
-            uint32_t flag = wd & 1u;
-            c += (wd >> 1) & (flag ? dmask : 0x7fffffffu);
-            bool pad = wd == 0;
-            if (!pad && c >= m) {
-                dev_fail(st, PACKSELL_ERR_CORRUPT, s + j * C + l);
+            const int64_t at = s + j * C + l;
+            const uint32_t wd = KIND == kValWords32 ? ((const uint32_t *)words)[at]
+                                                    : (uint32_t)((const uint16_t *)words)[at];
+            const uint32_t flag = wd & 1u;
+            c += (wd >> 1) & (flag ? dmask : wide);
+            if (wd != 0u && c >= m) {
+                dev_fail(st, PACKSELL_ERR_CORRUPT, at);
                 return;
             }
             cnt += flag;
         }
     } else {
+        bool pad = false;
         for (int64_t j = 0; j < w; ++j) {
-            int c = colv[s + j * C + l];
-            if (c < 0 || c >= m) {
+            const int c = colv[s + j * C + l];
+            // FP16 SELL: a row's slots after its first -1 are all -1 (the
+            // product stops at the first); nonpadding slots are counted
+            const bool bad = KIND == kValCols16 ? (c >= m || c < -1 || (pad && c != -1))
+                                                : (c < 0 || c >= m);
+            if (bad) {
                 dev_fail(st, PACKSELL_ERR_CORRUPT, s + j * C + l);
                 return;
+            }
+            if (KIND == kValCols16) {
+                pad = c < 0;
+                cnt += !pad;
             }
         }
     }
@@ -824,16 +840,26 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     PS_CUDA(T.get(&cnt, 8));
     PS_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
     PS_CUDA(cudaMemsetAsync(cnt, 0, 8, s));
+    const int fmt = A.p.format;
+    const bool counted = !is_sell(fmt);  // every format but plain SELL counts its values
     if (A.n > 0) {
         int g = blocks_for(A.n);
-        if (is_packed(A.p.format))
-            k_validate<true><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left, A.p.D,
-                                               A.offset, A.pack, nullptr, A.perm, A.perm_bytes,
-                                               cnt, st);
+        if (is_packed(fmt) || is_fixed(fmt))
+            k_validate<kValWords32><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,
+                                                      A.p.D, A.offset, A.pack, nullptr, A.perm,
+                                                      A.perm_bytes, cnt, st);
+        else if (is_w16(fmt))
+            k_validate<kValWords16><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,
+                                                      A.p.D, A.offset, A.pack16, nullptr, A.perm,
+                                                      A.perm_bytes, cnt, st);
+        else if (is_sell16(fmt))
+            k_validate<kValCols16><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,
+                                                     31, A.offset, nullptr, A.col, A.perm,
+                                                     A.perm_bytes, cnt, st);
         else
-            k_validate<false><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left, 31,
-                                                A.offset, nullptr, A.col, A.perm, A.perm_bytes,
-                                                cnt, st);
+            k_validate<kValCols><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left, 31,
+                                                   A.offset, nullptr, A.col, A.perm, A.perm_bytes,
+                                                   cnt, st);
         PS_LAUNCH_CHECK("k_validate");
     }
     DevStatus hst{};
@@ -844,7 +870,7 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     if (hst.code)
         return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad word, column or perm at index " +
                                               std::to_string(hst.index));
-    if (is_packed(A.p.format) && (int64_t)hc != A.nnz)
+    if (counted && (int64_t)hc != A.nnz)
         return fail(PACKSELL_ERR_CORRUPT, "packsell_import: value words do not match nnz");
     return PACKSELL_OK;
 }

@@ -521,9 +521,9 @@ def packsell_import(blob: bytes, stream=None) -> PackSELLMatrix:
 
 def packsell_arrays(A: PackSELLMatrix):
     """Host copies of the encoded arrays: dict with offset, perm, and pack
-    (PackSELL) or val/col (SELL), parsed from the export blob."""
+    (PackSELL words) or val/col (SELL), parsed from the export blob."""
     blob = packsell_export(A)
-    hdr = 8 + 3 * 8 + ctypes.sizeof(Params) + 4 * 8 + 2 * 4
+    hdr = 8 + 3 * 8 + ctypes.sizeof(Params) + 4 * 8 + 4 * 4
     pos = hdr
     S = A.n_slices
     out = {"offset": np.frombuffer(blob, np.int64, S + 1, pos)}
@@ -536,10 +536,10 @@ def packsell_arrays(A: PackSELLMatrix):
         out["perm"] = np.zeros(A.n, np.int32)
     if A.format == FMT_W16_E4M3:
         out["pack"] = np.frombuffer(blob, np.uint16, A.n_words, pos)
-    elif A.format in (FMT_FP16, FMT_E8MY):
+    elif A.format in (FMT_FP16, FMT_E8MY, FMT_FIXED):
         out["pack"] = np.frombuffer(blob, np.uint32, A.n_words, pos)
     else:
-        dt = np.float64 if A.format == FMT_SELL_F64 else np.float32
+        dt = {FMT_SELL_F64: np.float64, FMT_SELL_F16: np.float16}.get(A.format, np.float32)
         out["val"] = np.frombuffer(blob, dt, A.n_words, pos)
         pos += np.dtype(dt).itemsize * A.n_words
         out["col"] = np.frombuffer(blob, np.int32, A.n_words, pos)

@@ -49,14 +49,14 @@ def test_version_and_defaults_without_gpu():
 
 # ---- argument and blob checks that return before any CUDA call ----
 
-_MAGIC = 0x314C4C4553434B50  # "PKCSELL1"
+_MAGIC = 0x324C4C4553434B50  # "PKCSELL2"
 
 
 def _blob(n=64, m=64, C=32, sigma=1, D=15, fmt=1, widths=(3, 2), max_width=None,
-          offsets=None, magic=_MAGIC, words_extra=0):
-    """A packsell_export blob built by hand: 104-byte header (magic; n, m,
-    nnz; params; n_slices, n_words, n_dummies, n_pad; max_width, perm_bytes),
-    slice offsets, then the words (no perm with sigma = 1)."""
+          offsets=None, magic=_MAGIC, words_extra=0, value_exp=0):
+    """A packsell_export blob built by hand: 112-byte header (magic; n, m,
+    nnz; params; n_slices, n_words, n_dummies, n_pad; max_width, perm_bytes,
+    value_exp, 0), slice offsets, then the words (no perm with sigma = 1)."""
     import struct
     S = (n + C - 1) // C
     if offsets is None:
@@ -66,8 +66,8 @@ def _blob(n=64, m=64, C=32, sigma=1, D=15, fmt=1, widths=(3, 2), max_width=None,
     nw = offsets[-1]
     mw = max(widths) if max_width is None else max_width
     hdr = struct.pack("<Q3q6iq4q2i", magic, n, m, nw, C, sigma, D, fmt, 0, 0, 0,
-                      S, nw, 0, 0, mw, 0)
-    assert len(hdr) == 104
+                      S, nw, 0, 0, mw, 0) + struct.pack("<2i", value_exp, 0)
+    assert len(hdr) == 112
     return hdr + struct.pack(f"<{S + 1}q", *offsets) + b"\0" * (4 * (nw + words_extra))
 
 
@@ -89,6 +89,11 @@ def test_import_rejects_bad_blobs_on_the_host():
         (_blob(magic=0), "bad header"),
         (_patch(_blob(), 32, "<i", 0), "bad header"),  # C = 0
         (_blob(D=23), "bad header"),
+        (_blob(fmt=7, D=5), "bad header"),  # fixed point needs D in [6, 22]
+        (_blob(fmt=5, D=15), "bad header"),  # 16-bit words have D = 7
+        (_blob(value_exp=3), "bad header"),  # an exponent only fixed point has
+        (_blob(fmt=7, value_exp=5000), "bad header"),
+        (_blob(fmt=8), "bad header"),
         (_blob(sigma=300), "bad header"),  # perm_bytes 0 does not match sigma > 1
         (_blob()[:-4], "truncated"),
         (_blob(offsets=[32, 96, 160]), "offsets do not match"),

@@ -143,3 +143,53 @@ def test_export_import_roundtrip_and_corruption():
     with pytest.raises(packsell.PackSELLError) as e:
         packsell.packsell_import(bytes(bad))
     assert e.value.code == 9
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 9), ("fixed", 11), ("w16_e4m3", 7),
+                                   ("sell_f16", 15), ("sell_f32", 15), ("sell_f64", 15)])
+def test_export_import_roundtrip_every_format(fmt, D):
+    """Every storage format survives export and import: the same arrays,
+    the same fixed-point exponent and the same product bits."""
+    need_gpu()
+    ps = P()
+    csr = I.random_csr(700, 900, 0.02, seed=D, empty_rows=0.05, long_gaps=True)
+    A = encode_gpu(csr, fmt=fmt, D=D, C=32, sigma=64)
+    B = ps.packsell_import(ps.packsell_export(A))
+    assert (B.format, B.n_words, B.nnz, B.value_exp) == (A.format, A.n_words, A.nnz, A.value_exp)
+    a, b = ps.packsell_arrays(A), ps.packsell_arrays(B)
+    assert a.keys() == b.keys()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    if fmt != "sell_f64":
+        x = dev(I.uniform(900, seed=2))
+        assert torch.equal(ps.packsell_spmv(A, x), ps.packsell_spmv(B, x))
+
+
+@pytest.mark.gpu
+def test_import_rejects_sell_f16_slot_after_padding():
+    """FP16 SELL pads a row with column -1 and its product stops at the
+    first -1: a stored column after one, or one more stored column than
+    nnz, is a corrupt blob."""
+    need_gpu()
+    ps = P()
+    C = 32
+    csr = I.random_csr(300, 300, 0.03, seed=3, empty_rows=0.1)
+    A = encode_gpu(csr, fmt="sell_f16", C=C, sigma=1)
+    blob = ps.packsell_export(A)
+    off = ps.packsell_arrays(A)["offset"]
+    cols_at = len(blob) - 4 * A.n_words
+    cols = np.frombuffer(blob, np.int32, A.n_words, cols_at).copy()
+    assert ps.packsell_import(blob).nnz == A.nnz
+    # a row's last stored slot q followed by padding at q + C, same slice
+    slice_end = np.repeat(off[1:], np.diff(off))
+    q = np.nonzero((cols[:-C] >= 0) & (cols[C:] == -1) & (np.arange(A.n_words - C) + C <
+                                                           slice_end[:-C]))[0][0]
+    swapped = cols.copy()
+    swapped[q], swapped[q + C] = -1, cols[q]  # same count, wrong order
+    extra = cols.copy()
+    extra[q + C] = 0  # one stored column too many
+    for bad in (swapped, extra):
+        with pytest.raises(ps.PackSELLError) as e:
+            ps.packsell_import(blob[:cols_at] + bad.tobytes())
+        assert e.value.code == 9

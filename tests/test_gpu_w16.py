@@ -108,5 +108,3 @@ def test_w16_refused_calls():
         ps.packsell_spmv_transpose(A, x)
     with pytest.raises(ps.PackSELLError):
         ps.PackSELLBatch([A], [x], [torch.empty(csr.n, device="cuda")])
-    with pytest.raises(ps.PackSELLError):
-        ps.packsell_import(ps.packsell_export(A))
