@@ -33,6 +33,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 FMT_FP16 = 1
 FMT_E8MY = 2
 FMT_FIXED = 7  # fixed point: a V-bit two's-complement integer times 2^s (one s per matrix)
+FMT_W64_E11MY = 8  # 64-bit words, binary64 values with Y = 51 - D mantissa bits
 
 OK, ERR_ARG, ERR_UNSORTED, ERR_NONFINITE, ERR_RANGE = 0, 1, 2, 3, 4
 
@@ -101,6 +102,16 @@ def lib():
         L.orc_fixed_value.argtypes = [u32, ctypes.c_int, ctypes.c_int]
         L.orc_fixed_value.restype = ctypes.c_double
         L.orc_quantize_fixed.argtypes = [i64, P, i32, P, P, P, P]
+        u64 = ctypes.c_uint64
+        L.orc_e11my_bits.argtypes = [ctypes.c_double, ctypes.c_int, P]
+        L.orc_e11my_value.argtypes = [u64]
+        L.orc_e11my_value.restype = ctypes.c_double
+        L.orc_quantize_e11my.argtypes = [i64, P, i32, P, P, P]
+        L.orc_encode64_fill.argtypes = [i64, P, P, P, i32, i32, i32, i64, P, P, P]
+        L.orc_decode64.argtypes = [i64, i32, i32, i32, i64, P, P, P, P, P, P, P]
+        L.orc_packsell64_spmv_f64.argtypes = [i64, i32, i32, i32, i64, P, P, P, P, P,
+                                              ctypes.c_int]
+        L.orc_csr_spmv_fma_f64.argtypes = [i64, P, P, P, P, P]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
         _lib = L
@@ -372,6 +383,116 @@ def decode16(enc: Encoded16, rowptr: np.ndarray):
     lib().orc_decode16(enc.n, enc.C, enc.sigma, enc.k_left, _p(enc.perm), _p(enc.offset),
                        _p(enc.pack), _p(rowptr), _p(col), _p(codes), _p(counts))
     return col, codes, counts
+
+
+# --------------------------------------------------------------------------
+# 64-bit words (§4.2.1 with W = 64): E11MY values, FP64 products
+# --------------------------------------------------------------------------
+def e11my_bits(v: float, D: int) -> int:
+    """E11MY bits of v: E8MY's rule on binary64 (round half away from zero on
+    2^(e-53+D+1), clear the low D + 1 bits); D in [1, 31]."""
+    out = ctypes.c_uint64()
+    st = lib().orc_e11my_bits(float(v), int(D), ctypes.byref(out))
+    if st:
+        raise OracleError(st, "e11my_bits")
+    return out.value
+
+
+def e11my_value(bits: int) -> float:
+    return float(lib().orc_e11my_value(int(bits)))
+
+
+def quantize_e11my(val: np.ndarray, D: int):
+    """E11MY fields (uint64) and values (float64) of every entry."""
+    v = _c(np.asarray(val, np.float64).ravel(), np.float64)
+    field = np.empty(v.size, np.uint64)
+    deq = np.empty(v.size, np.float64)
+    bad = ctypes.c_int64(-1)
+    st = lib().orc_quantize_e11my(v.size, _p(v), int(D), _p(field), _p(deq), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"quantize_e11my (index {bad.value})")
+    return field, deq
+
+
+@dataclass
+class Encoded64:
+    """PackSELL with 64-bit words (W = 64, V = 63 - D, E11MY values)."""
+    n: int
+    m: int
+    C: int
+    sigma: int
+    D: int
+    k_left: int
+    words: np.ndarray  # int64 [n]
+    perm: np.ndarray  # int32 [n]
+    offset: np.ndarray  # int64 [S + 1]
+    pack: np.ndarray  # uint64 [N_w]
+    field: np.ndarray  # uint64 [nnz], E11MY fields in CSR order
+    deq: np.ndarray  # float64 [nnz]
+    n_words: int
+    n_dummies: int
+    n_pad: int
+
+    @property
+    def n_slices(self) -> int:
+        return self.offset.size - 1
+
+
+def encode64(csr, C: int = 32, sigma: int = 256, D: int = 11, k_left: int = -1) -> Encoded64:
+    """The PackSELL encoding with 64-bit words (§4.1-§4.3 with W = 64).
+    Parity: bit-exact."""
+    L = lib()
+    rowptr, col = _c(csr.rowptr, np.int64), _c(csr.col, np.int32)
+    field, deq = quantize_e11my(csr.val, D)
+    n, m = csr.n, csr.m
+    S = (n + C - 1) // C
+    words = np.empty(n, np.int64)
+    perm = np.empty(n, np.int32)
+    offset = np.empty(S + 1, np.int64)
+    stats = np.empty(4, np.int64)
+    st = L.orc_encode_plan_w(n, m, _p(rowptr), _p(col), C, sigma, D, 64, k_left, _p(words),
+                             _p(perm), _p(offset), _p(stats))
+    if st:
+        raise OracleError(st, "encode_plan_w")
+    pack = np.empty(int(stats[1]), np.uint64)
+    st = L.orc_encode64_fill(n, _p(rowptr), _p(col), _p(field), C, sigma, D, int(stats[0]),
+                             _p(perm), _p(offset), _p(pack))
+    if st:
+        raise OracleError(st, "encode64_fill")
+    return Encoded64(n=n, m=m, C=C, sigma=sigma, D=D, k_left=int(stats[0]), words=words,
+                     perm=perm, offset=offset, pack=pack, field=field, deq=deq,
+                     n_words=int(stats[1]), n_dummies=int(stats[2]), n_pad=int(stats[3]))
+
+
+def decode64(enc: Encoded64, rowptr: np.ndarray):
+    """(col, field, counts) of the 64-bit words, as decode()."""
+    rowptr = _c(rowptr, np.int64)
+    nnz = int(rowptr[-1])
+    col = np.full(nnz, -1, np.int32)
+    field = np.zeros(nnz, np.uint64)
+    counts = np.zeros(enc.n, np.int64)
+    lib().orc_decode64(enc.n, enc.C, enc.sigma, enc.D, enc.k_left, _p(enc.perm), _p(enc.offset),
+                       _p(enc.pack), _p(rowptr), _p(col), _p(field), _p(counts))
+    return col, field, counts
+
+
+def packsell64_spmv_f64(enc: Encoded64, x: np.ndarray, explicit: bool = False) -> np.ndarray:
+    """The §4.4 algorithm over 64-bit words: one double fused multiply-add
+    per real word in stored order, from +0."""
+    y = np.zeros(enc.n, np.float64)
+    lib().orc_packsell64_spmv_f64(enc.n, enc.C, enc.sigma, enc.D, enc.k_left, _p(enc.perm),
+                                  _p(enc.offset), _p(enc.pack), _p(_c(x, np.float64)), _p(y),
+                                  int(explicit))
+    return y
+
+
+def csr_spmv_fma_f64(csr, val: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A x in double, one fused multiply-add per nonzero in column order
+    from +0 (the result of one thread walking one row's words)."""
+    y = np.empty(csr.n, np.float64)
+    lib().orc_csr_spmv_fma_f64(csr.n, _p(_c(csr.rowptr, np.int64)), _p(_c(csr.col, np.int32)),
+                               _p(_c(val, np.float64)), _p(_c(x, np.float64)), _p(y))
+    return y
 
 
 def check_csr(csr) -> int:

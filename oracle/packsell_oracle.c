@@ -29,7 +29,7 @@
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_UNSORTED = 2, ORC_ERR_NONFINITE = 3,
        ORC_ERR_RANGE = 4 };
-enum { ORC_FMT_FP16 = 1, ORC_FMT_E8MY = 2, ORC_FMT_FIXED = 7 };
+enum { ORC_FMT_FP16 = 1, ORC_FMT_E8MY = 2, ORC_FMT_FIXED = 7, ORC_FMT_W64_E11MY = 8 };
 
 /* ------------------------------------------------------------------------ */
 /* Value formats (§4.2.2)                                                     */
@@ -109,6 +109,42 @@ int orc_e8my_bits(double v, int D, uint32_t *out)
     b = (b >> (D + 1)) << (D + 1);
     *out = b;
     return ORC_OK;
+}
+
+/* E11MY bits (1 sign, 11 exponent, Y = 51 - D mantissa bits, binary64 layout
+ * with the low D + 1 bits zero): the value format of 64-bit words (W = 64,
+ * V = 63 - D), E8MY's rule (§4.2.2) carried over to binary64: round half away
+ * from zero on the grid 2^(e - 53 + D + 1), e the binade of v, the grid of
+ * the smallest normal binade below it. D in [1, 31]. */
+static uint64_t f64_bits(double v)
+{
+    uint64_t b;
+    memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+int orc_e11my_bits(double v, int D, uint64_t *out)
+{
+    if (D < 1 || D > 31) return ORC_ERR_ARG;
+    if (isnan(v) || isinf(v)) return ORC_ERR_NONFINITE;
+    if (v == 0.0) { *out = signbit(v) ? 0x8000000000000000ull : 0ull; return ORC_OK; }
+    int ex;
+    (void)frexp(v, &ex); /* |v| in [2^(ex-1), 2^ex) */
+    if (ex < -1021) ex = -1021;
+    const double unit = ldexp(1.0, ex - 53 + D + 1);
+    const double r = round(v / unit) * unit; /* both steps exact; round(): halves away */
+    if (isinf(r)) return ORC_ERR_RANGE;
+    uint64_t b = f64_bits(r);
+    b = (b >> (D + 1)) << (D + 1);
+    *out = b;
+    return ORC_OK;
+}
+
+double orc_e11my_value(uint64_t bits)
+{
+    double v;
+    memcpy(&v, &bits, sizeof v);
+    return v;
 }
 
 /* Fixed point, an integer value format (§4.2.1 allows any V-bit format,
@@ -310,7 +346,7 @@ int64_t orc_row_words_w(int64_t i, const int64_t *rowptr, const int32_t *col, in
                         int64_t k_left, int D, int W, int64_t *dummies)
 {
     int64_t prev = orc_left_offset(i, sigma, k_left), words = 0;
-    const int64_t dmax = ((int64_t)1 << (W - 1)) - 1;
+    const int64_t dmax = W == 64 ? INT64_MAX : ((int64_t)1 << (W - 1)) - 1;
     *dummies = 0;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
         int64_t d = (int64_t)col[p] - prev;
@@ -352,7 +388,7 @@ int orc_encode_plan_w(int64_t n, int64_t m, const int64_t *rowptr, const int32_t
                       int64_t *words, int32_t *perm, int64_t *offset, int64_t *stats)
 {
     if (n < 0 || m < 0 || m >= ((int64_t)1 << 31) || C < 1 || sigma < 1 || D < 1 ||
-        D > W - 2 || (W != 16 && W != 32))
+        D > (W == 64 ? 31 : W - 2) || (W != 16 && W != 32 && W != 64))
         return ORC_ERR_ARG;
     int st = orc_check_csr(n, m, rowptr, col);
     if (st) return st;
@@ -451,6 +487,105 @@ int orc_decode(int64_t n, int32_t C, int32_t sigma, int32_t D, int64_t k_left,
         counts[orig] = cnt;
     }
     return ORC_OK;
+}
+
+/* 64-bit words (W = 64, §4.2.1 with V = 63 - D): a word with a value is
+ * field | (d << 1) | 1, the field an E11MY pattern whose low D + 1 bits are
+ * zero; a dummy is (d << 1) with flag 0 (63 delta bits, so one dummy covers any
+ * gap); padding is 0. Same slice layout and plan as the 32-bit words
+ * (orc_encode_plan_w with W = 64). */
+int orc_encode64_fill(int64_t n, const int64_t *rowptr, const int32_t *col, const uint64_t *field,
+                      int32_t C, int32_t sigma, int32_t D, int64_t k_left, const int32_t *perm,
+                      const int64_t *offset, uint64_t *pack)
+{
+    int64_t S = (n + C - 1) / C;
+    memset(pack, 0, sizeof(uint64_t) * (size_t)offset[S]);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t prev = orc_left_offset(i, sigma, k_left), j = 0;
+        for (int64_t p = rowptr[orig]; p < rowptr[orig + 1]; ++p) {
+            int64_t d = (int64_t)col[p] - prev;
+            if (d < 0) return ORC_ERR_ARG;
+            if (d >= ((int64_t)1 << D)) {
+                pack[offset[k] + j * C + l] = (uint64_t)d << 1;
+                ++j;
+                d = 0;
+            }
+            pack[offset[k] + j * C + l] = field[p] | ((uint64_t)d << 1) | 1u;
+            ++j;
+            prev = col[p];
+        }
+        if (offset[k] + j * C > offset[k + 1]) return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
+
+/* 64-bit words back to CSR in original row order (as orc_decode). */
+int orc_decode64(int64_t n, int32_t C, int32_t sigma, int32_t D, int64_t k_left,
+                 const int32_t *perm, const int64_t *offset, const uint64_t *pack,
+                 const int64_t *rowptr, int32_t *col_out, uint64_t *field_out, int64_t *counts)
+{
+    const uint64_t low = ((uint64_t)2 << D) - 1; /* flag and delta bits */
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C, orig = (i / sigma) * sigma + perm[i];
+        int64_t w = (offset[k + 1] - offset[k]) / C;
+        int64_t c = orc_left_offset(i, sigma, k_left), q = rowptr[orig], cnt = 0;
+        for (int64_t j = 0; j < w; ++j) {
+            const uint64_t wd = pack[offset[k] + j * C + l];
+            if (wd & 1u) {
+                c += (int64_t)((wd >> 1) & (((uint64_t)1 << D) - 1));
+                if (q < rowptr[orig + 1]) { col_out[q] = (int32_t)c; field_out[q] = wd & ~low; }
+                ++q;
+                ++cnt;
+            } else {
+                c += (int64_t)(wd >> 1);
+            }
+        }
+        counts[orig] = cnt;
+    }
+    return ORC_OK;
+}
+
+/* y = A x by the §4.4 algorithm over 64-bit words in double: per storage row,
+ * walk the slice's words, add every delta to the column, and for a word with
+ * a value add v * x_c with one fused multiply-add (fma(), correctly rounded),
+ * starting from +0, in stored order. y in original row order, or storage
+ * order with explicit_order. */
+void orc_packsell64_spmv_f64(int64_t n, int32_t C, int32_t sigma, int32_t D, int64_t k_left,
+                             const int32_t *perm, const int64_t *offset, const uint64_t *pack,
+                             const double *x, double *y, int explicit_order)
+{
+    const uint64_t low = ((uint64_t)2 << D) - 1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = i / C, l = i % C;
+        int64_t w = (offset[k + 1] - offset[k]) / C;
+        int64_t c = orc_left_offset(i, sigma, k_left);
+        double t = 0.0;
+        for (int64_t j = 0; j < w; ++j) {
+            const uint64_t wd = pack[offset[k] + j * C + l];
+            if (wd & 1u) {
+                c += (int64_t)((wd >> 1) & (((uint64_t)1 << D) - 1));
+                t = fma(orc_e11my_value(wd & ~low), x[c], t);
+            } else {
+                c += (int64_t)(wd >> 1);
+            }
+        }
+        y[explicit_order ? i : (i / sigma) * sigma + perm[i]] = t;
+    }
+}
+
+/* y = A x in double, one fused multiply-add per nonzero in column order from
+ * +0: the result of one thread walking one row's 64-bit words. */
+void orc_csr_spmv_fma_f64(int64_t n, const int64_t *rowptr, const int32_t *col,
+                          const double *val, const double *x, double *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) t = fma(val[p], x[col[p]], t);
+        y[i] = t;
+    }
 }
 
 /* 16-bit words (W = 16, D = 7): a word with a value is (code << 8) | (d << 1)
@@ -599,6 +734,19 @@ int orc_quantize(int64_t nnz, const double *val, int32_t fmt, int32_t D, uint32_
         int st = orc_value_field(val[p], fmt, D, &field[p]);
         if (st) { *bad = p; return st; }
         deq[p] = orc_field_value(field[p], fmt);
+    }
+    return ORC_OK;
+}
+
+/* E11MY fields (binary64 patterns) and their values of nnz values. */
+int orc_quantize_e11my(int64_t nnz, const double *val, int32_t D, uint64_t *field, double *deq,
+                       int64_t *bad)
+{
+    *bad = -1;
+    for (int64_t p = 0; p < nnz; ++p) {
+        int st = orc_e11my_bits(val[p], D, &field[p]);
+        if (st) { *bad = p; return st; }
+        deq[p] = orc_e11my_value(field[p]);
     }
     return ORC_OK;
 }
