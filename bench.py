@@ -186,11 +186,13 @@ class Clocks:
 
 
 def spmv_bytes(A, fmt_is_sell: bool):
-    # bytes per stored slot: FP32 SELL 8, FP16 SELL (format 6) 6, 16-bit words
-    # (format 5) 2, 32-bit PackSELL words 4
-    per = 8 if fmt_is_sell else (6 if A.format == 6 else 2 if A.format == 5 else 4)
+    # bytes per stored slot: FP32 SELL 8, FP64 SELL (format 4) 12, FP16 SELL
+    # (format 6) 6, 16-bit words (format 5) 2, 64-bit words (format 8) 8,
+    # 32-bit PackSELL words 4; x and y are FP64 for formats 4 and 8
+    per = {4: 12, 5: 2, 6: 6, 8: 8}.get(A.format, 8 if fmt_is_sell else 4)
+    vec = 8 if A.format in (4, 8) else 4
     perm = 0 if A.explicit_perm else A.n * A.perm_bytes
-    return per * A.n_words + 8 * (A.n_slices + 1) + perm + 4 * A.m + 4 * A.n
+    return per * A.n_words + 8 * (A.n_slices + 1) + perm + vec * (A.m + A.n)
 
 
 def time_launches(torch, fn, K, W):
@@ -593,7 +595,8 @@ def pcg_section(ps, torch, dev, grid, m_in):
     FP16, PackSELL E8M11 and FP32 SELL copies of the matrix. First with the
     paper's solver setting (sigma = 256, implicit permutation), then with
     sigma = 1 (no permutation: a stencil's rows are already of equal length,
-    and the permuted stores cost the SpMV about a fifth of its time)."""
+    and the permuted stores cost the SpMV about a fifth of its time). At sigma
+    = 256 also FP64 PCG and IO-CG with the FP64 operator in 64-bit words."""
     csr = I.poisson7_varcoef(grid, seed=0)
     b_h = I.uniform(csr.n, seed=1).astype(np.float64)
     rp = torch.from_numpy(csr.rowptr).to(dev)
@@ -627,6 +630,27 @@ def pcg_section(ps, torch, dev, grid, m_in):
                 sec[key]["inner_words"] = Ain.n_words
             del Ain
         del A64
+        if sigma == 256:
+            # the FP64 operator as 64-bit PackSELL words (E11M40, D = 11: 8 bytes
+            # per stored element against SELL's 12): FP64 PCG, and IO-CG with it
+            # as the outer operator
+            W64 = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="w64_e11my", D=11, sigma=sigma)
+            x.zero_()
+            _, info = ps.packsell_pcg(W64, b, x, rtol=1e-10, max_iters=20000, check_every=20,
+                                      check=False)
+            sec["fp64_pcg_w64"] = {k: info[k] for k in ("seconds", "iters", "relres_true", "status")}
+            sec["fp64_pcg_w64"]["speedup_vs_fp64_pcg"] = base / info["seconds"] if info["seconds"] else None
+            sec["fp64_pcg_w64"]["words"] = W64.n_words
+            Ain = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="fp16", D=15, sigma=sigma)
+            x.zero_()
+            _, info = ps.packsell_pcg(W64, b, x, A_inner=Ain, m_in=m_in[-1], rtol=1e-10,
+                                      max_iters=5000, check=False)
+            sec["iocg_fp16_w64_outer"] = {k: info[k] for k in ("seconds", "iters", "inner_iters",
+                                                               "relres_true", "status")}
+            sec["iocg_fp16_w64_outer"]["m_in"] = m_in[-1]
+            sec["iocg_fp16_w64_outer"]["speedup_vs_fp64_pcg"] = (base / info["seconds"]
+                                                                 if info["seconds"] else None)
+            del Ain, W64
     out["reordered_rcm"] = reordered_iocg(ps, torch, dev, csr, b_h, m_in[-1])
     return out
 
@@ -748,22 +772,32 @@ def run_ours(args):
                  ("fp16_v13", "fp16", 15),
                  ("e8m7", "e8my", 15),
                  ("e8m11", "e8my", 11), ("e8m15", "e8my", 7), ("w16_e4m3", "w16_e4m3", 7),
-                 ("sell_f16", "sell_f16", 15), ("fixed_d15", "fixed", 15))
+                 ("sell_f16", "sell_f16", 15), ("fixed_d15", "fixed", 15),
+                 # FP64 products (x, y FP64): plain SELL against 64-bit words
+                 ("sell_f64", "sell_f64", 15), ("w64_e11m40", "w64_e11my", 11))
         if args.formats != "all":
             keep = set(args.formats.split(",")) if args.formats != "none" else set()
             sweep = tuple(f for f in sweep if f[0] in keep)
         for name, fmt, D in sweep:
             A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt=fmt, D=D, **common)
+            f64op = fmt in ("sell_f64", "w64_e11my")
             if name.startswith("fp16_v"):
                 ps.packsell_set_spmv_variant(A, int(name.split("_v")[1]))
-            elif fmt not in ("sell_f32", "sell_f16", "fixed"):
+            elif fmt not in ("sell_f32", "sell_f16") and not f64op:
                 ps.packsell_tune_spmv(A, x, y, reps=20)
             nb = spmv_bytes(A, fmt == "sell_f32")
-            ms, _ = time_launches(torch, lambda: ps.packsell_spmv(A, x, y), K, W)
+            if f64op:
+                xd64 = x.double()
+                yd64 = torch.empty(csr.n, dtype=torch.float64, device=dev)
+                ms, _ = time_launches(torch, lambda: ps.packsell_spmv_f64(A, xd64, yd64), K, W)
+                yo = yd64
+            else:
+                ms, _ = time_launches(torch, lambda: ps.packsell_spmv(A, x, y), K, W)
+                yo = y
             formats[name] = {"GBps": nb / ms / 1e6, "GFLOPs": 2 * csr.nnz / ms / 1e6,
                              "us": ms * 1e3, "bytes": nb, "words": A.n_words,
                              "dummies": A.n_dummies, "footprint_vs_sell": None,
-                             "backward_error": backward_error(torch, ps, A, y, y64, normA, normx)}
+                             "backward_error": backward_error(torch, ps, A, yo, y64, normA, normx)}
             del A
         # the paper's FP16 SpMV configuration: x and y in binary16
         if args.formats == "all":
@@ -807,6 +841,9 @@ def run_ours(args):
     for v in formats.values():
         v["footprint_vs_sell"] = v["bytes"] / sell["bytes"] if sell else None
     formats.get("cusparse_csr_f32", {}).pop("footprint_vs_sell", None)
+    if "sell_f64" in formats and "w64_e11m40" in formats:  # the FP64 products
+        formats["w64_e11m40"]["speedup_vs_sell_f64"] = (formats["sell_f64"]["us"]
+                                                       / formats["w64_e11m40"]["us"])
 
     # whole-job numbers: max time over ranks, units summed over ranks
     value, t_step_ms = whole_job(torch, B16, total16 / K, world, dev)

@@ -96,9 +96,10 @@ typedef enum packsell_status {
  *         rounded half away from zero. Integer-valued matrices (stencils with
  *         integer coefficients) are exact. D in [6, 22] (V <= 25 bits, so
  *         every q converts to FP32 exactly). Supported by
- *         packsell_encode, packsell_spmv (the thread-per-row variant 1, which
- *         sums the decoded values q * 2^s in stored order: the bits of the FP32
- *         twin of the decoded matrix), packsell_spmv_host, packsell_get_info,
+ *         packsell_encode, packsell_spmv (the thread-per-row variant 1 and,
+ *         with C = 32, variant 13, both summing the decoded values q * 2^s in
+ *         stored order: the bits of the FP32 twin of the decoded matrix;
+ *         packsell_tune_spmv times the two), packsell_spmv_host, packsell_get_info,
  *         packsell_storage_rows, packsell_export and packsell_import (the
  *         blob carries s); the other calls return PACKSELL_ERR_INVALID_ARG.
  * SELL_F16: plain SELL-C-sigma (§3) with binary16 values (round to nearest
@@ -111,6 +112,22 @@ typedef enum packsell_status {
  *         thread-per-row kernel), packsell_get_info, packsell_storage_rows,
  *         packsell_export, packsell_import and packsell_f3r; the other calls
  *         return PACKSELL_ERR_INVALID_ARG.
+ * W64_E11MY: 64-bit words (W = 64, another word size of §4.2.1; V = 63 - D):
+ *         bit 0 flag, bits 1..D delta, bits D+1..63 an E11MY value, i.e. a
+ *         binary64 pattern (1 sign, 11 exponent bits, Y = 51 - D mantissa
+ *         bits) with the low D+1 bits clear, rounded half away from zero on
+ *         its grid (E8MY's rule carried over to binary64; a value that
+ *         rounds past the largest finite double is PACKSELL_ERR_RANGE). A
+ *         dummy holds a 63-bit delta, so one dummy covers any gap: the word
+ *         counts, perm and offsets are those of 32-bit words with the same D.
+ *         D in [1, 31]; n_words counts 64-bit words. The products are FP64
+ *         (x, y and accumulation): the FP64 operator of the solvers at 8
+ *         bytes per stored element (SELL_F64 takes 12). Supported by
+ *         packsell_encode, packsell_spmv_f64, packsell_inv_diag,
+ *         packsell_pcg and packsell_pcg_noalloc (as A_outer), packsell_f3r
+ *         (as A_outer, and as A_mid and A_low of FP64-F3R),
+ *         packsell_get_info, packsell_storage_rows, packsell_export and
+ *         packsell_import; the other calls return PACKSELL_ERR_INVALID_ARG.
  */
 typedef enum packsell_format {
     PACKSELL_FMT_FP16 = 1,
@@ -119,7 +136,8 @@ typedef enum packsell_format {
     PACKSELL_FMT_SELL_F64 = 4,
     PACKSELL_FMT_W16_E4M3 = 5,
     PACKSELL_FMT_SELL_F16 = 6,
-    PACKSELL_FMT_FIXED = 7
+    PACKSELL_FMT_FIXED = 7,
+    PACKSELL_FMT_W64_E11MY = 8
 } packsell_format;
 
 typedef struct packsell_params {
@@ -153,7 +171,8 @@ typedef struct packsell_info {
     int32_t perm_bytes;     /* bytes per perm entry: 0 (sigma = 1), 1 or 2 */
     int64_t bytes;          /* device bytes the matrix holds (all arrays) */
     /* device arrays (read-only views for tests and tools) */
-    const uint32_t *pack;   /* PackSELL words, NULL for SELL formats */
+    const uint32_t *pack;   /* 32-bit PackSELL words; NULL for SELL formats and for 16- and
+                               64-bit words (packsell_export copies those) */
     const void *val;        /* SELL values (float or double), NULL for PackSELL */
     const int32_t *col;     /* SELL columns, NULL for PackSELL */
     const int64_t *offset;  /* n_slices + 1 word offsets of the slices */
@@ -280,7 +299,10 @@ packsell_status packsell_spmv_x16(const packsell_matrix *A, const uint16_t *x, u
                                   void *stream);
 
 /* y = A x in double for a SELL_F64 matrix (§3's SELL-C-sigma; the FP64
- * operator of §5.2.2's outer iteration). */
+ * operator of §5.2.2's outer iteration) or a W64_E11MY matrix (§4.4's
+ * algorithm on 64-bit words: one thread per row, one FP64 fused multiply-add
+ * per real word in stored order from +0). x: double [m], y: double [n]
+ * (original order, or storage order with explicit_perm). No allocation. */
 packsell_status packsell_spmv_f64(const packsell_matrix *A, const double *x, double *y,
                                   void *stream);
 
@@ -575,7 +597,7 @@ typedef struct packsell_solve_result {
 } packsell_solve_result;
 
 /* The Jacobi preconditioner of §5.2 (diagonal scaling): out[i] = 1 / a_ii
- * (double [n]) for a square SELL_F64 matrix, in the
+ * (double [n]) for a square SELL_F64 or W64_E11MY matrix, in the
  * original row order: the Jacobi preconditioner of packsell_pcg. Rows whose
  * diagonal is missing or zero get 1. */
 packsell_status packsell_inv_diag(const packsell_matrix *A, double *out, void *stream);
@@ -593,7 +615,7 @@ size_t packsell_pcg_workspace_bytes(int64_t n, int32_t m_in, int32_t has_diag,
                                     int32_t max_iters);
 
 /* Solve A x = b for SPD A (§5.2.2: FP64 PCG, or the inner-outer CG).
- *   A_outer : SELL_F64 matrix (square, implicit permutation): the FP64
+ *   A_outer : SELL_F64 or W64_E11MY matrix (square, implicit permutation): the FP64
  *             operator of the outer iteration and of the residual check
  *   A_inner : PackSELL (FP16 / E8MY) or SELL_F32 copy of the same matrix for
  *             the inner FP32 PCG (ignored when m_in = 0)
@@ -697,8 +719,8 @@ void packsell_f3r_opts_default(packsell_f3r_opts *o);
  *  - FP16-F3R: A_mid SELL_F32 (layer 2 in FP32) and A_low a PackSELL FP16
  *    (or E8MY) or an FP16 SELL matrix (layers 3 and 4: FP32 vectors, the
  *    FP16 SpMV of the paper);
- *  - FP64-F3R: A_mid and A_low SELL_F64 (every layer in FP64).
- * A_outer is SELL_F64; all three square, of the same size, rows in original
+ *  - FP64-F3R: A_mid and A_low SELL_F64 or W64_E11MY (every layer in FP64).
+ * A_outer is SELL_F64 or W64_E11MY; all three square, of the same size, rows in original
  * order (any C and sigma). Krylov bases by classical Gram-Schmidt with
  * deterministic FP64 dot products, updates rounded once to the layer's
  * precision; Hessenberg matrices, Givens rotations and least-squares solves

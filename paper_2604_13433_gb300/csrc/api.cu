@@ -26,6 +26,7 @@ void clear_error() { g_last_error.clear(); }
 int64_t matrix_bytes(const Matrix &A) {
     int64_t b = 8 * (A.n_slices + 1) + (int64_t)A.perm_bytes * A.n;
     if (is_w16(A.p.format)) b += 2 * A.n_words;
+    else if (is_w64(A.p.format)) b += 8 * A.n_words;
     else if (is_sell16(A.p.format)) b += 6 * A.n_words;
     else if (is_packed(A.p.format) || is_fixed(A.p.format)) b += 4 * A.n_words;
     else b += (A.p.format == PACKSELL_FMT_SELL_F64 ? 12 : 8) * A.n_words;
@@ -48,6 +49,9 @@ packsell_status no_w16(const Matrix &A, const char *what) {
         return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for FP16 SELL");
     if (is_fixed(A.p.format))
         return fail(PACKSELL_ERR_INVALID_ARG, std::string(what) + ": not available for fixed point");
+    if (is_w64(A.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    std::string(what) + ": not available for 64-bit words (FP64 products only)");
     return PACKSELL_OK;
 }
 
@@ -71,6 +75,7 @@ struct BlobHeader {
 // column of plain SELL.
 inline size_t blob_word_bytes(int fmt) {
     if (is_w16(fmt)) return 2;
+    if (is_w64(fmt)) return 8;
     if (is_packed(fmt) || is_fixed(fmt)) return 4;
     if (is_sell16(fmt)) return 6;
     return fmt == PACKSELL_FMT_SELL_F64 ? 12 : 8;
@@ -182,6 +187,8 @@ packsell_status packsell_export(const packsell_matrix *Ah, void *h_blob, size_t 
     }
     if (is_w16(A.p.format)) {
         PS_CUDA(cudaMemcpyAsync(dst, A.pack16, 2 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
+    } else if (is_w64(A.p.format)) {
+        PS_CUDA(cudaMemcpyAsync(dst, A.pack64, 8 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
     } else if (is_packed(A.p.format) || is_fixed(A.p.format)) {
         PS_CUDA(cudaMemcpyAsync(dst, A.pack, 4 * (size_t)A.n_words, cudaMemcpyDeviceToHost, s));
     } else {
@@ -205,11 +212,12 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
     memcpy(&h, h_blob, sizeof(h));
     const packsell_params &p = h.p;
     const bool fmt_ok = is_packed(p.format) || is_sell(p.format) || is_w16(p.format) ||
-                        is_sell16(p.format) || is_fixed(p.format);
+                        is_sell16(p.format) || is_fixed(p.format) || is_w64(p.format);
     // delta bits each word format accepts (packsell_encode's own ranges)
     const bool d_ok = is_packed(p.format)  ? (p.D >= 1 && p.D <= 22)
                       : is_fixed(p.format) ? (p.D >= 6 && p.D <= 22)
                       : is_w16(p.format)   ? p.D == 7
+                      : is_w64(p.format)   ? (p.D >= 1 && p.D <= 31)
                                            : true;
     if (h.magic != kMagic || !fmt_ok || !d_ok || h.n < 0 || h.n >= (1ll << 31) || h.m < 0 ||
         h.m >= (1ll << 31) || p.C < 1 || p.C > 1024 || p.sigma < 1 || p.sigma > 65536 ||
@@ -267,7 +275,13 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
         src += (size_t)h.perm_bytes * h.n;
     }
     size_t nw = (size_t)std::max<int64_t>(h.n_words, 1);
-    if (is_w16(p.format)) {
+    if (is_w64(p.format)) {
+        if (cudaMalloc(&A->pack64, 8 * nw) != cudaSuccess)
+            return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
+        if (cudaMemcpyAsync(A->pack64, src, 8 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
+    } else if (is_w16(p.format)) {
         if (cudaMalloc(&A->pack16, 2 * nw) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_import: allocation"));
         if (cudaMemcpyAsync(A->pack16, src, 2 * (size_t)h.n_words, cudaMemcpyHostToDevice, s) !=
@@ -313,7 +327,8 @@ packsell_status packsell_set_spmv_variant(packsell_matrix *A, int32_t variant) {
     if (variant >= 2 && variant <= 4 && !m->part[variant - 2])
         return fail(PACKSELL_ERR_INVALID_ARG,
                     "packsell_set_spmv_variant: bulk-staged needs a PackSELL matrix with C = 32");
-    if (variant >= 5 && (!is_packed(m->p.format) || m->p.C != 32))
+    const bool fixed13 = variant == 13 && is_fixed(m->p.format);  // fixed point runs variant 13 too
+    if (variant >= 5 && ((!is_packed(m->p.format) && !fixed13) || m->p.C != 32))
         return fail(PACKSELL_ERR_INVALID_ARG,
                     "packsell_set_spmv_variant: variants 5-10, 12 and 13 need a PackSELL matrix with C = 32");
     if (variant == 12 && m->max_width > 16)
@@ -344,7 +359,8 @@ static packsell_status tune_variants(Matrix *m, const float *x, float *y, int re
     float best_ms = 0.f;
     packsell_status st = PACKSELL_OK;
     for (int var = 1; var <= nvar && st == PACKSELL_OK; ++var) {
-        if (var >= 2 && !is_packed(m->p.format)) continue;
+        // fixed point: the thread-per-row kernel and variant 13
+        if (var >= 2 && !is_packed(m->p.format) && !(is_fixed(m->p.format) && var == 13)) continue;
         if (var == 11 && !m->csr_items) continue;
         if (var == 14 && !m->split_items) continue;
         if (((var >= 5 && var <= 10) || var == 12 || var == 13) && m->p.C != 32) continue;
@@ -387,6 +403,8 @@ packsell_status packsell_tune_spmv(packsell_matrix *A, const float *x, float *y,
     clear_error();
     if (!A || (M(A)->m > 0 && !x) || (M(A)->n > 0 && !y) || reps < 1)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: bad argument");
+    if (is_f64_op(M(A)->p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_tune_spmv: FP64 matrices have one product");
     return tune_variants(reinterpret_cast<Matrix *>(A), x, y, reps, h_times, as_stream(stream),
                          nullptr, nullptr);
 }
@@ -578,6 +596,8 @@ packsell_status packsell_spmv_host(const packsell_matrix *A, const float *h_x, f
     const Matrix &m = *M(A);
     if ((m.m > 0 && (!h_x || !d_x)) || (m.n > 0 && (!h_y || !d_y)))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_host: NULL buffer");
+    if (is_f64_op(m.p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_host: FP64 matrices need packsell_spmv_f64");
     cudaStream_t s = as_stream(stream);
     if (m.m > 0)
         PS_CUDA(cudaMemcpyAsync(d_x, h_x, sizeof(float) * (size_t)m.m, cudaMemcpyHostToDevice, s));

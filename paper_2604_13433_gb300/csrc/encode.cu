@@ -171,6 +171,36 @@ __global__ void k_quantize(int64_t nnz, const T *__restrict__ val, int fmt, int 
     }
 }
 
+// E11MY field of a 64-bit word (the value bits D+1..63): the binary64
+// pattern of v with half a unit of the D + 1 dropped bits added to its
+// magnitude, then those bits cleared (round half away from zero, subnormals
+// on the grid of the smallest normal binade); an all-ones exponent after the
+// rounding is out of range.
+template <typename T>
+__device__ __forceinline__ int field_e11my(T v, int D, unsigned long long &field) {
+    const double d = (double)v;
+    if (!isfinite(d)) return PACKSELL_ERR_NONFINITE;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long sign = b & 0x8000000000000000ull;
+    unsigned long long mag = b & 0x7fffffffffffffffull;
+    mag = (mag + (1ull << D)) & ~((2ull << D) - 1ull);
+    if ((mag >> 52) == 0x7ffull) return PACKSELL_ERR_RANGE;
+    field = sign | mag;
+    return 0;
+}
+
+template <typename T>
+__global__ void k_quantize64(int64_t nnz, const T *__restrict__ val, int D,
+                             unsigned long long *__restrict__ field, DevStatus *st) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long f = 0;
+        const int err = field_e11my(val[p], D, f);
+        if (err) dev_fail(st, err, p);
+        field[p] = f;
+    }
+}
+
 __device__ __forceinline__ long long resolve_k_left(long long user, const unsigned long long *kl) {
     return user >= 0 ? user : (long long)*kl;
 }
@@ -191,7 +221,8 @@ __global__ void k_count_words(int n, const int64_t *__restrict__ rowptr,
         if (packed) {
             long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
             long long lim = 1ll << D;
-            const long long dmax = (1ll << (W - 1)) - 1;  // a dummy's delta field
+            // a dummy's delta field: W - 1 bits
+            const long long dmax = W >= 64 ? 0x7fffffffffffffffll : (1ll << (W - 1)) - 1;
             for (int64_t p = a; p < b; ++p) {
                 long long d = (long long)col[p] - prev;
                 if (d < 0) {
@@ -395,6 +426,42 @@ __global__ void k_scatter_packed(int n, int64_t rows_total, int C, int sigma, lo
     for (; j < w; ++j) dst[j * C] = 0u;
 }
 
+// 64-bit words: field | (d << 1) | 1 with a value, (d << 1) for a dummy (63
+// delta bits: one dummy covers any gap), 0 for padding.
+__global__ void k_scatter_w64(int n, int64_t rows_total, int C, int sigma, long long k_left_user,
+                              const unsigned long long *kl, int D,
+                              const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const unsigned long long *__restrict__ field, const void *perm,
+                              int perm_bytes, const int64_t *__restrict__ offset,
+                              unsigned long long *__restrict__ pack) {
+    int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ii >= rows_total) return;
+    int i = (int)ii;
+    int64_t k = ii / C;
+    int l = (int)(ii - k * C);
+    int64_t s = offset[k];
+    int64_t w = (offset[k + 1] - s) / C;
+    unsigned long long *dst = pack + s + l;
+    int64_t j = 0;
+    if (i < n) {
+        int r = orig_row(i, sigma, perm, perm_bytes);
+        long long prev = left_offset(i, sigma, resolve_k_left(k_left_user, kl));
+        const long long lim = 1ll << D;
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+            long long d = (long long)col[p] - prev;
+            if (d >= lim) {
+                dst[j * C] = (unsigned long long)d << 1;
+                ++j;
+                d = 0;
+            }
+            dst[j * C] = field[p] | ((unsigned long long)d << 1) | 1ull;
+            ++j;
+            prev = col[p];
+        }
+    }
+    for (; j < w; ++j) dst[j * C] = 0ull;
+}
+
 // 16-bit words: (code << 8) | (d << 1) | 1 with a value, (q << 1) for a
 // dummy of q < 2^15, 0 for padding; dummies while the delta is 2^7 or more.
 __global__ void k_scatter_w16(int n, int64_t rows_total, int C, int sigma, long long k_left_user,
@@ -528,6 +595,7 @@ struct Temps {
 void free_matrix_arrays(Matrix *A) {
     cudaFree(A->pack);
     cudaFree(A->pack16);
+    cudaFree(A->pack64);
     cudaFree(A->val);
     cudaFree(A->col);
     cudaFree(A->offset);
@@ -549,7 +617,8 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
     const int fmt = p.format;
     if (!out) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: out is NULL");
     *out = nullptr;
-    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt) && !is_sell16(fmt) && !is_fixed(fmt))
+    if (!is_packed(fmt) && !is_sell(fmt) && !is_w16(fmt) && !is_sell16(fmt) && !is_fixed(fmt) &&
+        !is_w64(fmt))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: unknown format");
     if (p.C < 1 || p.C > 1024) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: C must be in [1, 1024]");
     if (p.sigma < 1 || p.sigma > 65536)
@@ -563,15 +632,19 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: FIXED needs D in [6, 22]");
     if (is_w16(fmt) && p.D != 7)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: W16_E4M3 needs D = 7");
+    // 64-bit words: columns stay below 2^31, so more delta bits buy nothing
+    if (is_w64(fmt) && (p.D < 1 || p.D > 31))
+        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: W64_E11MY needs D in [1, 31]");
     if (n < 0 || m < 0 || nnz < 0 || n >= (1ll << 31) || m >= (1ll << 31))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: n and m must be in [0, 2^31)");
     if (!rowptr || (nnz > 0 && (!col || !val)))
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: NULL array");
     if (p.k_left < -1) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_encode: k_left < -1");
 
-    const bool packed = is_packed(fmt) || is_w16(fmt) || is_fixed(fmt);  // delta-value words
+    // delta-value words
+    const bool packed = is_packed(fmt) || is_w16(fmt) || is_fixed(fmt) || is_w64(fmt);
     const int D = packed ? p.D : 31;
-    const int W = is_w16(fmt) ? 16 : 32;
+    const int W = is_w16(fmt) ? 16 : is_w64(fmt) ? 64 : 32;
     const int64_t S = (n + p.C - 1) / p.C;
     const int perm_bytes = (p.sigma == 1) ? 0 : (p.sigma <= 256 ? 1 : 2);
 
@@ -595,13 +668,15 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         unsigned long long *kl = nullptr, *total = nullptr;
         int *maxw = nullptr;
         uint32_t *field = nullptr;
+        unsigned long long *field64 = nullptr;  // E11MY fields of 64-bit words
         int32_t *words = nullptr, *words_st = nullptr;
         int64_t *slice_words = nullptr;
         cudaError_t e = cudaSuccess;
         if ((e = T.get(&st, sizeof(DevStatus))) || (e = T.get(&kl, 8)) || (e = T.get(&total, 8)) ||
             (e = T.get(&maxw, 4)) || (e = T.get(&words, 4 * (size_t)n)) ||
             (e = T.get(&words_st, 4 * (size_t)n)) || (e = T.get(&slice_words, 8 * (size_t)S)) ||
-            ((packed || is_sell16(fmt)) && (e = T.get(&field, 4 * (size_t)nnz))))
+            (((packed && !is_w64(fmt)) || is_sell16(fmt)) && (e = T.get(&field, 4 * (size_t)nnz))) ||
+            (is_w64(fmt) && (e = T.get(&field64, 8 * (size_t)nnz))))
             return bail(e == cudaErrorMemoryAllocation
                             ? fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: temporaries")
                             : cuda_fail(e, "cudaMallocAsync"));
@@ -629,7 +704,13 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
             memcpy(&M, &hmax, sizeof M);
             A->value_exp = fixed_exponent(M, p.D);
         }
-        if ((packed || is_sell16(fmt)) && nnz > 0) {
+        if (is_w64(fmt) && nnz > 0) {
+            const int qb = std::min(blocks_for(nnz), 152 * 64);
+            if (val_is_f64)
+                k_quantize64<double><<<qb, TPB, 0, s>>>(nnz, (const double *)val, D, field64, st);
+            else
+                k_quantize64<float><<<qb, TPB, 0, s>>>(nnz, (const float *)val, D, field64, st);
+        } else if ((packed || is_sell16(fmt)) && nnz > 0) {
             int qb = blocks_for(nnz);
             qb = std::min(qb, 152 * 64);
             // FP16 SELL takes the FP16 quantiser of the packed format
@@ -684,7 +765,15 @@ packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int6
         A->n_pad = nw - (int64_t)htotal;
         A->max_width = hmaxw;
 
-        if (is_w16(fmt)) {
+        if (is_w64(fmt)) {
+            if (cudaMalloc(&A->pack64, sizeof(uint64_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
+                return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
+            int64_t rows_total = S * p.C;
+            if (rows_total > 0)
+                k_scatter_w64<<<blocks_for(rows_total), TPB, 0, s>>>(
+                    (int)n, rows_total, p.C, p.sigma, A->p.k_left, kl, D, rowptr, col, field64,
+                    A->perm, perm_bytes, A->offset, (unsigned long long *)A->pack64);
+        } else if (is_w16(fmt)) {
             if (cudaMalloc(&A->pack16, sizeof(uint16_t) * std::max<int64_t>(nw, 1)) != cudaSuccess)
                 return bail(fail(PACKSELL_ERR_NO_MEMORY, "packsell_encode: word array"));
             int64_t rows_total = S * p.C;
@@ -765,9 +854,10 @@ void destroy_matrix(Matrix *A) {
 
 // ---- validation of imported matrices ----
 namespace {
-// What k_validate decodes: 32-bit words (FP16, E8MY, fixed point), 16-bit
-// words, or the column array of plain SELL (FP16 SELL pads with column -1).
-enum ValidateKind { kValWords32 = 0, kValWords16 = 1, kValCols = 2, kValCols16 = 3 };
+// What k_validate decodes: 32-bit words (FP16, E8MY, fixed point), 16- or
+// 64-bit words, or the column array of plain SELL (FP16 SELL pads with
+// column -1).
+enum ValidateKind { kValWords32 = 0, kValWords16 = 1, kValCols = 2, kValCols16 = 3, kValWords64 = 4 };
 
 template <int KIND>
 __global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left, int D,
@@ -793,18 +883,23 @@ __global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left,
     }
     int64_t w = (e - s) / C;
     unsigned long long cnt = 0;
-    if (KIND == kValWords32 || KIND == kValWords16) {
+    if (KIND == kValWords32 || KIND == kValWords16 || KIND == kValWords64) {
         // flag 1: D delta bits; flag 0 (dummy, padding): the rest of the word
-        const uint32_t dmask = (1u << D) - 1u;
-        const uint32_t wide = KIND == kValWords32 ? 0x7fffffffu : 0x7fffu;
+        const unsigned long long dmask = (1ull << D) - 1ull;
+        const unsigned long long wide = KIND == kValWords64   ? 0x7fffffffffffffffull
+                                        : KIND == kValWords32 ? 0x7fffffffull
+                                                              : 0x7fffull;
         long long c = left_offset(i, sigma, k_left);
         for (int64_t j = 0; j < w; ++j) {
             const int64_t at = s + j * C + l;
-            const uint32_t wd = KIND == kValWords32 ? ((const uint32_t *)words)[at]
-                                                    : (uint32_t)((const uint16_t *)words)[at];
-            const uint32_t flag = wd & 1u;
-            c += (wd >> 1) & (flag ? dmask : wide);
-            if (wd != 0u && c >= m) {
+            const unsigned long long wd =
+                KIND == kValWords64   ? ((const unsigned long long *)words)[at]
+                : KIND == kValWords32 ? (unsigned long long)((const uint32_t *)words)[at]
+                                      : (unsigned long long)((const uint16_t *)words)[at];
+            const unsigned long long flag = wd & 1ull;
+            const unsigned long long delta = (wd >> 1) & (flag ? dmask : wide);
+            // a column past m (or a delta that would overflow the sum) is corrupt
+            if (wd != 0ull && (delta >= (unsigned long long)m || (c += (long long)delta) >= m)) {
                 dev_fail(st, PACKSELL_ERR_CORRUPT, at);
                 return;
             }
@@ -847,6 +942,10 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
         if (is_packed(fmt) || is_fixed(fmt))
             k_validate<kValWords32><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,
                                                       A.p.D, A.offset, A.pack, nullptr, A.perm,
+                                                      A.perm_bytes, cnt, st);
+        else if (is_w64(fmt))
+            k_validate<kValWords64><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,
+                                                      A.p.D, A.offset, A.pack64, nullptr, A.perm,
                                                       A.perm_bytes, cnt, st);
         else if (is_w16(fmt))
             k_validate<kValWords16><<<g, TPB, 0, s>>>((int)A.n, A.m, A.p.C, A.p.sigma, A.p.k_left,

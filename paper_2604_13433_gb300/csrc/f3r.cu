@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(FT) k_resid(int64_t n, const double *__restric
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// one product of a layer: double vectors on SELL_F64, float vectors on the
-// other formats
+// one product of a layer: double vectors on the FP64 formats (SELL_F64,
+// 64-bit words), float vectors on the others
 packsell_status layer_spmv(const Matrix &A, const double *x, double *y, cudaStream_t s) {
     return spmv_f64_impl(A, x, y, s);
 }
@@ -564,17 +564,17 @@ packsell_status f3r_impl(const Matrix *A1, const Matrix *A2, const Matrix *A3, c
     if (!A1 || !A2 || !A3) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_f3r: NULL matrix");
     const int64_t n = A1->n;
     auto square = [&](const Matrix *A) { return A->n == n && A->m == n && !A->p.explicit_perm; };
-    if (A1->p.format != PACKSELL_FMT_SELL_F64 || !square(A1) || !square(A2) || !square(A3))
+    if (!is_f64_op(A1->p.format) || !square(A1) || !square(A2) || !square(A3))
         return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_f3r: A_outer must be SELL_F64; all three square, of one size, rows "
-                    "in original order");
-    const bool all64 = A2->p.format == PACKSELL_FMT_SELL_F64 && A3->p.format == PACKSELL_FMT_SELL_F64;
+                    "packsell_f3r: A_outer must be SELL_F64 or W64_E11MY; all three square, of "
+                    "one size, rows in original order");
+    const bool all64 = is_f64_op(A2->p.format) && is_f64_op(A3->p.format);
     const bool mixed = A2->p.format == PACKSELL_FMT_SELL_F32 &&
                        (A3->p.format == PACKSELL_FMT_FP16 || A3->p.format == PACKSELL_FMT_SELL_F16 ||
                         A3->p.format == PACKSELL_FMT_E8MY);
     if (!all64 && !mixed)
         return fail(PACKSELL_ERR_INVALID_ARG,
-                    "packsell_f3r: layers 2-4 need SELL_F64 matrices (FP64-F3R) or SELL_F32 and a "
+                    "packsell_f3r: layers 2-4 need FP64 matrices (FP64-F3R) or SELL_F32 and a "
                     "PackSELL / FP16 SELL matrix (FP16-F3R)");
     if (o.m1 < 1 || o.m1 > 60 || o.m2 < 1 || o.m2 > 60 || o.m3 < 1 || o.m3 > 60 || o.m4 < 1 ||
         o.max_iters < 1 || !(o.rtol > 0.0) || !(o.omega > 0.0))

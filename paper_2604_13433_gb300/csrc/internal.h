@@ -38,6 +38,7 @@ struct Matrix {
     // device arrays
     uint32_t *pack = nullptr;  // PackSELL words
     uint16_t *pack16 = nullptr;  // 16-bit words (PACKSELL_FMT_W16_E4M3)
+    uint64_t *pack64 = nullptr;  // 64-bit words (PACKSELL_FMT_W64_E11MY)
     void *val = nullptr;       // SELL values (float / double)
     int32_t *col = nullptr;    // SELL columns
     int64_t *offset = nullptr; // n_slices + 1
@@ -75,6 +76,9 @@ inline bool is_sell(int fmt) { return fmt == PACKSELL_FMT_SELL_F32 || fmt == PAC
 inline bool is_w16(int fmt) { return fmt == PACKSELL_FMT_W16_E4M3; }
 inline bool is_sell16(int fmt) { return fmt == PACKSELL_FMT_SELL_F16; }
 inline bool is_fixed(int fmt) { return fmt == PACKSELL_FMT_FIXED; }
+inline bool is_w64(int fmt) { return fmt == PACKSELL_FMT_W64_E11MY; }
+// the formats whose products are FP64 (packsell_spmv_f64)
+inline bool is_f64_op(int fmt) { return fmt == PACKSELL_FMT_SELL_F64 || is_w64(fmt); }
 
 // thread-local error message
 packsell_status fail(packsell_status st, const std::string &msg);
@@ -205,6 +209,12 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
                              cudaStream_t s);
 packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
                              const Red &red, cudaStream_t s);
+
+// w64.cu: products on 64-bit words
+packsell_status spmv_w64_impl(const Matrix &A, const double *x, double *y, cudaStream_t s);
+packsell_status spmv_dot_w64(const Matrix &A, const double *x, double *y, const double *b,
+                             const Red &red, unsigned grid, cudaStream_t s);
+packsell_status inv_diag_w64(const Matrix &A, double *out, cudaStream_t s);
 
 }  // namespace packsell
 

@@ -339,8 +339,9 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
     packsell_solve_opts o = o_in;
     if (noalloc) o.use_graph = 0;
     const bool io = o.m_in > 0;
-    if (!A64 || A64->p.format != PACKSELL_FMT_SELL_F64)
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_pcg: A_outer must be a SELL_F64 matrix");
+    if (!A64 || !is_f64_op(A64->p.format))
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_pcg: A_outer must be a SELL_F64 or W64_E11MY matrix");
     const int64_t n = A64->n;
     if (A64->m != n || A64->p.explicit_perm)
         return fail(PACKSELL_ERR_INVALID_ARG,

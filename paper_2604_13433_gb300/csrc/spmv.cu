@@ -466,6 +466,16 @@ packsell_status launch_prefetch_pdl(const Matrix &A, const void *perm, int pb, c
     return PACKSELL_OK;
 }
 
+// variant 13 with its round size fitted to the widest slice (as variant 5)
+template <int FMT>
+packsell_status prefetch_pdl_rounds(int pf, const Matrix &A, const void *perm, int pb,
+                                    const float *x, float *y, cudaStream_t s) {
+    if (pf == 8) return launch_prefetch_pdl<FMT, 8, 6>(A, perm, pb, x, y, s);
+    if (pf == 10) return launch_prefetch_pdl<FMT, 10, 6>(A, perm, pb, x, y, s);
+    if (pf == 12) return launch_prefetch_pdl<FMT, 12, 5>(A, perm, pb, x, y, s);
+    return launch_prefetch_pdl<FMT, 16, 5>(A, perm, pb, x, y, s);
+}
+
 template <int FMT, int PF, int MINB, bool PERM>
 int pipe_blocks() {
     // persistent grid: every block resident at once (cached as in launch_dual)
@@ -1113,22 +1123,15 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
         return h ? launch_dual<PACKSELL_FMT_FP16, 16, 3>(A, perm, pb, x, y, s)
                  : launch_dual<PACKSELL_FMT_E8MY, 16, 3>(A, perm, pb, x, y, s);
     }
-    if (var == 13 && is_packed(A.p.format)) {
+    if (var == 13 && (is_packed(A.p.format) || is_fixed(A.p.format))) {
         if (A.p.C != 32)
             return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: variant 13 needs C = 32");
-        const bool h = A.p.format == PACKSELL_FMT_FP16;
         const int pf = round_words(A.max_width);
-        if (pf == 8)
-            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 8, 6>(A, perm, pb, x, y, s)
-                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 8, 6>(A, perm, pb, x, y, s);
-        if (pf == 10)
-            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 10, 6>(A, perm, pb, x, y, s)
-                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 10, 6>(A, perm, pb, x, y, s);
-        if (pf == 12)
-            return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 12, 5>(A, perm, pb, x, y, s)
-                     : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 12, 5>(A, perm, pb, x, y, s);
-        return h ? launch_prefetch_pdl<PACKSELL_FMT_FP16, 16, 5>(A, perm, pb, x, y, s)
-                 : launch_prefetch_pdl<PACKSELL_FMT_E8MY, 16, 5>(A, perm, pb, x, y, s);
+        switch (A.p.format) {
+            case PACKSELL_FMT_FP16: return prefetch_pdl_rounds<PACKSELL_FMT_FP16>(pf, A, perm, pb, x, y, s);
+            case PACKSELL_FMT_E8MY: return prefetch_pdl_rounds<PACKSELL_FMT_E8MY>(pf, A, perm, pb, x, y, s);
+            default: return prefetch_pdl_rounds<PACKSELL_FMT_FIXED>(pf, A, perm, pb, x, y, s);
+        }
     }
     if ((var == 5 || var == 6) && is_packed(A.p.format)) {
         if (A.p.C != 32)
@@ -1189,15 +1192,18 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
             break;
         }
         default:
-            return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv: SELL_F64 needs packsell_spmv_f64");
+            return fail(PACKSELL_ERR_INVALID_ARG,
+                        "packsell_spmv: SELL_F64 and W64_E11MY need packsell_spmv_f64");
     }
     PS_LAUNCH_CHECK("packsell_spmv");
     return PACKSELL_OK;
 }
 
 packsell_status spmv_f64_impl(const Matrix &A, const double *x, double *y, cudaStream_t s) {
+    if (is_w64(A.p.format)) return spmv_w64_impl(A, x, y, s);
     if (A.p.format != PACKSELL_FMT_SELL_F64)
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_spmv_f64: matrix is not SELL_F64");
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_spmv_f64: matrix is neither SELL_F64 nor W64_E11MY");
     if (A.n == 0) return PACKSELL_OK;
     const void *perm = A.p.explicit_perm ? nullptr : A.perm;
     int pb = A.p.explicit_perm ? 0 : A.perm_bytes;
@@ -1412,6 +1418,7 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
 
 packsell_status spmv_dot_f64(const Matrix &A, const double *x, double *y, const double *b,
                              const Red &red, cudaStream_t s) {
+    if (is_w64(A.p.format)) return spmv_dot_w64(A, x, y, b, red, (unsigned)(device_sms() * 4), s);
     const cudaError_t e = launch_pdl(k_spmv_sell_dot64, (unsigned)(device_sms() * 4),
                                      TPB, s, (int)A.n, A.p.C, A.p.sigma, (const int64_t *)A.offset,
                                      (const double *)A.val, (const int32_t *)A.col,
@@ -1457,8 +1464,10 @@ __global__ void __launch_bounds__(TPB)
 }  // namespace
 
 packsell_status inv_diag_impl(const Matrix &A, double *out, cudaStream_t s) {
-    if (A.p.format != PACKSELL_FMT_SELL_F64 || A.n != A.m)
-        return fail(PACKSELL_ERR_INVALID_ARG, "packsell_inv_diag: needs a square SELL_F64 matrix");
+    if (!is_f64_op(A.p.format) || A.n != A.m)
+        return fail(PACKSELL_ERR_INVALID_ARG,
+                    "packsell_inv_diag: needs a square SELL_F64 or W64_E11MY matrix");
+    if (is_w64(A.p.format)) return inv_diag_w64(A, out, s);
     if (A.n == 0) return PACKSELL_OK;
     k_inv_diag<<<grid_for(A.n), TPB, 0, s>>>((int)A.n, A.p.C, A.p.sigma, A.offset,
                                              (const double *)A.val, A.col, A.perm, A.perm_bytes, out);

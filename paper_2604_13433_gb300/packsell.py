@@ -21,10 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpacksell.so")
 
 FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3, FMT_SELL_F16 = 1, 2, 3, 4, 5, 6
-FMT_FIXED = 7
+FMT_FIXED, FMT_W64_E11MY = 7, 8
 _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
             "sell_f64": FMT_SELL_F64, "w16_e4m3": FMT_W16_E4M3, "sell_f16": FMT_SELL_F16,
-            "fixed": FMT_FIXED}
+            "fixed": FMT_FIXED, "w64_e11my": FMT_W64_E11MY}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
           6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
@@ -384,7 +384,7 @@ def packsell_spmv(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = N
 
 def packsell_spmv_f64(A: PackSELLMatrix, x: torch.Tensor, y: torch.Tensor | None = None,
                       stream=None) -> torch.Tensor:
-    """y = A x (float64, SELL_F64 matrices)."""
+    """y = A x (float64; SELL_F64 and W64_E11MY matrices)."""
     if y is None:
         y = torch.empty(A.n, dtype=torch.float64, device=x.device)
     _check(lib().packsell_spmv_f64(A.handle, _dev(x, torch.float64, "x", A.m),
@@ -446,7 +446,7 @@ def packsell_spmv_backward(A: PackSELLMatrix, x: torch.Tensor, dy: torch.Tensor,
 
 def packsell_inv_diag(A: PackSELLMatrix, out: torch.Tensor | None = None,
                       stream=None) -> torch.Tensor:
-    """1 / a_ii of a square SELL_F64 matrix (Jacobi preconditioner)."""
+    """1 / a_ii of a square SELL_F64 or W64_E11MY matrix (Jacobi preconditioner)."""
     if out is None:
         out = torch.empty(A.n, dtype=torch.float64, device="cuda")
     _check(lib().packsell_inv_diag(A.handle, _dev(out, torch.float64, "out", A.n),
@@ -536,6 +536,8 @@ def packsell_arrays(A: PackSELLMatrix):
         out["perm"] = np.zeros(A.n, np.int32)
     if A.format == FMT_W16_E4M3:
         out["pack"] = np.frombuffer(blob, np.uint16, A.n_words, pos)
+    elif A.format == FMT_W64_E11MY:
+        out["pack"] = np.frombuffer(blob, np.uint64, A.n_words, pos)
     elif A.format in (FMT_FP16, FMT_E8MY, FMT_FIXED):
         out["pack"] = np.frombuffer(blob, np.uint32, A.n_words, pos)
     else:

@@ -93,7 +93,8 @@ def test_import_rejects_bad_blobs_on_the_host():
         (_blob(fmt=5, D=15), "bad header"),  # 16-bit words have D = 7
         (_blob(value_exp=3), "bad header"),  # an exponent only fixed point has
         (_blob(fmt=7, value_exp=5000), "bad header"),
-        (_blob(fmt=8), "bad header"),
+        (_blob(fmt=9), "bad header"),  # no such format
+        (_blob(fmt=8, D=32), "bad header"),  # 64-bit words have D in [1, 31]
         (_blob(sigma=300), "bad header"),  # perm_bytes 0 does not match sigma > 1
         (_blob()[:-4], "truncated"),
         (_blob(offsets=[32, 96, 160]), "offsets do not match"),

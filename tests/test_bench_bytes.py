@@ -43,6 +43,11 @@ def test_bytes_are_the_encoded_arrays(explicit, sigma):
     assert e16.pack.dtype == np.uint16
     assert b.spmv_bytes(_matrix(e16, explicit, 5), False) == \
         e16.pack.nbytes + e16.offset.astype(np.int64).nbytes + perm + vectors
+    # 64-bit words: FP64 x and y
+    e64 = O.encode64(csr, C=32, sigma=sigma, D=11)
+    assert e64.pack.dtype == np.uint64
+    assert b.spmv_bytes(_matrix(e64, explicit, 8), False) == \
+        e64.pack.nbytes + e64.offset.astype(np.int64).nbytes + perm + 2 * vectors
 
 
 def test_headline_bytes():

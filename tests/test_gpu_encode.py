@@ -147,7 +147,8 @@ def test_export_import_roundtrip_and_corruption():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 9), ("fixed", 11), ("w16_e4m3", 7),
-                                   ("sell_f16", 15), ("sell_f32", 15), ("sell_f64", 15)])
+                                   ("sell_f16", 15), ("sell_f32", 15), ("sell_f64", 15),
+                                   ("w64_e11my", 11)])
 def test_export_import_roundtrip_every_format(fmt, D):
     """Every storage format survives export and import: the same arrays,
     the same fixed-point exponent and the same product bits."""
@@ -161,7 +162,10 @@ def test_export_import_roundtrip_every_format(fmt, D):
     assert a.keys() == b.keys()
     for k in a:
         assert np.array_equal(a[k], b[k]), k
-    if fmt != "sell_f64":
+    if fmt in ("sell_f64", "w64_e11my"):
+        x = dev(I.uniform(900, seed=2).astype(np.float64))
+        assert torch.equal(ps.packsell_spmv_f64(A, x), ps.packsell_spmv_f64(B, x))
+    else:
         x = dev(I.uniform(900, seed=2))
         assert torch.equal(ps.packsell_spmv(A, x), ps.packsell_spmv(B, x))
 

@@ -31,6 +31,12 @@ def test_fixed_encoding_and_spmv_match_oracle(case, D, C, sigma):
     twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), x)
     assert np.array_equal(enc.deq.astype(np.float32).astype(np.float64), enc.deq)  # exact in FP32
     assert np.array_equal(y.view(np.uint32), twin.view(np.uint32))
+    if C == 32:  # the row-prefetch kernel with programmatic launch: the same chain
+        ps.packsell_set_spmv_variant(A, 13)
+        y13 = ps.packsell_spmv(A, dev(x)).cpu().numpy()
+        assert np.array_equal(y13.view(np.uint32), twin.view(np.uint32))
+        ps.packsell_set_spmv_variant(A, 0)
+        assert set(ps.packsell_tune_spmv(A, dev(x), reps=2)) == {1, 13}
 
 
 def test_fixed_integer_matrix_is_exact():
