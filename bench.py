@@ -472,7 +472,7 @@ def batch_section(ps, torch, dev, K, W, peak):
         mats = [ps.packsell_encode_csr(c, fmt="fp16", D=15, C=C, sigma=sigma) for c in batch]
         B = ps.packsell_batch_create(mats, xs, ys)
         ms, _ = time_launches(torch, B.spmv, K, W)
-        out[key] = _rate(B.bytes, ms, peak, "k_spmv_batched" if C == 32 else "k_split_multi",
+        out[key] = _rate(B.bytes, ms, peak, "k_spmv_batched" if C == 32 else "k_spmv_split_batch",
                          C=C, sigma=sigma, words=B.words, items=B.items)
         del B
         if C == 1:
@@ -481,8 +481,8 @@ def batch_section(ps, torch, dev, K, W, peak):
                 Ys = [torch.empty(c.n, k, device=dev) for c in batch]
                 Bm = ps.packsell_batch_create_spmm(mats, Xs, Ys)
                 ms, _ = time_launches(torch, Bm.spmm, KS, 3)
-                out[f"csr_order_spmm_k{k}"] = _rate(Bm.bytes, ms, peak, "k_split_multi", k=k,
-                                                    items=Bm.items)
+                kern = "k_spmv_split_batch" if k == 1 else "k_split_multi"
+                out[f"csr_order_spmm_k{k}"] = _rate(Bm.bytes, ms, peak, kern, k=k, items=Bm.items)
                 del Bm, Xs, Ys
         del mats
     return out

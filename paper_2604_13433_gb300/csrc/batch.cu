@@ -5,9 +5,11 @@
 //    counts; warps take items round-robin and lane l of a warp computes row l
 //    of each slice of its item (thread-per-row, stored order, fused
 //    multiply-adds: the same bits as packsell_spmv on each matrix alone);
-//  * matrices with C = 1 (CSR order): the split-row items of multi.cu (tiles
-//    of rows and single long rows, long rows first), one persistent launch
-//    of the split-row kernel for all of them, with k right-hand sides.
+//  * matrices with C = 1 (CSR order): split-row items (tiles of rows and
+//    single long rows, long rows first) in one persistent launch for all of
+//    them: a batched SpMV takes the items and kernel of variant 14 (each y
+//    the bits of variant 14 on its matrix alone), a batched SpMM those of
+//    multi.cu with k right-hand sides.
 #include <cuda_fp16.h>
 #include <string.h>
 
@@ -49,6 +51,8 @@ struct Batch {
     SplitMat *d_smats = nullptr;
     MultiItem *d_mitems = nullptr;
     int n_mitems = 0;
+    bool split1 = false;  // the items are variant 14's (one right-hand side)
+    bool sorted = false;  // a CSR-order matrix has sigma > 1
 };
 
 namespace {
@@ -219,7 +223,12 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
             return fail(PACKSELL_ERR_CUDA, "packsell_batch_create: reading offsets");
         }
         if (m->p.C == 1) {
-            multi_items_append(offs.data(), m->n, i, mitems);
+            B->sorted = B->sorted || m->p.sigma > 1;
+            const packsell_status st = split_items_append(offs.data(), m->n, i, mitems);
+            if (st != PACKSELL_OK) {
+                batch_free(B);
+                return st;
+            }
             continue;
         }
         int k0 = 0;
@@ -246,6 +255,7 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
         batch_free(B);
         return cuda_fail(e, "packsell_batch_create: plan copy");
     }
+    B->split1 = true;
     const packsell_status st = upload_split(B, smats, mitems, s);
     if (st != PACKSELL_OK) {
         batch_free(B);
@@ -267,7 +277,10 @@ packsell_status batch_create_mm(int count, const Matrix *const *A, int k, const 
     std::vector<SplitMat> smats(count);
     std::vector<MultiItem> mitems;
     std::vector<int64_t> offs;
+    std::vector<std::vector<int64_t>> offs_all;  // row offsets of the matrices with rows
     bool vec = k % 4 == 0;
+    // one right-hand side in contiguous vectors: the SpMV items and kernel
+    bool split1 = k == 1;
     for (int i = 0; i < count; ++i) {
         const Matrix *m = A[i];
         const int64_t lx = ldx ? ldx[i] : k, ly = ldy ? ldy[i] : k;
@@ -285,6 +298,8 @@ packsell_status batch_create_mm(int count, const Matrix *const *A, int k, const 
         }
         vec = vec && lx % 4 == 0 && ly % 4 == 0 && ((uintptr_t)X[i] & 15) == 0 &&
               ((uintptr_t)Y[i] & 15) == 0;
+        split1 = split1 && lx == 1 && ly == 1;
+        B->sorted = B->sorted || m->p.sigma > 1;
         smats[i] = split_mat(*m, X[i], lx, Y[i], ly, k);
         B->words += m->n_words;
         B->rows += m->n;
@@ -297,9 +312,23 @@ packsell_status batch_create_mm(int count, const Matrix *const *A, int k, const 
             batch_free(B);
             return fail(PACKSELL_ERR_CUDA, "packsell_batch_create_spmm: reading offsets");
         }
-        multi_items_append(offs.data(), m->n, i, mitems);
+        offs_all.push_back(offs);
     }
     B->vec = vec;
+    B->split1 = split1;
+    for (int i = 0, j = 0; i < count; ++i) {
+        if (A[i]->n == 0) continue;
+        const std::vector<int64_t> &o = offs_all[j++];
+        if (split1) {
+            const packsell_status st = split_items_append(o.data(), A[i]->n, i, mitems);
+            if (st != PACKSELL_OK) {
+                batch_free(B);
+                return st;
+            }
+        } else {
+            multi_items_append(o.data(), A[i]->n, i, mitems);
+        }
+    }
     const packsell_status st = upload_split(B, smats, mitems, s);
     if (st != PACKSELL_OK) {
         batch_free(B);
@@ -323,12 +352,13 @@ packsell_status batch_spmv(const Batch &B, cudaStream_t s) {
         k_spmv_batched<<<B.blocks, BTPB, 0, s>>>(B.d_mats, B.d_items, B.nitems);
         PS_LAUNCH_CHECK("packsell_batch_spmv");
     }
-    return launch_multi(SplitMat{}, B.d_smats, B.d_mitems, B.n_mitems, 1, false, s);
+    return launch_split_batch(B.d_smats, B.d_mitems, B.n_mitems, B.sorted, s);
 }
 
 packsell_status batch_spmm(const Batch &B, cudaStream_t s) {
     if (B.d_mats)
         return fail(PACKSELL_ERR_INVALID_ARG, "packsell_batch_spmm: the plan is a batched SpMV plan");
+    if (B.split1) return launch_split_batch(B.d_smats, B.d_mitems, B.n_mitems, B.sorted, s);
     return launch_multi(SplitMat{}, B.d_smats, B.d_mitems, B.n_mitems, B.k, B.vec, s);
 }
 

@@ -150,6 +150,10 @@ packsell_status launch_multi(const SplitMat &single, const SplitMat *mats, const
 // split.cu
 packsell_status plan_split(Matrix &A, cudaStream_t s);
 void split_plan_free(Matrix &A);
+packsell_status split_items_append(const int64_t *off, int64_t n, int mat,
+                                   std::vector<MultiItem> &items);
+packsell_status launch_split_batch(const SplitMat *mats, const MultiItem *items, int nitems,
+                                   bool sorted, cudaStream_t s);
 packsell_status launch_split(const Matrix &A, const void *perm, int pb, const float *x, float *y,
                              cudaStream_t s);
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ int split_left(int row, int sigma, int sig_shift, int
 template <bool PERM>
 __device__ __forceinline__ int split_out(int row, int sigma, int sig_shift, const void *perm,
                                          int perm_bytes) {
-    if (!PERM) return row;
+    if (!PERM || perm_bytes == 0) return row;
     const int blk = sig_shift >= 0 ? (row >> sig_shift) << sig_shift : (row / sigma) * sigma;
     return blk + (perm_bytes == 1 ? (int)((const uint8_t *)perm)[row]
                                   : (int)((const uint16_t *)perm)[row]);
@@ -76,9 +76,12 @@ __device__ __forceinline__ uint4 ld_words4(const uint32_t *p) {
     return __ldcs(reinterpret_cast<const uint4 *>(p));
 }
 
+// FMT 0: the format is chosen at run time (a batch): FP16 when dc.vshift is 1
 template <int FMT>
 __device__ __forceinline__ float split_value(uint32_t wd, Decode dc) {
+    const bool h = FMT == PACKSELL_FMT_FP16 || (FMT == 0 && dc.vshift != 0);
     if (FMT == PACKSELL_FMT_FP16) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
+    if (FMT == 0 && h) return __high2float(*reinterpret_cast<const __half2 *>(&wd));
     return __uint_as_float(wd & dc.vmask);
 }
 
@@ -105,8 +108,9 @@ __device__ __forceinline__ void split_load(const uint32_t *__restrict__ pack, lo
     wv[1] = p + 4 < lim ? ld_words4(pack + first + p + 4) : make_uint4(0, 0, 0, 0);
 }
 
+template <typename Item>
 __device__ __forceinline__ void split_load_item(const uint32_t *__restrict__ pack,
-                                                const SplitItem &d, int lane, uint4 (&wv)[2]) {
+                                                const Item &d, int lane, uint4 (&wv)[2]) {
     const long long a0 = d.base & ~3ll;
     const int nwd = d.meta < 0 ? -d.meta : (d.meta & 0xFFFF);
     split_load(pack, a0, (int)(d.base - a0) + nwd, lane, wv);
@@ -282,7 +286,8 @@ __device__ __forceinline__ void cp_async_wait_older() {
 // Start copying the low 32 bits of a tile's nrows + 1 row offsets (int64,
 // little-endian) into soff; every lane commits one group per item (empty for
 // a long row) so the group counts stay equal.
-__device__ __forceinline__ void split_prefetch_offsets(const SplitItem &d, bool live,
+template <typename Item>
+__device__ __forceinline__ void split_prefetch_offsets(const Item &d, bool live,
                                                        const int64_t *__restrict__ offset,
                                                        uint32_t *soff, int lane) {
     if (live && d.meta >= 0) {
@@ -343,6 +348,80 @@ __global__ void __launch_bounds__(SW * 32, 4)
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// The same kernel over many matrices (a batched SpMV of CSR-order matrices):
+// each item names its matrix, whose descriptor gives the words, offsets,
+// perm, vectors, left offset and value format. A matrix's items are cut by
+// the same rule as its own plan's, so each y equals variant 14's on that
+// matrix alone, bit for bit. SORTED = false: every matrix has sigma = 1 (no
+// sort, no perm); SORTED = true takes any sigma. The per-item matrix
+// parameters live in registers (the single-matrix kernel has them as launch
+// arguments), so the kernel runs three blocks per SM: at four it spills.
+template <bool SORTED>
+__global__ void __launch_bounds__(SW * 32, 3)
+    k_spmv_split_batch(const SplitMat *__restrict__ mats, const MultiItem *__restrict__ items,
+                       int nitems) {
+    __shared__ __align__(16) uint32_t s_lft[SW][ST];
+    __shared__ __align__(16) int s_io[SW][ST];
+    __shared__ __align__(16) uint32_t s_off[SW][2][SR_MAX + 4];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int it = gw;
+    if (it >= nitems) return;
+    MultiItem d = items[it], dn{0, 0, 0, 0};
+    if (it + nwarps < nitems) dn = items[it + nwarps];
+    uint4 wv[2];
+    split_load_item(mats[d.mat].pack, d, lane, wv);
+    split_prefetch_offsets(d, true, mats[d.mat].offset, s_off[wl][0], lane);
+    int buf = 0;
+    for (; it < nitems; it += nwarps) {
+        const bool has_next = it + nwarps < nitems;
+        MultiItem dnn{0, 0, 0, 0};
+        if (it + 2 * nwarps < nitems) dnn = items[it + 2 * nwarps];
+        uint4 wn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        const SplitMat *Mn = has_next ? &mats[dn.mat] : nullptr;
+        if (has_next) split_load_item(Mn->pack, dn, lane, wn);
+        split_prefetch_offsets(dn, has_next, has_next ? Mn->offset : nullptr, s_off[wl][buf ^ 1],
+                               lane);
+        cp_async_wait_older();
+        __syncwarp();
+        const SplitMat &M = mats[d.mat];
+        const Decode dc{M.dmask, M.vmask, M.fmt == PACKSELL_FMT_FP16 ? 1 : 0, 1.f};
+        const int sg = SORTED ? M.sigma : 1, sh = SORTED ? M.sig_shift : 0;
+        if (d.meta < 0)
+            split_long_row<0, SORTED>(d.r0, d.base, -d.meta, sg, sh, M.kl, M.pack, M.perm,
+                                      M.perm_bytes, dc, M.X, M.Y, lane, wv);
+        else
+            split_tile<0, SORTED>(d.r0, d.meta >> 16, d.base, d.meta & 0xFFFF, sg, sh, M.kl,
+                                  M.perm, M.perm_bytes, dc, M.X, M.Y, lane, wv, s_lft[wl],
+                                  s_io[wl], s_off[wl][buf]);
+        __syncwarp();
+        d = dn;
+        dn = dnn;
+        wv[0] = wn[0];
+        wv[1] = wn[1];
+        buf ^= 1;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <bool SORTED>
+int split_batch_blocks() {
+    static std::atomic<int> cached{0};
+    int blocks = cached.load(std::memory_order_relaxed);
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_spmv_split_batch<SORTED>, SW * 32, 0) !=
+                cudaSuccess)
+            return 0;
+        blocks = sms * std::max(per, 1);
+        cached.store(blocks, std::memory_order_relaxed);
+    }
+    return blocks;
+}
+
 template <int FMT, bool PERM>
 int split_blocks() {
     // persistent grid: every block resident at once (cached per process)
@@ -374,6 +453,37 @@ void split_plan_free(Matrix &A) {
 // the group holds at most SCT words and SR_MAX rows; a row of more words is
 // an item of its own. Long rows come first, longest first: they are the
 // longest serial paths of the launch and start before the short tiles.
+// Cut rows [0, n) with row offsets `off` into items: consecutive rows of at
+// most SCT words grouped greedily while the group holds at most SCT words and
+// SR_MAX rows; a row of more words is an item of its own. push(base, r0,
+// meta) receives each item in row order.
+template <typename Push>
+static packsell_status split_cut(const int64_t *off, int n, Push push) {
+    auto tile = [&](int a, int b) {
+        push((long long)off[a], a, ((b - a) << 16) | (int)(off[b] - off[a]));
+    };
+    int r0 = 0;
+    for (int r = 0; r < n; ++r) {
+        const int64_t w = off[r + 1] - off[r];
+        if (w > SCT) {
+            if (r > r0) tile(r0, r);
+            if (w >= INT32_MAX) return fail(PACKSELL_ERR_RANGE, "split-row plan: row too long");
+            push((long long)off[r], r, -(int)w);
+            r0 = r + 1;
+            continue;
+        }
+        if (off[r + 1] - off[r0] > SCT || r + 1 - r0 > SR_MAX) {
+            tile(r0, r);
+            r0 = r;
+        }
+    }
+    if (n > r0) tile(r0, n);
+    return PACKSELL_OK;
+}
+
+// Items of variant 14 (C = 1 PackSELL matrices), built on the host from the
+// row offsets by split_cut. Long rows come first, longest first: they are the
+// longest serial paths of the launch and start before the short tiles.
 packsell_status plan_split(Matrix &A, cudaStream_t s) {
     split_plan_free(A);
     if (!is_packed(A.p.format) || A.p.C != 1 || A.n == 0) return PACKSELL_OK;
@@ -383,25 +493,10 @@ packsell_status plan_split(Matrix &A, cudaStream_t s) {
     PS_CUDA(cudaStreamSynchronize(s));
     std::vector<SplitItem> items;
     items.reserve((size_t)(A.n_words / SCT + A.n / SR_MAX + 16));
-    auto tile = [&](int a, int b) {
-        items.push_back(SplitItem{(long long)off[a], a, ((b - a) << 16) | (int)(off[b] - off[a])});
-    };
-    int r0 = 0;
-    for (int r = 0; r < (int)A.n; ++r) {
-        const int64_t w = off[r + 1] - off[r];
-        if (w > SCT) {
-            if (r > r0) tile(r0, r);
-            if (w >= INT32_MAX) return fail(PACKSELL_ERR_RANGE, "plan_split: row too long");
-            items.push_back(SplitItem{(long long)off[r], r, -(int)w});
-            r0 = r + 1;
-            continue;
-        }
-        if (off[r + 1] - off[r0] > SCT || r + 1 - r0 > SR_MAX) {
-            tile(r0, r);
-            r0 = r;
-        }
-    }
-    if ((int)A.n > r0) tile(r0, (int)A.n);
+    const packsell_status st = split_cut(off.data(), (int)A.n, [&](long long b, int r0, int meta) {
+        items.push_back(SplitItem{b, r0, meta});
+    });
+    if (st != PACKSELL_OK) return st;
     auto is_long = [](const SplitItem &a) { return a.meta < 0; };
     std::stable_partition(items.begin(), items.end(), is_long);
     const size_t nlong = (size_t)std::count_if(items.begin(), items.end(), is_long);
@@ -414,6 +509,27 @@ packsell_status plan_split(Matrix &A, cudaStream_t s) {
                             cudaMemcpyHostToDevice, s));
     PS_CUDA(cudaStreamSynchronize(s));
     A.split_nitems = (int)items.size();
+    return PACKSELL_OK;
+}
+
+// A batch's items of matrix `mat` (n rows, row offsets `off`), by the rule of
+// the matrix's own plan; the caller orders the whole list (multi_items_order).
+packsell_status split_items_append(const int64_t *off, int64_t n, int mat,
+                                   std::vector<MultiItem> &items) {
+    return split_cut(off, (int)n, [&](long long b, int r0, int meta) {
+        items.push_back(MultiItem{b, r0, meta, mat});
+    });
+}
+
+packsell_status launch_split_batch(const SplitMat *mats, const MultiItem *items, int nitems,
+                                   bool sorted, cudaStream_t s) {
+    if (nitems <= 0) return PACKSELL_OK;
+    int blocks = sorted ? split_batch_blocks<true>() : split_batch_blocks<false>();
+    if (!blocks) return fail(PACKSELL_ERR_CUDA, "packsell_batch_spmv: device query failed");
+    blocks = std::min(blocks, (nitems + SW - 1) / SW);
+    if (sorted) k_spmv_split_batch<true><<<blocks, SW * 32, 0, s>>>(mats, items, nitems);
+    else k_spmv_split_batch<false><<<blocks, SW * 32, 0, s>>>(mats, items, nitems);
+    PS_LAUNCH_CHECK("packsell_batch_spmv (split rows)");
     return PACKSELL_OK;
 }
 

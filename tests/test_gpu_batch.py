@@ -66,8 +66,9 @@ def _split_bound_check(y, csr, deq, X, words):
 
 def test_batch_mixes_slice_heights():
     """C = 32 and C = 1 (CSR order) matrices in one plan: the C = 32 ones give
-    packsell_spmv's bits, the C = 1 ones (split rows) stay within gamma_w of
-    the oracle; empty rows, sigma sorting and both orders among them."""
+    packsell_spmv's bits, the C = 1 ones (split rows) the bits of variant 14
+    on the matrix alone, within gamma_w of the oracle; empty rows, sigma
+    sorting and both orders among them."""
     need_gpu()
     ps = P()
     rng = np.random.default_rng(3)
@@ -94,6 +95,8 @@ def test_batch_mixes_slice_heights():
             ref = ps.packsell_spmv(A, x)
             assert torch.equal(y.view(torch.int32), ref.view(torch.int32))
             continue
+        ps.packsell_set_spmv_variant(A, ps.SPMV_SPLIT)
+        assert torch.equal(y.view(torch.int32), ps.packsell_spmv(A, x).view(torch.int32))
         if A.explicit_perm:
             yo = np.empty_like(yv)
             yo[O.storage_rows(enc)] = yv
@@ -118,8 +121,11 @@ def test_batched_spmm_csr_order(k):
     B = ps.packsell_batch_create_spmm(mats, Xs, Ys)
     B.spmm()
     torch.cuda.synchronize()
-    for c, X, Y, enc in zip(batch, Xs, Ys, encs):
+    for A, c, X, Y, enc in zip(mats, batch, Xs, Ys, encs):
         _split_bound_check(Y.cpu().numpy(), c, enc.deq, X.cpu().numpy(), enc.words)
+        if k == 1:  # the SpMV's items and kernel: variant 14's bits
+            ref = ps.packsell_spmv(A, X[:, 0].contiguous())
+            assert torch.equal(Y[:, 0].contiguous().view(torch.int32), ref.view(torch.int32))
     with pytest.raises(ps.PackSELLError):  # an SpMM plan does not run as a batched SpMV
         ps._check(ps.lib().packsell_batch_spmv(B._h, None))
 
