@@ -465,6 +465,16 @@ packsell_status packsell_set_wait_limit(int64_t polls);
  * its work), else PACKSELL_OK. */
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
+/* Housekeeping (no counterpart in the paper): decode the whole matrix on the
+ * device and check it against the record kept at encode time - every slice
+ * offset C-aligned and increasing, every perm entry inside its sigma block,
+ * every column (Eq. 2 from Eq. 4's left offset) below m, and the words with
+ * a value (or the FP16 SELL slots that are not padding) counting nnz.
+ * packsell_import runs the same check on every blob. Reads the matrix only;
+ * synchronises `stream`. Returns CORRUPT (with the first bad index in the
+ * message) or OK. */
+packsell_status packsell_validate(const packsell_matrix *A, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Batched SpMV: many matrices, one persistent launch                       */
 /* ---------------------------------------------------------------------- */

@@ -303,7 +303,7 @@ packsell_status packsell_import(const void *h_blob, size_t bytes, void *stream,
                             cudaMemcpyHostToDevice, s) != cudaSuccess)
             return bail(fail(PACKSELL_ERR_CUDA, "packsell_import: copy"));
     }
-    packsell_status st = validate_impl(*A, s);
+    packsell_status st = validate_impl(*A, s, "packsell_import");
     if (st != PACKSELL_OK) return bail(st);
     st = plan_spmv(*A, s);
     if (st != PACKSELL_OK) return bail(st);
@@ -505,6 +505,12 @@ packsell_status packsell_set_wait_limit(int64_t polls) {
     set_data_wait_limit(polls < 0 ? kWaitLimit
                                   : (uint32_t)std::min<int64_t>(polls, (int64_t)UINT32_MAX));
     return PACKSELL_OK;
+}
+
+packsell_status packsell_validate(const packsell_matrix *A, void *stream) {
+    clear_error();
+    if (!A) return fail(PACKSELL_ERR_INVALID_ARG, "packsell_validate: NULL matrix");
+    return validate_impl(*M(A), as_stream(stream), "packsell_validate");
 }
 
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream) {

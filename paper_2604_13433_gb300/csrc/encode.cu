@@ -927,7 +927,7 @@ __global__ void k_validate(int n, int64_t m, int C, int sigma, long long k_left,
 }
 }  // namespace
 
-packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
+packsell_status validate_impl(const Matrix &A, cudaStream_t s, const char *what) {
     Temps T(s);
     DevStatus *st = nullptr;
     unsigned long long *cnt = nullptr;
@@ -967,10 +967,11 @@ packsell_status validate_impl(const Matrix &A, cudaStream_t s) {
     PS_CUDA(cudaMemcpyAsync(&hc, cnt, 8, cudaMemcpyDeviceToHost, s));
     PS_CUDA(cudaStreamSynchronize(s));
     if (hst.code)
-        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: bad word, column or perm at index " +
+        return fail(PACKSELL_ERR_CORRUPT, std::string(what) +
+                                              ": bad word, column or perm at index " +
                                               std::to_string(hst.index));
     if (counted && (int64_t)hc != A.nnz)
-        return fail(PACKSELL_ERR_CORRUPT, "packsell_import: value words do not match nnz");
+        return fail(PACKSELL_ERR_CORRUPT, std::string(what) + ": value words do not match nnz");
     return PACKSELL_OK;
 }
 

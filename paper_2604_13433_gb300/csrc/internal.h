@@ -91,7 +91,7 @@ int64_t matrix_bytes(const Matrix &A);
 packsell_status encode_impl(const packsell_params &p, int64_t n, int64_t m, int64_t nnz,
                             const int64_t *rowptr, const int32_t *col, const void *val,
                             int val_is_f64, cudaStream_t s, Matrix **out);
-packsell_status validate_impl(const Matrix &A, cudaStream_t s);
+packsell_status validate_impl(const Matrix &A, cudaStream_t s, const char *what);
 void destroy_matrix(Matrix *A);
 packsell_status scan_i64(const int64_t *in, int64_t *out, int64_t S, cudaStream_t s);
 packsell_status quantize_impl(int fmt, int D, int64_t n, const void *val, int is64, uint32_t *field,

@@ -107,6 +107,7 @@ SIGNATURES = {
     "packsell_pattern_outer": (ctypes.c_int, [_P, _F32, _P, _P, _P, _P]),
     "packsell_set_spmv_variant": (ctypes.c_int, [_P, _I32]),
     "packsell_check_status": (ctypes.c_int, [_P, _P]),
+    "packsell_validate": (ctypes.c_int, [_P, _P]),
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "packsell_quantize": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P]),
     "packsell_set_wait_limit": (ctypes.c_int, [_I64]),
@@ -503,6 +504,11 @@ def packsell_pattern_outer_f64(A: PackSELLMatrix, alpha: float, u: torch.Tensor,
                                             _dev(out, torch.float64, "out", A.nnz),
                                             _stream(stream)))
     return out
+
+
+def packsell_validate(A: PackSELLMatrix, stream=None) -> None:
+    """Decode the whole matrix on the device and check it (raises CORRUPT)."""
+    _check(lib().packsell_validate(A.handle, _stream(stream)))
 
 
 def packsell_export(A: PackSELLMatrix, stream=None) -> bytes:

@@ -197,3 +197,42 @@ def test_import_rejects_sell_f16_slot_after_padding():
         with pytest.raises(ps.PackSELLError) as e:
             ps.packsell_import(blob[:cols_at] + bad.tobytes())
         assert e.value.code == 9
+
+
+def _device_words(ptr, count):
+    """A torch view (int32) of a matrix's device word array."""
+    class _View:
+        pass
+    v = _View()
+    v.__cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, False),
+                                  "version": 3}
+    return torch.as_tensor(v, device="cuda")
+
+
+@pytest.mark.gpu
+def test_validate_finds_corrupted_words():
+    """packsell_validate decodes the matrix on the device: a word whose delta
+    runs past the last column, and a padding word turned into a value, are
+    CORRUPT; the restored matrix validates again. (No product runs on the
+    corrupted matrix.)"""
+    need_gpu()
+    ps = P()
+    csr = I.random_csr(500, 600, 0.02, seed=5, long_gaps=True)
+    A = encode_gpu(csr, fmt="e8my", D=4, C=32, sigma=64)
+    ps.packsell_validate(A)
+    words = _device_words(A.info.pack, A.n_words)
+    arr = ps.packsell_arrays(A)["pack"]
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), arr)
+    first_value = int(np.nonzero(arr & 1)[0][0])
+    first_pad = int(np.nonzero(arr == 0)[0][0])
+    for at, bad, why in ((first_value, 0x7FFFFFFE, "bad word"),  # a dummy of 2^30 - 1
+                         (first_pad, 0x3F800001, "do not match nnz")):  # 1.0, delta 0
+        keep = int(words[at].item())
+        words[at] = bad
+        torch.cuda.synchronize()
+        with pytest.raises(ps.PackSELLError) as e:
+            ps.packsell_validate(A)
+        assert e.value.code == 9 and why in str(e.value), str(e.value)
+        words[at] = keep
+        torch.cuda.synchronize()
+        ps.packsell_validate(A)
