@@ -63,8 +63,10 @@ typedef enum packsell_status {
     PACKSELL_ERR_BREAKDOWN = 7,     /* solver: p^T A p <= 0 or a non-finite residual */
     PACKSELL_ERR_NO_MEMORY = 8,     /* device allocation failed */
     PACKSELL_ERR_CORRUPT = 9,       /* imported data fails validation */
-    PACKSELL_ERR_TIMEOUT = 10       /* a kernel's bounded wait ran out (see
+    PACKSELL_ERR_TIMEOUT = 10,      /* a kernel's bounded wait ran out (see
                                        packsell_check_status) */
+    PACKSELL_ERR_CHECK = 11         /* bounds-check build only: a decoded index was
+                                       out of range (see packsell_check_status) */
 } packsell_status;
 
 /* Value formats.
@@ -181,6 +183,16 @@ typedef struct packsell_info {
 } packsell_info;
 
 const char *packsell_version(void);
+
+/* 1 when the library is the bounds-check build (compiled with
+ * -DPACKSELL_CHECKS: libpacksell_checks.so), 0 otherwise. In that build
+ * every gather of x (or a row of X) at a column decoded from the words, and
+ * every write the decoded words steer (the transpose's scatter, the pattern
+ * product's output), first checks its index against the array's length;
+ * an index out of range skips the access and is counted, and
+ * packsell_check_status reports the count. Plain SELL columns are stored,
+ * not decoded, and are checked at encode and import instead. */
+int32_t packsell_checks_build(void);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char *packsell_last_error(void);
@@ -462,7 +474,11 @@ packsell_status packsell_set_wait_limit(int64_t polls);
  * device status word (synchronises `stream`).
  * Returns PACKSELL_ERR_TIMEOUT if a kernel's bounded wait on a shared-memory
  * stage ran out since the last check (the kernel then skipped the rest of
- * its work), else PACKSELL_OK. */
+ * its work). In the bounds-check build (packsell_checks_build) it also reads
+ * and clears the out-of-range counters of the current device - kept for the
+ * whole library, not per matrix - and returns PACKSELL_ERR_CHECK, with the
+ * count and the first index in the message, if any access was skipped since
+ * the last check. Else PACKSELL_OK. */
 packsell_status packsell_check_status(const packsell_matrix *A, void *stream);
 
 /* Housekeeping (no counterpart in the paper): decode the whole matrix on the

@@ -36,6 +36,34 @@ int64_t matrix_bytes(const Matrix &A) {
 
 void destroy_matrix(Matrix *A);
 
+// Readers of the bounds-check counters, one per translation unit (registered
+// while the library loads; empty in the regular build).
+static std::vector<ChecksReader> &checks_readers() {
+    static std::vector<ChecksReader> r;
+    return r;
+}
+
+void register_checks_reader(ChecksReader r) { checks_readers().push_back(r); }
+
+// Sum and clear every unit's counters: PACKSELL_ERR_CHECK if any access was
+// skipped, else OK.
+static packsell_status read_checks() {
+    unsigned long long total = 0;
+    long long first = -1;
+    for (ChecksReader r : checks_readers()) {
+        unsigned long long c = 0;
+        long long f = 0;
+        PS_CUDA(r(&c, &f));
+        if (c && first < 0) first = f;
+        total += c;
+    }
+    if (total)
+        return fail(PACKSELL_ERR_CHECK, "packsell_check_status: " + std::to_string(total) +
+                                            " out-of-range accesses skipped (first index " +
+                                            std::to_string(first) + ")");
+    return PACKSELL_OK;
+}
+
 // The SpMV of a matrix: 16-bit words have their own kernel.
 packsell_status spmv_route(const Matrix &A, const float *x, float *y, cudaStream_t s) {
     return is_w16(A.p.format) ? spmv_w16_impl(A, x, y, s) : spmv_impl(A, x, y, s);
@@ -100,6 +128,14 @@ void packsell_params_default(packsell_params *p) {
 }
 
 const char *packsell_version(void) { return "packsell-gb300 0.1 (sm_103a)"; }
+
+int32_t packsell_checks_build(void) {
+#ifdef PACKSELL_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 const char *packsell_last_error(void) { return g_last_error.c_str(); }
 
@@ -526,7 +562,7 @@ packsell_status packsell_check_status(const packsell_matrix *A, void *stream) {
     if (h.code)
         return fail((packsell_status)h.code,
                     "packsell_check_status: a bounded wait ran out in warp " + std::to_string(h.index));
-    return PACKSELL_OK;
+    return read_checks();
 }
 
 packsell_status packsell_spmv(const packsell_matrix *A, const float *x, float *y, void *stream) {

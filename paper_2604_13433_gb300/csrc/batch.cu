@@ -29,7 +29,7 @@ struct BatchMat {
     const float *x;
     float *y;
     long long k_left;
-    int n, sigma, sig_shift, perm_bytes, fmt;
+    int n, m, sigma, sig_shift, perm_bytes, fmt;
     uint32_t dmask, vmask;
 };
 
@@ -77,7 +77,7 @@ __device__ __forceinline__ float row_dot(const BatchMat &M, int row, int64_t s, 
         for (int u = 0; u < BPF; ++u) {
             f[u] = (wd[u] & 1u) != 0u;
             c += (int)((wd[u] >> 1) & (f[u] ? M.dmask : 0x7fffffffu));
-            if (f[u]) xv[u] = __ldg(M.x + c);
+            if (f[u]) xv[u] = PS_IN_RANGE(c, M.m) ? __ldg(M.x + c) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < BPF; ++u) {
@@ -204,6 +204,7 @@ packsell_status batch_create(int count, const Matrix *const *A, const float *con
         d.y = y[i];
         d.k_left = m->p.k_left;
         d.n = (int)m->n;
+        d.m = (int)m->m;
         d.sigma = sg;
         d.sig_shift = (sg & (sg - 1)) == 0 ? __builtin_ctz((unsigned)sg) : -1;
         d.fmt = m->p.format;

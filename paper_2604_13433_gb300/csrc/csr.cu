@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(CW * 32, 4)
                 }
                 float xv[CT / 32];
 #pragma unroll
-                for (int u = 0; u < CT / 32; ++u) xv[u] = (wd[u] & 1u) ? __ldg(x + c[u]) : 0.f;
+                for (int u = 0; u < CT / 32; ++u)
+                    xv[u] = ((wd[u] & 1u) && PS_IN_RANGE(c[u], dc.xlen)) ? __ldg(x + c[u]) : 0.f;
                 // a word without a value (dummy, or past the row's end) is
                 // stored as the pair (-0, 0): fmaf(-0, 0, t) == t for every t
                 // (including -0, infinities and NaN), so the chain below

@@ -16,6 +16,46 @@ __device__ __forceinline__ void dev_fail(DevStatus *st, int code, long long inde
     if (atomicCAS(&st->code, 0, code) == 0) st->index = index;
 }
 
+// ---- the bounds-check build (compiled with -DPACKSELL_CHECKS) ----
+// Every x (or X row) gather at a column decoded from the words, and every
+// write the decoded words steer (the transpose's scatter, the pattern
+// product's output), first checks its index against the array's length; an
+// index out of range skips the access and is counted, with the first such
+// index kept. Each translation unit has its own counters (a device variable
+// per unit, since the library is not built for relocatable device code);
+// packsell_check_status sums them through the readers that the units
+// register at load time. The regular build compiles every check to `true`.
+#ifdef PACKSELL_CHECKS
+namespace {
+__device__ unsigned long long g_checks[2];  // out-of-range accesses; first index
+
+__device__ __forceinline__ bool check_in_range(long long i, long long len) {
+    if (i >= 0 && i < len) return true;
+    if (atomicAdd(&g_checks[0], 1ull) == 0ull) g_checks[1] = (unsigned long long)i;
+    return false;
+}
+
+// read and clear this unit's counters (host; the current device)
+cudaError_t read_checks_here(unsigned long long *count, long long *first) {
+    unsigned long long h[2] = {0ull, 0ull};
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_checks, sizeof h);
+    if (e != cudaSuccess) return e;
+    *count = h[0];
+    *first = (long long)h[1];
+    const unsigned long long z[2] = {0ull, 0ull};
+    return cudaMemcpyToSymbol(g_checks, z, sizeof z);
+}
+
+struct ChecksRegistrar {
+    ChecksRegistrar() { register_checks_reader(&read_checks_here); }
+};
+ChecksRegistrar g_checks_registrar;
+}  // namespace
+#define PS_IN_RANGE(i, len) ::packsell::check_in_range((long long)(i), (long long)(len))
+#else
+#define PS_IN_RANGE(i, len) true
+#endif
+
 // Left offset of Eq. 4: the same for every row of a block of sigma rows, so it
 // can be computed from the storage row index.
 __device__ __forceinline__ int left_offset(int i, int sigma, long long k_left) {
@@ -54,11 +94,13 @@ struct Word {
 };
 
 // Masks of a matrix's word layout: delta bits (flag 1) and value bits; for
-// fixed point the shift of the value field and the matrix's scale 2^s.
+// fixed point the shift of the value field and the matrix's scale 2^s; the
+// length of x (m: what the bounds-check build checks columns against).
 struct Decode {
     uint32_t dmask, vmask;
     int vshift;
     float vscale;
+    int xlen;
 };
 
 inline Decode make_decode(const Matrix &A) {
@@ -67,6 +109,7 @@ inline Decode make_decode(const Matrix &A) {
     d.vmask = ~((2u << A.p.D) - 1u);
     d.vshift = A.p.D + 1;
     d.vscale = ldexpf(1.0f, A.value_exp);
+    d.xlen = (int)A.m;
     return d;
 }
 
@@ -76,7 +119,7 @@ __device__ __forceinline__ void word_gather(uint32_t wd, Decode dc, const float 
                                             int &c, bool &f, float &xv) {
     f = (wd & 1u) != 0u;
     c += (int)((wd >> 1) & (f ? dc.dmask : 0x7fffffffu));
-    if (f) xv = __ldg(x + c);
+    if (f) xv = PS_IN_RANGE(c, dc.xlen) ? __ldg(x + c) : 0.f;
 }
 
 // The value a word carries (FP16 in the upper half, or E8MY bits).

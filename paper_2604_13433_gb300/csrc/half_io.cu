@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(TPB)
         for (int u = 0; u < PF; ++u) {
             f[u] = (wd[u] & 1u) != 0u;
             c += (int)((wd[u] >> 1) & (f[u] ? dc.dmask : 0x7fffffffu));
-            if (f[u]) xv[u] = __half2float(__ldg(x + c));
+            if (f[u]) xv[u] = PS_IN_RANGE(c, dc.xlen) ? __half2float(__ldg(x + c)) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < PF; ++u)

@@ -80,6 +80,11 @@ inline bool is_w64(int fmt) { return fmt == PACKSELL_FMT_W64_E11MY; }
 // the formats whose products are FP64 (packsell_spmv_f64)
 inline bool is_f64_op(int fmt) { return fmt == PACKSELL_FMT_SELL_F64 || is_w64(fmt); }
 
+// bounds-check build: each translation unit registers a reader of its
+// counters (out-of-range accesses, first index; read and cleared)
+using ChecksReader = cudaError_t (*)(unsigned long long *count, long long *first);
+void register_checks_reader(ChecksReader r);
+
 // thread-local error message
 packsell_status fail(packsell_status st, const std::string &msg);
 packsell_status cuda_fail(cudaError_t e, const char *where);
@@ -131,6 +136,7 @@ struct SplitMat {  // one matrix of a split-row product and its vectors
     long long ldx, ldy;
     int k, sigma, sig_shift, kl, perm_bytes, fmt;
     uint32_t dmask, vmask;
+    int xlen;  // rows of X (m)
 };
 struct __align__(16) MultiItem {  // a tile (meta = rows << 16 | words) or a long row (meta = -words)
     long long base;

@@ -173,7 +173,8 @@ __device__ __forceinline__ void multi_long_row(const SplitMat &M, int row, long 
             MVec<NV> xv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                xv[j] = (wd[j] & 1u) ? mload<NV, VEC>(M.X + (size_t)(before + cs[j]) * M.ldx + q0, q0, M.k)
+                xv[j] = ((wd[j] & 1u) && PS_IN_RANGE(before + cs[j], M.xlen))
+                            ? mload<NV, VEC>(M.X + (size_t)(before + cs[j]) * M.ldx + q0, q0, M.k)
                                      : mzero<NV>();
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -252,7 +253,8 @@ __device__ __forceinline__ void multi_tile(const SplitMat &M, int r0, int nrows,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             MVec<NV> xv = mzero<NV>();
-            if (wd[j] & 1u) xv = mload<NV, VEC>(M.X + (size_t)col[j] * M.ldx + q0, q0, M.k);
+            if ((wd[j] & 1u) && PS_IN_RANGE(col[j], M.xlen))
+                xv = mload<NV, VEC>(M.X + (size_t)col[j] * M.ldx + q0, q0, M.k);
 #pragma unroll
             for (int i = 0; i < NV; ++i) pv[j].v[i] = val[j] * xv.v[i];
         }
@@ -408,6 +410,7 @@ SplitMat split_mat(const Matrix &A, const float *X, int64_t ldx, float *Y, int64
     M.kl = (int)std::min<int64_t>(A.p.k_left, INT32_MAX);
     M.fmt = A.p.format;
     M.dmask = (1u << A.p.D) - 1u;
+    M.xlen = (int)A.m;
     M.vmask = ~((2u << A.p.D) - 1u);
     return M;
 }

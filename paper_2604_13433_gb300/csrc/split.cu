@@ -158,7 +158,9 @@ __device__ __forceinline__ void split_long_row(int row, long long base, int nwd,
         carry += __shfl_sync(0xffffffffu, inc, 31);
         float xv[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xv[j] = (wd[j] & 1u) ? __ldg(x + (before + cs[j])) : 0.f;
+        for (int j = 0; j < 8; ++j)
+            xv[j] = ((wd[j] & 1u) && PS_IN_RANGE(before + cs[j], dc.xlen)) ? __ldg(x + (before + cs[j]))
+                                                                             : 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             if (wd[j] & 1u) t = fmaf(split_value<FMT>(wd[j], dc), xv[j], t);
@@ -233,7 +235,9 @@ __device__ __forceinline__ void split_tile(int r0, int nrows, long long base, in
     float pv[8];  // value * x of every word (0 without a value)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float xv = (wd[j] & 1u) ? __ldg(xb + col_comb(exc, cs[j])) : 0.f;
+        const float xv = ((wd[j] & 1u) && PS_IN_RANGE(col_comb(exc, cs[j]) - kAbs, dc.xlen))
+                             ? __ldg(xb + col_comb(exc, cs[j]))
+                             : 0.f;
         pv[j] = (wd[j] & 1u) ? split_value<FMT>(wd[j], dc) * xv : 0.f;
     }
     // segmented suffix sums. A: the lane's words before its first row start
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(SW * 32, 3)
         cp_async_wait_older();
         __syncwarp();
         const SplitMat &M = mats[d.mat];
-        const Decode dc{M.dmask, M.vmask, M.fmt == PACKSELL_FMT_FP16 ? 1 : 0, 1.f};
+        const Decode dc{M.dmask, M.vmask, M.fmt == PACKSELL_FMT_FP16 ? 1 : 0, 1.f, M.xlen};
         const int sg = SORTED ? M.sigma : 1, sh = SORTED ? M.sig_shift : 0;
         if (d.meta < 0)
             split_long_row<0, SORTED>(d.r0, d.base, -d.meta, sg, sh, M.kl, M.pack, M.perm,

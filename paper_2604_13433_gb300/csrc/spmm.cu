@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TPB)
                 for (int u = 0; u < SPF; ++u) {
                     const bool f = (wd[u] & 1u) != 0u;
                     c += (int)((wd[u] >> 1) & (f ? dc.dmask : 0x7fffffffu));
-                    if (f)
+                    if (f && PS_IN_RANGE(c, dc.xlen))
                         spmm_gather<KV, VEC>(X + (int64_t)c * ldx + qa, qa, step, k,
                                              word_value<FMT>(wd[u], dc), acc);
                 }
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(TPB)
                     float4 xv[GB][KV];
 #pragma unroll
                     for (int u = 0; u < GB; ++u) {
+                        if (!PS_IN_RANGE(cc[g0 + u], dc.xlen)) wd[g0 + u] &= ~1u;  // skipped
                         if (wd[g0 + u] & 1u)
                             spmm_load<KV, VEC>(X + (int64_t)cc[g0 + u] * ldx + qa, qa, step, k, xv[u]);
                     }

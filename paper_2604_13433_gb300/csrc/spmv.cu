@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(TPB)
             uint32_t d;
             Word<FMT>::decode(wd[u], dc.dmask, dc.vmask, fl[u], d, vv[u], dc.vshift, dc.vscale);
             c += (int)d;
-            xv[u] = fl[u] ? __ldg(x + c) : 0.f;
+            xv[u] = (fl[u] && PS_IN_RANGE(c, dc.xlen)) ? __ldg(x + c) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u)
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(TPB)
         if (wj == 0u) break;
         Word<FMT>::decode(wj, dc.dmask, dc.vmask, f, d, v, dc.vshift, dc.vscale);
         c += (int)d;
-        if (f) t = fmaf(v, __ldg(x + c), t);
+        if (f && PS_IN_RANGE(c, dc.xlen)) t = fmaf(v, __ldg(x + c), t);
     }
     y[orig_row(i, sigma, perm, perm_bytes)] = t;
 }
@@ -950,7 +950,7 @@ __global__ void __launch_bounds__(TPB)
         float v;
         Word<FMT>::decode(pack[s + (int64_t)j * C + l], dc.dmask, dc.vmask, f, d, v);
         c += (int)d;
-        if (f && g != 0.f) atomicAdd(dx + c, v * g);
+        if (f && g != 0.f && PS_IN_RANGE(c, dc.xlen)) atomicAdd(dx + c, v * g);
     }
 }
 
@@ -995,7 +995,8 @@ __global__ void __launch_bounds__(TPB)
         float val;
         Word<FMT>::decode(pack[s + (int64_t)j * C + l], dc.dmask, dc.vmask, f, d, val);
         c += (int)d;
-        if (f) out[q++] = a * v[c];
+        if (f && PS_IN_RANGE(c, dc.xlen) && PS_IN_RANGE(q, rowptr[io + 1])) out[q] = a * v[c];
+        q += f;
     }
 }
 

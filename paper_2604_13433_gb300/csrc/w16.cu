@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(TPB, MINB)
     k_spmv_w16(int n, int Cr, int sigma, int sig_shift, long long k_left,
                const int64_t *__restrict__ offset, const uint16_t *__restrict__ pack,
                const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
-               float *__restrict__ y) {
+               float *__restrict__ y, int xlen) {
     const int C = C32 ? 32 : Cr;  // a constant word stride when C = 32
     grid_dep_launch();  // one pass over the rows: signal at block start
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(TPB, MINB)
         for (int u = 0; u < PF; ++u) {
             f[u] = (wd[u] & 1u) != 0u;
             c += (int)((wd[u] >> 1) & (f[u] ? 0x7Fu : 0x7FFFu));
-            if (f[u]) xv[u] = __ldg(x + c);
+            if (f[u]) xv[u] = PS_IN_RANGE(c, xlen) ? __ldg(x + c) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < PF; ++u)
@@ -83,7 +83,8 @@ cudaError_t launch_w16(const Matrix &A, const void *perm, int pb, const float *x
     auto kern = pb ? (c32 ? k_spmv_w16<PF, MINB, true, true> : k_spmv_w16<PF, 3, true, false>)
                    : (c32 ? k_spmv_w16<PF, MINB, false, true> : k_spmv_w16<PF, 3, false, false>);
     return launch_pdl(kern, g, TPB, s, (int)A.n, A.p.C, sg, sh, A.p.k_left,
-                      (const int64_t *)A.offset, (const uint16_t *)A.pack16, perm, pb, x, y);
+                      (const int64_t *)A.offset, (const uint16_t *)A.pack16, perm, pb, x, y,
+                      (int)A.m);
 }
 
 }  // namespace

@@ -21,7 +21,7 @@ namespace packsell {
 namespace {
 
 constexpr int TPB = 256;
-constexpr int WU = 4;  // words per round
+constexpr int WU = 4;  // words per round (8 and 16 measured slower on the 27-point matrix)
 
 template <bool DOT>
 __device__ __forceinline__ void w64_rows(int n, int C, int sigma, long long k_left, int D,
@@ -29,12 +29,15 @@ __device__ __forceinline__ void w64_rows(int n, int C, int sigma, long long k_le
                                          const unsigned long long *__restrict__ pack,
                                          const void *__restrict__ perm, int perm_bytes,
                                          const double *__restrict__ x, double *__restrict__ y,
-                                         const double *__restrict__ b, Red red) {
+                                         const double *__restrict__ b, Red red, int xlen) {
     if (DOT) grid_dep_sync();  // the reducing form waits before it starts
     else grid_dep_launch();    // one pass over the rows: signal at block start
     if (DOT && red.sc->done) return;  // solver converged: idle (grid-uniform)
-    const unsigned long long dmask = (1ull << D) - 1ull;
-    const unsigned long long vmask = ~((2ull << D) - 1ull);
+    // a decoded delta, and every column, stays below 2^31 (columns are int32 and
+    // a dummy's delta is at most a column gap), so the delta comes from the low
+    // half of the word; the value's upper 32 bits are the word's own
+    const uint32_t dmask = (1u << D) - 1u;
+    const uint32_t vmask_lo = (uint32_t)~((2ull << D) - 1ull);
     double d1 = 0.0, d2 = 0.0;
     const int stride = DOT ? gridDim.x * blockDim.x : n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -42,7 +45,7 @@ __device__ __forceinline__ void w64_rows(int n, int C, int sigma, long long k_le
         const int64_t s = offset[k];
         const int w = (int)((offset[k + 1] - s) / C);
         const unsigned long long *pp = pack + s + l;
-        long long c = left_offset(i, sigma, k_left);
+        int c = left_offset(i, sigma, k_left);
         double t = 0.0;
         if (!DOT && w == 0) grid_dep_wait();
         for (int j0 = 0; j0 < w; j0 += WU) {
@@ -55,13 +58,16 @@ __device__ __forceinline__ void w64_rows(int n, int C, int sigma, long long k_le
             double xv[WU];
 #pragma unroll
             for (int u = 0; u < WU; ++u) {
-                f[u] = (wd[u] & 1ull) != 0ull;
-                c += (long long)((wd[u] >> 1) & (f[u] ? dmask : 0x7fffffffffffffffull));
-                xv[u] = f[u] ? __ldg(x + c) : 0.0;
+                const uint32_t lo = (uint32_t)wd[u];
+                f[u] = (lo & 1u) != 0u;
+                c += (int)((lo >> 1) & (f[u] ? dmask : 0x7fffffffu));
+                xv[u] = (f[u] && PS_IN_RANGE(c, xlen)) ? __ldg(x + c) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < WU; ++u)
-                if (f[u]) t = fma(__longlong_as_double((long long)(wd[u] & vmask)), xv[u], t);
+                if (f[u])
+                    t = fma(__hiloint2double((int)(wd[u] >> 32), (int)((uint32_t)wd[u] & vmask_lo)),
+                            xv[u], t);
         }
         const int io = orig_row(i, sigma, perm, perm_bytes);
         y[io] = t;
@@ -76,8 +82,9 @@ __device__ __forceinline__ void w64_rows(int n, int C, int sigma, long long k_le
 __global__ void __launch_bounds__(TPB)
     k_spmv_w64(int n, int C, int sigma, long long k_left, int D, const int64_t *__restrict__ offset,
                const unsigned long long *__restrict__ pack, const void *__restrict__ perm,
-               int perm_bytes, const double *__restrict__ x, double *__restrict__ y) {
-    w64_rows<false>(n, C, sigma, k_left, D, offset, pack, perm, perm_bytes, x, y, nullptr, Red{});
+               int perm_bytes, const double *__restrict__ x, double *__restrict__ y, int xlen) {
+    w64_rows<false>(n, C, sigma, k_left, D, offset, pack, perm, perm_bytes, x, y, nullptr, Red{},
+                    xlen);
 }
 
 // The reducing form (y = A x, then x.y and, with b, x.b into the solver's
@@ -86,8 +93,8 @@ __global__ void __launch_bounds__(TPB, 4)
     k_spmv_w64_dot(int n, int C, int sigma, long long k_left, int D,
                    const int64_t *__restrict__ offset, const unsigned long long *__restrict__ pack,
                    const void *__restrict__ perm, int perm_bytes, const double *__restrict__ x,
-                   double *__restrict__ y, const double *__restrict__ b, Red red) {
-    w64_rows<true>(n, C, sigma, k_left, D, offset, pack, perm, perm_bytes, x, y, b, red);
+                   double *__restrict__ y, const double *__restrict__ b, Red red, int xlen) {
+    w64_rows<true>(n, C, sigma, k_left, D, offset, pack, perm, perm_bytes, x, y, b, red, xlen);
 }
 
 // 1 / a_ii of a square matrix (1 where the diagonal is absent or 0).
@@ -125,7 +132,8 @@ packsell_status spmv_w64_impl(const Matrix &A, const double *x, double *y, cudaS
     const cudaError_t e = launch_pdl(k_spmv_w64, rows_grid(A.n), TPB, s, (int)A.n, A.p.C,
                                      A.p.sigma, (long long)A.p.k_left, A.p.D,
                                      (const int64_t *)A.offset,
-                                     (const unsigned long long *)A.pack64, perm, pb, x, y);
+                                     (const unsigned long long *)A.pack64, perm, pb, x, y,
+                                     (int)A.m);
     if (e != cudaSuccess) return cuda_fail(e, "packsell_spmv_f64 (64-bit words)");
     PS_LAUNCH_CHECK("packsell_spmv_f64 (64-bit words)");
     return PACKSELL_OK;
@@ -136,7 +144,8 @@ packsell_status spmv_dot_w64(const Matrix &A, const double *x, double *y, const 
     const cudaError_t e = launch_pdl(k_spmv_w64_dot, grid, TPB, s, (int)A.n, A.p.C, A.p.sigma,
                                      (long long)A.p.k_left, A.p.D, (const int64_t *)A.offset,
                                      (const unsigned long long *)A.pack64,
-                                     (const void *)A.perm, A.perm_bytes, x, y, b, red);
+                                     (const void *)A.perm, A.perm_bytes, x, y, b, red,
+                                     (int)A.m);
     if (e != cudaSuccess) return cuda_fail(e, "spmv_dot_f64 (64-bit words)");
     PS_LAUNCH_CHECK("spmv_dot_f64 (64-bit words)");
     return PACKSELL_OK;

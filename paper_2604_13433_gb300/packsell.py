@@ -19,6 +19,8 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpacksell.so")
+# the bounds-check build, loaded instead when PACKSELL_CHECKS=1
+LIB_CHECKS_PATH = os.path.join(_HERE, "libpacksell_checks.so")
 
 FMT_FP16, FMT_E8MY, FMT_SELL_F32, FMT_SELL_F64, FMT_W16_E4M3, FMT_SELL_F16 = 1, 2, 3, 4, 5, 6
 FMT_FIXED, FMT_W64_E11MY = 7, 8
@@ -27,7 +29,8 @@ _FORMATS = {"fp16": FMT_FP16, "e8my": FMT_E8MY, "sell_f32": FMT_SELL_F32,
             "fixed": FMT_FIXED, "w64_e11my": FMT_W64_E11MY}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSORTED", 3: "NONFINITE", 4: "RANGE", 5: "CUDA",
-          6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT"}
+          6: "NOT_CONVERGED", 7: "BREAKDOWN", 8: "NO_MEMORY", 9: "CORRUPT", 10: "TIMEOUT",
+          11: "CHECK"}
 SPMV_AUTO, SPMV_ROWTHREAD, SPMV_BULK = 0, 1, 2
 SPMV_BULK_VARIANTS = (2, 3, 4)
 SPMV_PREFETCH = (5, 6)
@@ -108,6 +111,7 @@ SIGNATURES = {
     "packsell_set_spmv_variant": (ctypes.c_int, [_P, _I32]),
     "packsell_check_status": (ctypes.c_int, [_P, _P]),
     "packsell_validate": (ctypes.c_int, [_P, _P]),
+    "packsell_checks_build": (ctypes.c_int32, []),
     "packsell_tune_spmv": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "packsell_quantize": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P]),
     "packsell_set_wait_limit": (ctypes.c_int, [_I64]),
@@ -138,14 +142,17 @@ SIGNATURES = {
 
 
 def lib():
-    """Load ``libpacksell.so`` (built in-tree); raise if it is missing."""
+    """Load ``libpacksell.so`` (built in-tree; ``libpacksell_checks.so`` when
+    the environment sets PACKSELL_CHECKS=1); raise if it is missing."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
+        checks = os.environ.get("PACKSELL_CHECKS") == "1"
+        path = LIB_CHECKS_PATH if checks else LIB_PATH
+        if not os.path.exists(path):
             raise RuntimeError(
-                f"{LIB_PATH} is missing: build it with `python -m paper_2604_13433_gb300.build` "
-                "(there is no CPU fallback)")
-        L = ctypes.CDLL(LIB_PATH)
+                f"{path} is missing: build it with `python -m paper_2604_13433_gb300.build"
+                f"{' --checks' if checks else ''}` (there is no CPU fallback)")
+        L = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)
             f.restype = res
