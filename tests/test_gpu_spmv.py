@@ -339,6 +339,33 @@ def test_spmv_host_buffers():
                                                           xd.data_ptr(), yd.data_ptr(), None))
 
 
+@pytest.mark.parametrize("host", ["pinned", "pinned_offset", "pageable"])
+def test_spmv_host_copy_paths(host):
+    """Host buffers of every kind - pinned, pinned starting one float into its
+    allocation, pageable - give packsell_spmv's bits, on sizes that are not
+    multiples of 4, over repeated calls."""
+    need_gpu()
+    packsell = P()
+    csr = I.random_csr(1001, 999, 0.01, seed=4, empty_rows=0.05)
+    A = encode_gpu(csr, fmt="e8my", D=9)
+    x = torch.from_numpy(I.uniform(csr.m, seed=5))
+    if host == "pageable":
+        xh, yh = x.clone(), torch.full((csr.n,), float("nan"))
+    else:
+        off = 1 if host == "pinned_offset" else 0
+        xb = torch.empty(csr.m + off, dtype=torch.float32).pin_memory()
+        yb = torch.full((csr.n + off,), float("nan"), dtype=torch.float32).pin_memory()
+        xh, yh = xb[off:], yb[off:]
+        xh.copy_(x)
+    xd = torch.empty(csr.m, device="cuda")
+    yd = torch.empty(csr.n, device="cuda")
+    for _ in range(3):  # repeated calls reuse the buffers
+        packsell.packsell_spmv_host(A, xh, yh, xd, yd)
+    torch.cuda.synchronize()
+    ref = packsell.packsell_spmv(A, x.cuda()).cpu()
+    assert torch.equal(yh.view(torch.int32), ref.view(torch.int32))
+
+
 def test_tune_spmv_picks_a_variant():
     need_gpu()
     packsell = P()
