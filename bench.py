@@ -275,6 +275,47 @@ def e2e_pipelined(torch, ps, A, xp, K, W):
     return t0.elapsed_time(t1) / K
 
 
+def link_ceiling(torch, xp, n_out, reps=30):
+    """The host link's copy rates with pinned buffers (CUDA events): host to
+    device alone, device to host alone, and each direction while both run on
+    two streams. An end-to-end step that moves Bi in and Bo out cannot beat
+    max(Bi, Bo) / (rate with both running)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xd = torch.empty(xp.numel(), dtype=torch.float32, device=dev)
+    yd = torch.empty(n_out, dtype=torch.float32, device=dev)
+    yp = torch.empty(n_out, dtype=torch.float32).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fns):
+        for _ in range(3):
+            for st, fn in fns:
+                with torch.cuda.stream(st):
+                    fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s1)
+        s2.wait_event(e0)
+        for _ in range(reps):
+            for st, fn in fns:
+                with torch.cuda.stream(st):
+                    fn()
+        s1.wait_stream(s2)
+        e1.record(s1)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps  # ms per repetition
+
+    h2d = lambda: xd.copy_(xp, non_blocking=True)
+    d2h = lambda: yp.copy_(yd, non_blocking=True)
+    bi, bo = 4 * xp.numel(), 4 * n_out
+    t_in, t_out = timed([(s1, h2d)]), timed([(s1, d2h)])
+    t_both = timed([(s1, h2d), (s2, d2h)])
+    return {"h2d_GBps": bi / t_in / 1e6, "d2h_GBps": bo / t_out / 1e6,
+            "both_directions_ms": t_both,
+            "floor_us_per_step": t_both * 1e3,
+            "how": "pinned buffers, CUDA events, 30 repetitions; the floor is both copies "
+                   "of one step running at once"}
+
+
 def oracle_spmv_median(O, csr, deq, x, threads, fp32=False, reps=10, warm=2):
     """Median seconds of the oracle's CSR SpMV (FP64, or the FP32 fused
     multiply-add chain per row) on `threads` host threads, over `reps` runs
@@ -824,10 +865,11 @@ def run_ours(args):
         def e2e_step():
             ps.packsell_spmv_host(A16, xp, yp, xd, y)
 
-        ms_e2e = ms_e2e_serial = None
+        ms_e2e = ms_e2e_serial = link = None
         if not args.no_e2e:
             ms_e2e_serial, _ = time_launches(torch, e2e_step, max(K // 10, 100), max(W // 10, 5))
             ms_e2e = e2e_pipelined(torch, ps, A16, xp, max(K // 10, 100), max(W // 10, 5))
+            link = link_ceiling(torch, xp, csr.n)
     sell = formats.get("sell_f32")
     ps.packsell_spmv(A16, x, y)
     ms_cold = time_cold(torch, lambda: ps.packsell_spmv(A16, x, y))
@@ -878,7 +920,8 @@ def run_ours(args):
                 "us_per_step": ms_e2e * 1e3 if ms_e2e else None,
                 "mode": "packsell_spmv_host (copy in, SpMV, copy out); steps rotate over three streams",
                 "serial_value": B16 / ms_e2e_serial / 1e6 if ms_e2e_serial else None,
-                "serial_us_per_step": ms_e2e_serial * 1e3 if ms_e2e_serial else None},
+                "serial_us_per_step": ms_e2e_serial * 1e3 if ms_e2e_serial else None,
+                "host_link": link},
         "gpu_launches": K,
         "clocks": clk.summary(),
     }

@@ -174,3 +174,78 @@ def test_diff_solve_512_sampled_systems(m_in, fmt, D):
             f"system {i}: dL/dtheta"
         xs, _, _ = S.pcg(c, b_h[sl], tol=1e-13, maxit=100000)
         assert np.linalg.norm(xg[sl] - xs) <= 1e-4 * np.linalg.norm(xs), f"system {i}: x"
+
+
+def test_batch_256_csr_order_full_size():
+    """The bench's batch of 256 in CSR order (C = 1) in one launch: every
+    matrix's y is variant 14's on that matrix alone, bit for bit, and within
+    the gamma_w bound of the oracle's FP64 product."""
+    need_gpu()
+    ps = P()
+    mats = I.zipf_batch(256, seed=5)
+    As, xs, ys = [], [], []
+    for i, c in enumerate(mats):
+        As.append(ps.packsell_encode_csr(c, fmt="fp16", D=15, C=1, sigma=1))
+        xs.append(dev(I.uniform(c.m, seed=100 + i)))
+        ys.append(torch.empty(c.n, dtype=torch.float32, device="cuda"))
+    B = ps.PackSELLBatch(As, xs, ys)
+    B.spmv()
+    torch.cuda.synchronize()
+    for i, c in enumerate(mats):
+        single = ps.packsell_spmv(As[i], xs[i])
+        assert torch.equal(ys[i].view(torch.int32), single.view(torch.int32)), f"matrix {i}"
+        if i % 16 == 0:
+            _, deq = O.quantize(c.val, O.FMT_FP16, 15)
+            xh = xs[i].cpu().numpy().astype(np.float64)
+            ref = O.csr_spmv_f64(c, deq, xh)
+            bound = O.spmv_error_bound(c, deq, xh, np.diff(c.rowptr))
+            y = ys[i].cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(y - ref) <= bound), f"matrix {i}"
+
+
+@pytest.fixture(scope="module")
+def st27():
+    need_gpu()
+    return I.stencil27(128, seed=0)
+
+
+@pytest.mark.parametrize("fmt,D", [("fixed", 15), ("e8my", 11), ("sell_f16", 15)])
+def test_headline_matrix_formats_full_size(st27, fmt, D):
+    """The bench's format sweep on the 27-point 128^3 matrix (C = 32, sigma =
+    256, explicit order, tuned variant): every row bitwise the FP32 twin of
+    the format's values."""
+    ps = P()
+    csr = st27
+    x = I.uniform(csr.m, seed=0)
+    xd = dev(x)
+    A = ps.packsell_encode_csr(csr, fmt=fmt, D=D, C=32, sigma=256, explicit_perm=True)
+    if fmt != "sell_f16":
+        ps.packsell_tune_spmv(A, xd, reps=3)
+    y = ps.packsell_spmv(A, xd).cpu().numpy()
+    if fmt == "fixed":
+        enc = O.encode(csr, C=32, sigma=256, D=D, fmt=O.FMT_FIXED)
+        deq = enc.deq
+    else:
+        qf = O.FMT_FP16 if fmt == "sell_f16" else O.FMT_E8MY
+        enc = O.encode(csr, C=32, sigma=256, D=D, fmt=qf)
+        deq = enc.deq
+    twin = O.csr_spmv_fma_f32(csr, deq.astype(np.float32), x)
+    rows = ps.packsell_storage_rows(A).cpu().numpy()
+    assert np.array_equal(y.view(np.uint32), twin[rows].view(np.uint32))
+
+
+def test_headline_matrix_64_bit_words_full_size(st27):
+    """The bench's FP64 pair on the 27-point 128^3 matrix: the 64-bit words
+    (E11M40, D = 11) byte for byte the oracle's encoding and the FP64
+    product bit for bit the oracle's stored-order chain."""
+    ps = P()
+    csr = st27
+    enc = O.encode64(csr, C=32, sigma=256, D=11)
+    A = ps.packsell_encode_csr(csr, fmt="w64_e11my", D=11, C=32, sigma=256, explicit_perm=True)
+    arr = ps.packsell_arrays(A)
+    assert np.array_equal(arr["offset"], enc.offset)
+    assert np.array_equal(arr["pack"], enc.pack)
+    x = I.uniform(csr.m, seed=0).astype(np.float64)
+    y = ps.packsell_spmv_f64(A, dev(x)).cpu().numpy()
+    want = O.packsell64_spmv_f64(enc, x, explicit=True)
+    assert np.array_equal(y.view(np.uint64), want.view(np.uint64))
