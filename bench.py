@@ -517,7 +517,7 @@ def batch_section(ps, torch, dev, K, W, peak):
                          C=C, sigma=sigma, words=B.words, items=B.items)
         del B
         if C == 1:
-            for k in (1, 4, 16):
+            for k in (1, 4, 16, 64):
                 Xs = [torch.rand(c.m, k, device=dev) for c in batch]
                 Ys = [torch.empty(c.n, k, device=dev) for c in batch]
                 Bm = ps.packsell_batch_create_spmm(mats, Xs, Ys)

@@ -104,7 +104,7 @@ def test_batch_mixes_slice_heights():
         _split_bound_check(yv, csr, enc.deq, x.cpu().numpy(), enc.words)
 
 
-@pytest.mark.parametrize("k", [1, 4, 16])
+@pytest.mark.parametrize("k", [1, 4, 16, 64])
 def test_batched_spmm_csr_order(k):
     """Batched SpMM over C = 1 matrices in one launch: every Y_i within
     gamma_w of the oracle's product; k = 1 takes the one-column form."""
