@@ -501,7 +501,7 @@ def stencil_spmm_section(ps, torch, dev, K, peak):
 def batch_section(ps, torch, dev, K, W, peak):
     """256 irregular matrices of 1k-100k rows (log-uniform sizes) per launch:
     SELL slices (C = 32) at sigma = 256 and 65,536, CSR order (C = 1, split
-    rows), and batched SpMM over the CSR-order matrices for k in {1, 4, 16}."""
+    rows), and batched SpMM over the CSR-order matrices for k in {1, 4, 16, 64}."""
     KS = max(K // 2, 5)
     batch = I.zipf_batch(256, seed=5)
     xs = [torch.from_numpy(I.uniform(c.m, seed=c.n)).to(dev) for c in batch]
