@@ -75,7 +75,7 @@ def parse():
                     help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
                          "e8m15), 'all' or 'none'")
     ap.add_argument("--pcg-grid", type=int, default=256, help="7-point Poisson grid side")
-    ap.add_argument("--pcg-min", default="20,80",
+    ap.add_argument("--pcg-min", default="20,50,80",
                     help="inner iterations of IO-CG, comma-separated (the paper sweeps 20, 50, 80)")
     return ap.parse_args()
 

@@ -111,10 +111,12 @@ __device__ __forceinline__ void stv(T *p, int64_t v, const T (&e)[V<T>::W]) {
     reinterpret_cast<typename V<T>::type *>(p)[v] = *reinterpret_cast<const typename V<T>::type *>(e);
 }
 
-// x += alpha p, r -= alpha q; s1 = r.z (z = M r), s2 = r.r. Each thread sums
-// its own elements in T (FP32 for the inner PCG: GB300's FP64 rate is too low
-// to spend per element) and the block and grid sums are FP64.
-template <typename T, bool VEC>
+// r -= alpha q and, with XUP, x += alpha p; s1 = r.z (z = M r), s2 = r.r.
+// Each thread sums its own elements in T (FP32 for the inner PCG: GB300's
+// FP64 rate is too low to spend per element) and the block and grid sums
+// are FP64. Without XUP the x update of the iteration is left to the next
+// direction kernel (k_pupdate, which reads p anyway), or to the final one.
+template <typename T, bool VEC, bool XUP>
 __global__ void __launch_bounds__(VTPB)
     k_update(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
              const T *__restrict__ q, const T *__restrict__ M, Red red) {
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(VTPB)
     const T a = (T)red.sc->alpha;
     T rz = 0, rr = 0;
     auto one = [&](int64_t i) {
-        x[i] = fma(a, p[i], x[i]);
+        if (XUP) x[i] = fma(a, p[i], x[i]);
         const T ri = fma(-a, q[i], r[i]);
         r[i] = ri;
         const T z = M ? M[i] * ri : ri;
@@ -140,8 +142,10 @@ __global__ void __launch_bounds__(VTPB)
             for (int h = 0; h < 2; ++h) {
                 const int64_t v = v0 + h * st;
                 if (v < nv) {
-                    ldv(x, v, xe[h]);
-                    ldv(p, v, pe[h]);
+                    if (XUP) {
+                        ldv(x, v, xe[h]);
+                        ldv(p, v, pe[h]);
+                    }
                     ldv(q, v, qe[h]);
                     ldv(r, v, re[h]);
                     if (M) ldv(M, v, me[h]);
@@ -153,13 +157,13 @@ __global__ void __launch_bounds__(VTPB)
                 if (v < nv) {
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
-                        xe[h][k] = fma(a, pe[h][k], xe[h][k]);
+                        if (XUP) xe[h][k] = fma(a, pe[h][k], xe[h][k]);
                         re[h][k] = fma(-a, qe[h][k], re[h][k]);
                         const T z = M ? me[h][k] * re[h][k] : re[h][k];
                         rz = fma(re[h][k], z, rz);
                         rr = fma(re[h][k], re[h][k], rr);
                     }
-                    stv(x, v, xe[h]);
+                    if (XUP) stv(x, v, xe[h]);
                     stv(r, v, re[h]);
                 }
             }
@@ -171,45 +175,67 @@ __global__ void __launch_bounds__(VTPB)
     reduce_publish(red, (double)rz, (double)rr);
 }
 
-// p = M r + beta p
-template <typename T, bool VEC>
+// Direction update. MODE 0: p = M r + beta p. MODE 1: first x += alpha p
+// (the previous iteration's x update, deferred from k_update: the same fused
+// multiply-add on the same p), then p = M r + beta p. MODE 2: x += alpha p
+// alone (the last iteration of a fixed-length solve). alpha and beta are
+// the iteration's (alpha is not rewritten before the next product).
+template <typename T, bool VEC, int MODE>
 __global__ void __launch_bounds__(VTPB)
     k_pupdate(int64_t n, const T *__restrict__ r, const T *__restrict__ M, T *__restrict__ p,
-              const SolveScalars *sc) {
+              T *__restrict__ x, const SolveScalars *sc) {
     grid_dep_sync();  // launched by launch_pdl, as k_update
     if (sc->done) return;
     const T b = (T)sc->beta;
+    const T a = (T)sc->alpha;
+    constexpr bool XU = MODE != 0, PU = MODE != 2;
     if (VEC) {
         constexpr int W = V<T>::W;
         const int64_t nv = n / W, tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         const int64_t st = (int64_t)gridDim.x * blockDim.x;
         for (int64_t v0 = tid; v0 < nv; v0 += 2 * st) {
-            T re[2][W], pe[2][W], me[2][W];
+            T re[2][W], pe[2][W], me[2][W], xe[2][W];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int64_t v = v0 + h * st;
                 if (v < nv) {
-                    ldv(r, v, re[h]);
                     ldv(p, v, pe[h]);
-                    if (M) ldv(M, v, me[h]);
+                    if (XU) ldv(x, v, xe[h]);
+                    if (PU) {
+                        ldv(r, v, re[h]);
+                        if (M) ldv(M, v, me[h]);
+                    }
                 }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int64_t v = v0 + h * st;
                 if (v < nv) {
+                    if (XU) {
 #pragma unroll
-                    for (int k = 0; k < W; ++k)
-                        pe[h][k] = fma(b, pe[h][k], M ? me[h][k] * re[h][k] : re[h][k]);
-                    stv(p, v, pe[h]);
+                        for (int k = 0; k < W; ++k) xe[h][k] = fma(a, pe[h][k], xe[h][k]);
+                        stv(x, v, xe[h]);
+                    }
+                    if (PU) {
+#pragma unroll
+                        for (int k = 0; k < W; ++k)
+                            pe[h][k] = fma(b, pe[h][k], M ? me[h][k] * re[h][k] : re[h][k]);
+                        stv(p, v, pe[h]);
+                    }
                 }
             }
         }
-        for (int64_t i = nv * W + tid; i < n; i += st) p[i] = fma(b, p[i], M ? M[i] * r[i] : r[i]);
+        for (int64_t i = nv * W + tid; i < n; i += st) {
+            if (XU) x[i] = fma(a, p[i], x[i]);
+            if (PU) p[i] = fma(b, p[i], M ? M[i] * r[i] : r[i]);
+        }
     } else {
         PS_FOR(i, n) {
-            const T z = M ? M[i] * r[i] : r[i];
-            p[i] = fma(b, p[i], z);
+            if (XU) x[i] = fma(a, p[i], x[i]);
+            if (PU) {
+                const T z = M ? M[i] * r[i] : r[i];
+                p[i] = fma(b, p[i], z);
+            }
         }
     }
 }
@@ -221,19 +247,23 @@ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // drains.
 template <typename T>
 cudaError_t launch_update(int G, cudaStream_t q, int64_t n, T *x, T *r, const T *p, const T *qv,
-                          const T *M, const Red &red) {
+                          const T *M, const Red &red, bool xup = true) {
     const bool vec =
         aligned16(x) && aligned16(r) && aligned16(p) && aligned16(qv) && (!M || aligned16(M));
-    return launch_pdl(vec ? k_update<T, true> : k_update<T, false>, (unsigned)G, VTPB, q, n, x, r,
-                      p, qv, M, red);
+    auto k = vec ? (xup ? k_update<T, true, true> : k_update<T, true, false>)
+                 : (xup ? k_update<T, false, true> : k_update<T, false, false>);
+    return launch_pdl(k, (unsigned)G, VTPB, q, n, x, r, p, qv, M, red);
 }
 
+// mode: 0 direction only, 1 deferred x update then direction, 2 x update only
 template <typename T>
-cudaError_t launch_pupdate(int G, cudaStream_t q, int64_t n, const T *r, const T *M, T *p,
-                           const SolveScalars *sc) {
-    const bool vec = aligned16(r) && aligned16(p) && (!M || aligned16(M));
-    return launch_pdl(vec ? k_pupdate<T, true> : k_pupdate<T, false>, (unsigned)G, VTPB, q, n, r,
-                      M, p, sc);
+cudaError_t launch_pupdate(int G, cudaStream_t q, int64_t n, const T *r, const T *M, T *p, T *x,
+                           const SolveScalars *sc, int mode = 0) {
+    const bool vec = aligned16(r) && aligned16(p) && (!M || aligned16(M)) && aligned16(x);
+    auto k = mode == 0 ? (vec ? k_pupdate<T, true, 0> : k_pupdate<T, false, 0>)
+             : mode == 1 ? (vec ? k_pupdate<T, true, 1> : k_pupdate<T, false, 1>)
+                         : (vec ? k_pupdate<T, true, 2> : k_pupdate<T, false, 2>);
+    return launch_pdl(k, (unsigned)G, VTPB, q, n, r, M, p, x, sc);
 }
 
 // Outer: z = ||r|| x_in (FP64), s1 = z.q (q = A p of the previous direction)
@@ -449,10 +479,14 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                     for (int k = 0; k < o.m_in; ++k) {
                         packsell_status e = spmv_dot_f32(*Ain, w.pi, w.qi, red(FIN_PQ_ALPHA), q);
                         if (e != PACKSELL_OK) return e;
+                        // the inner solve has a fixed length: each iteration's
+                        // x update rides on the next direction update (which
+                        // reads p anyway), the last one on its own
                         cudaError_t ce = launch_update<float>(G, q, n, w.xi, w.ri, w.pi, w.qi,
-                                                              w.M32, red(FIN_RZ_BETA));
-                        if (ce == cudaSuccess && k + 1 < o.m_in)
-                            ce = launch_pupdate<float>(G, q, n, w.ri, w.M32, w.pi, w.sc);
+                                                              w.M32, red(FIN_RZ_BETA), false);
+                        if (ce == cudaSuccess)
+                            ce = launch_pupdate<float>(G, q, n, w.ri, w.M32, w.pi, w.xi, w.sc,
+                                                       k + 1 < o.m_in ? 1 : 2);
                         if (ce != cudaSuccess) return cuda_fail(ce, "packsell_pcg: inner update");
                     }
                     k_outer_z<<<G, VTPB, 0, q>>>(n, w.xi, w.z, w.q, red(FIN_ZQ_BETA));
@@ -465,7 +499,8 @@ packsell_status solve_impl(const Matrix *A64, const Matrix *Ain, const double *i
                     if (e != PACKSELL_OK) return e;
                     cudaError_t ce = launch_update<double>(G, q, n, x, w.r, w.p, w.q, inv_diag,
                                                            red(FIN_RZ_BETA_RR));
-                    if (ce == cudaSuccess) ce = launch_pupdate<double>(G, q, n, w.r, inv_diag, w.p, w.sc);
+                    if (ce == cudaSuccess)
+                        ce = launch_pupdate<double>(G, q, n, w.r, inv_diag, w.p, x, w.sc);
                     if (ce != cudaSuccess) return cuda_fail(ce, "packsell_pcg: update");
                 }
             }
