@@ -1379,8 +1379,8 @@ packsell_status spmv_dot_f32(const Matrix &A, const float *x, float *y, const Re
             e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 8, 5>(A, x, y, red, s)
                   : launch_pipe_dot<PACKSELL_FMT_E8MY, 8, 5>(A, x, y, red, s);
         else if (pf == 10)
-            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 10, 4>(A, x, y, red, s)
-                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 10, 4>(A, x, y, red, s);
+            e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 10, 6>(A, x, y, red, s)
+                  : launch_pipe_dot<PACKSELL_FMT_E8MY, 10, 6>(A, x, y, red, s);
         else if (pf == 12)
             e = h ? launch_pipe_dot<PACKSELL_FMT_FP16, 12, 4>(A, x, y, red, s)
                   : launch_pipe_dot<PACKSELL_FMT_E8MY, 12, 4>(A, x, y, red, s);
