@@ -99,7 +99,7 @@ typedef enum packsell_status {
  *         integer coefficients) are exact. D in [6, 22] (V <= 25 bits, so
  *         every q converts to FP32 exactly). Supported by
  *         packsell_encode, packsell_spmv (the thread-per-row variant 1 and,
- *         with C = 32, variant 13, both summing the decoded values q * 2^s in
+ *         with C = 32, variant 13, the default there; both summing the decoded values q * 2^s in
  *         stored order: the bits of the FP32 twin of the decoded matrix;
  *         packsell_tune_spmv times the two), packsell_spmv_host, packsell_get_info,
  *         packsell_storage_rows, packsell_export and packsell_import (the

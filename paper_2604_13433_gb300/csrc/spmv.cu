@@ -1046,6 +1046,8 @@ packsell_status plan_spmv(Matrix &A, cudaStream_t s) {
         else if (A.csr_items) A.auto_variant = 11;
         return PACKSELL_OK;
     }
+    // fixed point in slices of 32 rows: the row-prefetch kernel (variant 13)
+    if (is_fixed(A.p.format) && A.p.C == 32 && A.n > 0) A.auto_variant = 13;
     // the bulk kernel indexes a warp's words with 32-bit integers
     if (!is_packed(A.p.format) || A.p.C != 32 || A.n == 0 || A.n_words >= (1ll << 31) - 4096)
         return PACKSELL_OK;
