@@ -117,4 +117,6 @@ def test_null_arguments_refused_without_gpu():
     assert lib.packsell_set_spmv_variant(None, 5) == 1
     assert lib.packsell_storage_rows(None, None, None) == 1
     assert lib.packsell_spmv_host(None, None, None, None, None, None) == 1
+    assert lib.packsell_validate(None, None) == 1
+    assert lib.packsell_checks_build() == 0  # the regular build (the checks build is separate)
     assert b"NULL" in lib.packsell_last_error()
