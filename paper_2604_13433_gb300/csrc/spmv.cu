@@ -859,11 +859,13 @@ __global__ void __launch_bounds__(TPB, 4)
 // UNROLL slots go out before any is used, as in the FP32 SELL kernel, and the
 // launch is programmatic (values and columns load before the wait on the
 // previous kernel of the stream; x and y after it).
+template <int U, bool C32>
 __global__ void __launch_bounds__(TPB)
-    k_spmv_sell16(int n, int C, int sigma, const int64_t *__restrict__ offset,
+    k_spmv_sell16(int n, int Cr, int sigma, const int64_t *__restrict__ offset,
                   const uint16_t *__restrict__ val, const int32_t *__restrict__ col,
                   const void *__restrict__ perm, int perm_bytes, const float *__restrict__ x,
                   float *__restrict__ y) {
+    const int C = C32 ? 32 : Cr;  // a constant slot stride when C = 32
     grid_dep_launch();  // one pass over the rows: signal at block start
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) {
@@ -877,11 +879,11 @@ __global__ void __launch_bounds__(TPB)
     const int32_t *cp = col + s + l;
     float t = 0.f;
     bool waited = false;
-    for (int j = 0; j < w; j += UNROLL) {
-        uint16_t v[UNROLL];
-        int cc[UNROLL];
+    for (int j = 0; j < w; j += U) {
+        uint16_t v[U];
+        int cc[U];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
+        for (int u = 0; u < U; ++u) {
             const bool ok = j + u < w;
             v[u] = ok ? __ldcs(vp + (int64_t)(j + u) * C) : (uint16_t)0;
             cc[u] = ok ? __ldcs(cp + (int64_t)(j + u) * C) : -1;
@@ -890,13 +892,13 @@ __global__ void __launch_bounds__(TPB)
             grid_dep_wait();
             waited = true;
         }
-        float xv[UNROLL];
+        float xv[U];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.f;
+        for (int u = 0; u < U; ++u) xv[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : 0.f;
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u)
+        for (int u = 0; u < U; ++u)
             if (cc[u] >= 0) t = fmaf(__half2float(__ushort_as_half(v[u])), xv[u], t);
-        if (cc[UNROLL - 1] < 0) break;  // padding: the row has ended
+        if (cc[U - 1] < 0) break;  // padding: the row has ended
     }
     if (!waited) grid_dep_wait();
     y[orig_row(i, sigma, perm, perm_bytes)] = t;
@@ -1187,7 +1189,12 @@ packsell_status spmv_impl(const Matrix &A, const float *x, float *y, cudaStream_
                 (int)A.n, A.p.C, A.p.sigma, A.p.k_left, A.offset, A.pack, perm, pb, make_decode(A), x, y);
             break;
         case PACKSELL_FMT_SELL_F16: {
-            const cudaError_t e = launch_pdl(k_spmv_sell16, (unsigned)g, TPB, s, (int)A.n, A.p.C,
+            // rounds of 16 slots where rows are longer than 8 (as the PackSELL
+            // row-prefetch kernel), a constant slot stride when C = 32
+            const bool wide = A.max_width > 8, c32 = A.p.C == 32;
+            auto k = wide ? (c32 ? k_spmv_sell16<16, true> : k_spmv_sell16<16, false>)
+                          : (c32 ? k_spmv_sell16<8, true> : k_spmv_sell16<8, false>);
+            const cudaError_t e = launch_pdl(k, (unsigned)g, TPB, s, (int)A.n, A.p.C,
                                              A.p.sigma, (const int64_t *)A.offset,
                                              (const uint16_t *)A.val, (const int32_t *)A.col, perm,
                                              pb, x, y);
