@@ -75,6 +75,8 @@ def parse():
                     help="comma list of the format sweep (sell_f32,fp16_v1..v6,e8m7,e8m11,"
                          "e8m15), 'all' or 'none'")
     ap.add_argument("--pcg-grid", type=int, default=256, help="7-point Poisson grid side")
+    ap.add_argument("--irregular-rows", type=int, default=4194304,
+                    help="rows of the irregular power-law matrix (4M by default)")
     ap.add_argument("--pcg-min", default="20,50,80",
                     help="inner iterations of IO-CG, comma-separated (the paper sweeps 20, 50, 80)")
     return ap.parse_args()
@@ -401,23 +403,29 @@ def spmm_bytes(A, k):
     return 4 * A.n_words + 8 * (A.n_slices + 1) + perm + 4 * k * (A.m + A.n)
 
 
-SPMM_KERNEL = {1: "k_split_multi", 32: "k_spmm_packed"}
+def spmm_kernel(C, k):
+    """The kernel packsell_spmm runs for a C-row-slice matrix and k > 1 columns
+    (16-byte-aligned X and Y with k % 4 == 0)."""
+    if C == 1:
+        return "k_split_rows" if k > 16 else "k_split_multi"
+    return "k_spmm_packed"
 
 
-def irregular_section(ps, torch, dev, K, W, peak):
+def irregular_section(ps, torch, dev, K, W, peak, n_rows=4194304):
     """The irregular non-symmetric 4M-row matrix (Zipf(2) row lengths up to
     4,096, columns around the diagonal plus 5 % uniform, FP16 values): SpMV in
     SELL slices (C = 32, sigma = 256, tuned variant) and in CSR order (C = 1,
     the split-row variant 14 and the stored-order variant 11), FP32 SELL and
     cuSPARSE CSR for comparison, SpMM for k in {1, 4, 16, 64} in both layouts."""
     KS = max(K // 2, 5)
-    csr = I.zipf_irregular(4194304, seed=3)
+    csr = I.zipf_irregular(n_rows, seed=3)
     rp = torch.from_numpy(csr.rowptr).to(dev)
     cl = torch.from_numpy(csr.col).to(dev)
     vl = torch.from_numpy(csr.val).to(dev)
     x = torch.from_numpy(I.uniform(csr.m, seed=4)).to(dev)
     y = torch.empty(csr.n, dtype=torch.float32, device=dev)
-    sec = {"workload": "zipf2_irregular_4M", "n": csr.n, "nnz": csr.nnz, "K": K, "K_spmm": KS}
+    name = "zipf2_irregular_4M" if n_rows == 4194304 else f"zipf2_irregular_{n_rows}"
+    sec = {"workload": name, "n": csr.n, "nnz": csr.nnz, "K": K, "K_spmm": KS}
     A = ps.packsell_encode(rp, cl, vl, csr.n, csr.m, fmt="fp16", D=15, explicit_perm=True)
     tuned = ps.packsell_tune_spmv(A, x, y, reps=10)
     v = min(tuned, key=tuned.get)
@@ -446,7 +454,7 @@ def irregular_section(ps, torch, dev, K, W, peak):
             Y = torch.empty(csr.n, k, device=dev)
             ms, _ = time_launches(torch, lambda: ps.packsell_spmm(M, X, Y), KS, 3)
             kern = (KERNEL_NAMES[ps.SPMV_SPLIT] if M.C == 1 else KERNEL_NAMES.get(v, "k_spmv")) \
-                if k == 1 else SPMM_KERNEL[M.C]
+                if k == 1 else spmm_kernel(M.C, k)
             rows[str(k)] = _rate(spmm_bytes(M, k), ms, peak, kern,
                                  GFLOPs=2 * k * csr.nnz / ms / 1e6)
             del X, Y
@@ -492,7 +500,7 @@ def stencil_spmm_section(ps, torch, dev, K, peak):
         X = torch.rand(csr.m, k, device=dev)
         Y = torch.empty(csr.n, k, device=dev)
         ms, _ = time_launches(torch, lambda: ps.packsell_spmm(A, X, Y), KS, 3)
-        out[str(k)] = _rate(spmm_bytes(A, k), ms, peak, "k_spmm_packed",
+        out[str(k)] = _rate(spmm_bytes(A, k), ms, peak, spmm_kernel(32, k),
                             GFLOPs=2 * k * csr.nnz / ms / 1e6)
         del X, Y
     return out
@@ -522,7 +530,7 @@ def batch_section(ps, torch, dev, K, W, peak):
                 Ys = [torch.empty(c.n, k, device=dev) for c in batch]
                 Bm = ps.packsell_batch_create_spmm(mats, Xs, Ys)
                 ms, _ = time_launches(torch, Bm.spmm, KS, 3)
-                kern = "k_spmv_split_batch" if k == 1 else "k_split_multi"
+                kern = "k_spmv_split_batch" if k == 1 else spmm_kernel(1, k)
                 out[f"csr_order_spmm_k{k}"] = _rate(Bm.bytes, ms, peak, kern, k=k, items=Bm.items)
                 del Bm, Xs, Ys
         del mats
@@ -930,7 +938,7 @@ def run_ours(args):
                                   [int(v) for v in str(args.pcg_min).split(",")])
     secs = set() if args.quick else set(args.sections.split(","))
     if "irregular" in secs:
-        line["irregular_4M"] = irregular_section(ps, torch, dev, K, W, peak)
+        line["irregular_4M"] = irregular_section(ps, torch, dev, K, W, peak, args.irregular_rows)
     if "spmm" in secs:
         line["stencil27_128_spmm"] = stencil_spmm_section(ps, torch, dev, K, peak)
     if "batch" in secs:

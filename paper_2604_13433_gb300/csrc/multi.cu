@@ -364,6 +364,344 @@ __global__ void __launch_bounds__(MW * 32)
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// ---- k > 16 with 16-byte X and Y rows: words walked from a decoded table ----
+// The segmented sums above re-run every scan once per group of four columns,
+// and each of their gather instructions touches 32 rows of X. For wider k a
+// warp decodes the item's words once into a table in shared memory (column,
+// or -1 for a word without a value; value; the y row where a row starts) and
+// then multiplies from it: lane (cg, h), cg = lane % KG, h = lane / KG, owns
+// NQ groups of four columns, 4 cg + 4 KG i (i < NQ), of a pass of 4 KG NQ
+// columns, and the RPI = 32 / KG lane groups split the tile's words into
+// runs of about equal length that begin at row starts. A group walks its run
+// in stored order from +0 per row, so every row of a tile gets the same fused
+// multiply-adds as the thread-per-row SpMV (the same bits); one gather
+// instruction fetches RPI rows of X, 16 KG contiguous bytes each. A long row
+// is decoded chunk by chunk into the table; group h takes the chunk's words
+// h, h + RPI, ..., and the groups' sums are added by a butterfly (a fixed
+// tree: within gamma_w).
+template <int NQ>
+struct RowAcc {
+    float4 t[NQ];
+};
+
+template <int KG, int NQ, int U>
+__device__ __forceinline__ void rows_step(const SplitMat &M, const int2 (&e)[U], int qb, int cg,
+                                          RowAcc<NQ> &a) {
+    float4 xv[U][NQ];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = qb + 4 * cg + 4 * KG * i;
+            if (e[u].x >= 0 && q < M.k)
+                xv[u][i] = __ldg(reinterpret_cast<const float4 *>(M.X + (size_t)e[u].x * M.ldx + q));
+        }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float v = __int_as_float(e[u].y);
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = qb + 4 * cg + 4 * KG * i;
+            if (e[u].x >= 0 && q < M.k) {
+                a.t[i].x = fmaf(v, xv[u][i].x, a.t[i].x);
+                a.t[i].y = fmaf(v, xv[u][i].y, a.t[i].y);
+                a.t[i].z = fmaf(v, xv[u][i].z, a.t[i].z);
+                a.t[i].w = fmaf(v, xv[u][i].w, a.t[i].w);
+            }
+        }
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void rows_zero(RowAcc<NQ> &a) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) a.t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int KG, int NQ>
+__device__ __forceinline__ void rows_store(const SplitMat &M, float *__restrict__ yr, int qb, int cg,
+                                           const RowAcc<NQ> &a) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const int q = qb + 4 * cg + 4 * KG * i;
+        if (q < M.k) *reinterpret_cast<float4 *>(yr + q) = a.t[i];
+    }
+}
+
+// words of a round per lane group: four gathers in flight per lane
+template <int NQ>
+constexpr int rows_round() {
+    return NQ >= 4 ? 1 : 4 / NQ;
+}
+
+// A tile: the words are split into RPI runs of about nwd / RPI words, each
+// moved forward to the next row start, so that every row lies in one run;
+// lane group h walks run h in stored order, U words (their gathers issued
+// together) at a time, and writes a row's sums when the next row starts.
+template <int KG, int NQ>
+__device__ __forceinline__ void rows_tile(const SplitMat &M, int r0, int nrows, long long base,
+                                          int nwd, int lane, const uint4 &wv,
+                                          uint32_t *__restrict__ s_lft, int *__restrict__ s_io,
+                                          int4 *__restrict__ s_tab, const uint32_t *__restrict__ soff) {
+    constexpr int RPI = 32 / KG, U = rows_round<NQ>();
+    const long long a0 = base & ~3ll;
+    const int lead = (int)(base - a0);
+    const uint32_t a0lo = (uint32_t)a0;
+    reinterpret_cast<uint4 *>(s_lft)[lane] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    // row starts: kAbs | left offset and the y row; an empty row's y is zeroed here
+    for (int kk = lane; kk < nrows; kk += 32) {
+        const int r = r0 + kk;
+        const uint32_t o0 = soff[kk], o1 = soff[kk + 1];
+        const int io = mout(M, r);
+        if (o1 != o0) {
+            const int pos = (int)(o0 - a0lo);
+            s_lft[pos] = kAbsM | (uint32_t)mleft(r, M.sigma, M.sig_shift, M.kl);
+            s_io[pos] = io;
+        } else {
+            for (int q = 0; q < M.k; q += 4)
+                *reinterpret_cast<float4 *>(M.Y + (size_t)io * M.ldy + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncwarp();
+    const uint4 hv = reinterpret_cast<const uint4 *>(s_lft)[lane];
+    const uint32_t hl[4] = {hv.x, hv.y, hv.z, hv.w};
+    uint32_t wd[4] = {wv.x, wv.y, wv.z, wv.w}, cs[4], acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int p = 4 * lane + j;
+        if ((unsigned)(p - lead) >= (unsigned)nwd) wd[j] = 0u;
+        acc = mcomb(acc, hl[j] + mdelta(M, wd[j]));
+        cs[j] = acc;
+    }
+    uint32_t inc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = mcomb(v, inc);
+    }
+    uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc = 0u;  // the tile's first word starts a row
+    // table entry: column (-1: no value), value bits, y row at a row start (-1 elsewhere)
+    unsigned hb[4];  // hb[j] bit l: position 4 l + j starts a row
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t col = mcomb(exc, cs[j]) & ~kAbsM;
+        const bool ok = (wd[j] & 1u) && PS_IN_RANGE(col, M.xlen);
+        const bool head = (hl[j] & kAbsM) != 0u;
+        hb[j] = __ballot_sync(0xffffffffu, head);
+        s_tab[4 * lane + j] = make_int4(ok ? (int)col : -1, ok ? __float_as_int(mvalue(M, wd[j])) : 0,
+                                        head ? s_io[4 * lane + j] : -1, 0);
+    }
+    __syncwarp();
+    // this group's run [S, E): from the first row start at or after its share
+    const int cg = lane % KG, h = lane / KG;
+    const int end = lead + nwd;
+    auto first_start = [&](int T) {
+        int best = MT;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int lmin = max(0, (T - j + 3) >> 2);
+            const unsigned m = lmin >= 32 ? 0u : (hb[j] & (0xffffffffu << lmin));
+            if (m) best = min(best, 4 * (__ffs(m) - 1) + j);
+        }
+        return min(best, end);
+    };
+    const int S = first_start(lead + (h * nwd) / RPI);
+    const int E = h == RPI - 1 ? end : first_start(lead + ((h + 1) * nwd) / RPI);
+    for (int qb = 0; qb < M.k; qb += 4 * KG * NQ) {
+        RowAcc<NQ> a;
+        rows_zero(a);
+        int yrow = -1;
+        for (int p = S; p < E; p += U) {
+            int4 e[U];
+            float4 xv[U][NQ];
+#pragma unroll
+            for (int u = 0; u < U; ++u) e[u] = p + u < E ? s_tab[p + u] : make_int4(-1, 0, -1, 0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) {
+                    const int q = qb + 4 * cg + 4 * KG * i;
+                    if (e[u].x >= 0 && q < M.k)
+                        xv[u][i] = __ldg(reinterpret_cast<const float4 *>(M.X + (size_t)e[u].x * M.ldx + q));
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e[u].z >= 0) {  // a row starts: the previous one is complete
+                    if (yrow >= 0) rows_store<KG, NQ>(M, M.Y + (size_t)yrow * M.ldy, qb, cg, a);
+                    rows_zero(a);
+                    yrow = e[u].z;
+                }
+                const float v = __int_as_float(e[u].y);
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) {
+                    const int q = qb + 4 * cg + 4 * KG * i;
+                    if (e[u].x >= 0 && q < M.k) {
+                        a.t[i].x = fmaf(v, xv[u][i].x, a.t[i].x);
+                        a.t[i].y = fmaf(v, xv[u][i].y, a.t[i].y);
+                        a.t[i].z = fmaf(v, xv[u][i].z, a.t[i].z);
+                        a.t[i].w = fmaf(v, xv[u][i].w, a.t[i].w);
+                    }
+                }
+            }
+        }
+        if (yrow >= 0) rows_store<KG, NQ>(M, M.Y + (size_t)yrow * M.ldy, qb, cg, a);
+    }
+    __syncwarp();
+}
+
+template <int KG, int NQ>
+__device__ __forceinline__ void rows_long(const SplitMat &M, int row, long long base, int nwd,
+                                          int lane, int4 *__restrict__ s_tab) {
+    constexpr int RPI = 32 / KG, U = rows_round<NQ>();
+    static_assert(MT % (U * RPI) == 0, "a chunk splits evenly over the lane groups");
+    const long long a0 = base & ~3ll;
+    const int lead = (int)(base - a0), lim = lead + nwd;
+    const int io = mout(M, row);
+    const uint32_t c0 = (uint32_t)mleft(row, M.sigma, M.sig_shift, M.kl);
+    const int cg = lane % KG, h = lane / KG;
+    for (int qb = 0; qb < M.k; qb += 4 * KG * NQ) {  // the same trip count in every lane
+        uint32_t carry = c0;
+        RowAcc<NQ> a;
+        rows_zero(a);
+        uint4 cur = mload_words(M.pack, a0, lim, lane);
+        for (int k0 = 0; k0 < lim; k0 += MT) {
+            const uint4 nxt = mload_words(M.pack, a0 + k0 + MT, lim - k0 - MT, lane);
+            uint32_t wd[4] = {cur.x, cur.y, cur.z, cur.w}, cs[4], acc = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = k0 + 4 * lane + j;
+                if ((unsigned)(p - lead) >= (unsigned)nwd) wd[j] = 0u;
+                acc += mdelta(M, wd[j]);
+                cs[j] = acc;
+            }
+            uint32_t inc = acc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const uint32_t before = carry + inc - acc;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+            int2 e4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t col = before + cs[j];
+                const bool ok = (wd[j] & 1u) && PS_IN_RANGE(col, M.xlen);
+                e4[j] = ok ? make_int2((int)col, __float_as_int(mvalue(M, wd[j]))) : make_int2(-1, 0);
+            }
+            __syncwarp();  // the previous chunk's table reads are done
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s_tab[4 * lane + j] = make_int4(e4[j].x, e4[j].y, -1, 0);
+            __syncwarp();
+            for (int p = h; p < MT; p += U * RPI) {
+                int2 e[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int4 t = s_tab[p + u * RPI];
+                    e[u] = make_int2(t.x, t.y);
+                }
+                rows_step<KG, NQ, U>(M, e, qb, cg, a);
+            }
+            cur = nxt;
+        }
+#pragma unroll
+        for (int o = KG; o < 32; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                a.t[i].x += __shfl_xor_sync(0xffffffffu, a.t[i].x, o);
+                a.t[i].y += __shfl_xor_sync(0xffffffffu, a.t[i].y, o);
+                a.t[i].z += __shfl_xor_sync(0xffffffffu, a.t[i].z, o);
+                a.t[i].w += __shfl_xor_sync(0xffffffffu, a.t[i].w, o);
+            }
+        }
+        if (h == 0) rows_store<KG, NQ>(M, M.Y + (size_t)io * M.ldy, qb, cg, a);
+    }
+}
+
+// Persistent grid over the same items as k_split_multi, the next item's words
+// and row offsets loading while the current one is processed.
+template <int KG, int NQ, bool SINGLE>
+__global__ void __launch_bounds__(MW * 32, SINGLE ? 3 : 2)
+    k_split_rows(SplitMat M0, const SplitMat *__restrict__ mats, const MultiItem *__restrict__ items,
+                 int nitems) {
+    __shared__ __align__(16) uint32_t s_lft[MW][MT];
+    __shared__ __align__(16) int s_io[MW][MT];
+    __shared__ __align__(16) int4 s_tab[MW][MT];
+    __shared__ __align__(16) uint32_t s_off[MW][2][MR_MAX + 4];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int it = gw;
+    if (it >= nitems) return;
+    MultiItem d = items[it];
+    {
+        const uint32_t *pk = SINGLE ? M0.pack : mats[d.mat].pack;
+        const int64_t *of = SINGLE ? M0.offset : mats[d.mat].offset;
+        uint4 wv = multi_first_words(pk, d, lane);
+        multi_prefetch(of, d, true, s_off[wl][0], lane);
+        int buf = 0;
+        for (; it < nitems; it += nwarps) {
+            const bool has_next = it + nwarps < nitems;
+            MultiItem dn{0, 0, 0, 0, 0, 0, 0};
+            uint4 wn = make_uint4(0, 0, 0, 0);
+            if (has_next) {
+                dn = items[it + nwarps];
+                const uint32_t *pn = SINGLE ? M0.pack : mats[dn.mat].pack;
+                wn = multi_first_words(pn, dn, lane);
+                multi_prefetch(SINGLE ? M0.offset : mats[dn.mat].offset, dn, true,
+                               s_off[wl][buf ^ 1], lane);
+            } else {
+                multi_prefetch(nullptr, dn, false, s_off[wl][buf ^ 1], lane);
+            }
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __syncwarp();
+            const SplitMat M = SINGLE ? M0 : mats[d.mat];
+            if (d.meta < 0)
+                rows_long<KG, NQ>(M, d.r0, d.base, -d.meta, lane, s_tab[wl]);
+            else
+                rows_tile<KG, NQ>(M, d.r0, d.meta >> 16, d.base, d.meta & 0xFFFF, lane, wv,
+                                  s_lft[wl], s_io[wl], s_tab[wl], s_off[wl][buf]);
+            __syncwarp();
+            d = dn;
+            wv = wn;
+            buf ^= 1;
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <int KG, int NQ, bool SINGLE>
+packsell_status launch_rows_t(const SplitMat &single, const SplitMat *mats, const MultiItem *items,
+                              int nitems, cudaStream_t s) {
+    static std::atomic<int> cached{0};
+    int blocks = cached.load(std::memory_order_relaxed);
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_split_rows<KG, NQ, SINGLE>, MW * 32,
+                                                          0) != cudaSuccess)
+            return fail(PACKSELL_ERR_CUDA, "split-row product: device query failed");
+        blocks = sms * std::max(per, 1);
+        cached.store(blocks, std::memory_order_relaxed);
+    }
+    blocks = std::min(blocks, (nitems + MW - 1) / MW);
+    k_split_rows<KG, NQ, SINGLE><<<blocks, MW * 32, 0, s>>>(single, mats, items, nitems);
+    PS_LAUNCH_CHECK("split-row product");
+    return PACKSELL_OK;
+}
+
+template <bool SINGLE>
+packsell_status launch_rows(const SplitMat &single, const SplitMat *mats, const MultiItem *items,
+                            int nitems, int k, cudaStream_t s) {
+    // eight lanes per row group (four row groups per warp): one column group
+    // per lane up to k = 32, two above (passes of 64 columns)
+    if (k <= 32) return launch_rows_t<8, 1, SINGLE>(single, mats, items, nitems, s);
+    return launch_rows_t<8, 2, SINGLE>(single, mats, items, nitems, s);
+}
+
 template <int NV, bool VEC, bool SINGLE>
 int multi_blocks() {
     static std::atomic<int> cached{0};
@@ -482,6 +820,9 @@ packsell_status launch_multi(const SplitMat &single, const SplitMat *mats, const
     if (k == 1)
         return one ? launch_multi_t<1, false, true>(single, mats, items, nitems, s)
                    : launch_multi_t<1, false, false>(single, mats, items, nitems, s);
+    if (vec && k > 16)  // words walked from a decoded table
+        return one ? launch_rows<true>(single, mats, items, nitems, k, s)
+                   : launch_rows<false>(single, mats, items, nitems, k, s);
     if (vec)
         return one ? launch_multi_t<4, true, true>(single, mats, items, nitems, s)
                    : launch_multi_t<4, true, false>(single, mats, items, nitems, s);

@@ -485,6 +485,34 @@ def test_spmm_strided_layouts(fmt, C, sigma, explicit, k):
         assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32)), f"column {r}"
 
 
+@pytest.mark.parametrize("fmt,sigma,explicit,k", [("fp16", 256, True, 8), ("e8my", 64, False, 12),
+                                                  ("fp16", 1, False, 20), ("e8my", 256, True, 36),
+                                                  ("fp16", 100, False, 64), ("fp16", 256, True, 64)])
+def test_spmm_aligned_column_slices(fmt, sigma, explicit, k):
+    """C = 32 with 16-byte-aligned column slices of wider arrays (ld = k + 8):
+    the 16-byte gathers of the lane-group SpMM, in both row orders, with k
+    not a multiple of a pass's column count (12, 20, 36). Every column equals
+    the twin bit for bit and nothing outside Y's columns is written."""
+    need_gpu()
+    packsell = P()
+    D = 11 if fmt == "e8my" else 15
+    csr = I.random_csr(1000, 800, 0.012, seed=100 + k, empty_rows=0.05, long_gaps=True)
+    enc = O.encode(csr, C=32, sigma=sigma, D=D, fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, C=32, sigma=sigma, D=D, explicit_perm=explicit)
+    Xw = np.random.default_rng(k).uniform(-1, 1, (800, k + 8)).astype(np.float32)
+    Xd = dev(Xw)[:, 4:k + 4]
+    Yd = torch.full((1000, k + 8), float("nan"), device="cuda")
+    packsell.packsell_spmm(A, Xd, Yd[:, 4:k + 4])
+    Y = Yd.cpu().numpy()
+    assert np.isnan(Y[:, :4]).all() and np.isnan(Y[:, k + 4:]).all()
+    Y = Y[:, 4:k + 4]
+    if explicit:
+        Y = Y[np.argsort(O.storage_rows(enc))]
+    for r in range(k):
+        twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), np.ascontiguousarray(Xw[:, r + 4]))
+        assert np.array_equal(Y[:, r].view(np.uint32), twin.view(np.uint32)), f"column {r}"
+
+
 def assert_within_bound(Y, csr, deq, X, words):
     """Every entry of Y (original row order) within gamma_w * sum_j |a_ij X_jq|
     of the oracle's FP64 product, w the stored words of the row."""
@@ -521,6 +549,36 @@ def test_spmm_csr_order_split_rows(fmt, D, sigma, k):
     packsell.packsell_spmm(A, Xd, Yd)
     assert np.array_equal(Y1.view(np.uint32), Yd.cpu().numpy().view(np.uint32))
     assert_within_bound(Y1, csr, enc.deq, X, enc.words)
+
+
+@pytest.mark.parametrize("fmt,D,sigma,k", [("fp16", 15, 1, 20), ("e8my", 7, 1, 36), ("fp16", 15, 64, 64),
+                                           ("e8my", 11, 1, 100)])
+def test_spmm_csr_order_wide_k(fmt, D, sigma, k):
+    """CSR-order SpMM with 16 < k and 16-byte-aligned column slices (ld = k + 8;
+    k = 100 takes two passes of 64 columns): the rows of a tile (at most 125
+    words) are walked in stored order from the decoded table, so they equal
+    the twin bit for bit; the longer rows, summed by lane groups and a
+    butterfly, stay within gamma_w; nothing outside Y's columns is written."""
+    need_gpu()
+    packsell = P()
+    csr = I.zipf_irregular(12000, seed=70 + k)
+    enc = O.encode(csr, C=1, sigma=sigma, D=D, fmt=FMT[fmt])
+    A = encode_gpu(csr, fmt=fmt, D=D, C=1, sigma=sigma)
+    Xw = np.random.default_rng(k).uniform(-1, 1, (csr.m, k + 8)).astype(np.float32)
+    Yd = torch.full((csr.n, k + 8), float("nan"), device="cuda")
+    packsell.packsell_spmm(A, dev(Xw)[:, 4:k + 4], Yd[:, 4:k + 4])
+    Yw = Yd.cpu().numpy()
+    assert np.isnan(Yw[:, :4]).all() and np.isnan(Yw[:, k + 4:]).all()
+    Y = Yw[:, 4:k + 4]
+    X = Xw[:, 4:k + 4]
+    assert_within_bound(Y, csr, enc.deq, X, enc.words)
+    tile_rows = np.asarray(enc.words) <= 125
+    assert tile_rows.sum() > 0.9 * csr.n and (~tile_rows).any()
+    for r in sorted({0, 1, k // 2, k - 1}):
+        twin = O.csr_spmv_fma_f32(csr, enc.deq.astype(np.float32), np.ascontiguousarray(X[:, r]))
+        got = Y[:, r]
+        assert np.array_equal(got[tile_rows].view(np.uint32), twin[tile_rows].view(np.uint32)), \
+            f"column {r}"
 
 
 @pytest.mark.parametrize("fmt,D", [("fp16", 15), ("e8my", 3), ("sell_f32", 15)])
