@@ -61,6 +61,8 @@ def run_all(A, x, m):
             ps.packsell_set_spmv_variant(A, v)
             out[f"v{v}"] = ps.packsell_spmv(A, x).clone()
         ps.packsell_set_spmv_variant(A, 0)
+        for k in (4, 20):  # the split-row SpMM and, above k = 16, the table walk
+            out[f"spmm{k}"] = ps.packsell_spmm(A, x[:, None].repeat(1, k).contiguous()).clone()
         y = torch.empty(A.n, device="cuda")
         B = ps.PackSELLBatch([A], [x], [y])
         B.spmv()
@@ -81,6 +83,8 @@ for C in (32, 1):
     assert status() == (0, ""), status()
     key = "v1" if C == 32 else "v11"  # the stored-order chains: the twin's bits
     assert np.array_equal(good[key].cpu().numpy().view(np.uint32), twin.view(np.uint32))
+    if C == 1:  # rows of at most 125 words: the table walk's stored-order chain
+        assert np.array_equal(good["spmm20"][:, 7].cpu().numpy().view(np.uint32), twin.view(np.uint32))
 
     # rewrite a row's last value word so that it decodes to column m
     words = words_view(A)
@@ -109,6 +113,13 @@ for C in (32, 1):
             code, msg = status()
             assert code == 11, (C, name, code, msg)
     ps.packsell_set_spmv_variant(A, 0)
+    for name in list(good):
+        if name.startswith("spmm") and name != "spmm":
+            k = int(name[4:])
+            ps.packsell_spmm(A, x[:, None].repeat(1, k).contiguous())
+            torch.cuda.synchronize()
+            code, msg = status()
+            assert code == 11 and f"first index {m})" in msg, (C, name, code, msg)
     # restore the word: no skips again
     words[at] = np.array(int(arr[at]), np.uint32).view(np.int32).item()
     torch.cuda.synchronize()
