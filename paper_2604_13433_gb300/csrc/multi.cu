@@ -22,7 +22,10 @@
 //    butterfly reduction; once per group of four columns.
 // The summation order is fixed (the same bits on every run) but is a tree:
 // every entry of Y is within gamma_w * sum_j |a_ij X_jq| of the exact product
-// (w stored words of the row).
+// (w stored words of the row). For k > 16 with 16-byte X and Y rows a second
+// kernel, k_split_rows below, decodes each item once into a table in shared
+// memory and walks its words; there a tile's rows keep the stored-order
+// chain of the thread-per-row SpMV.
 #include <cuda_fp16.h>
 
 #include <algorithm>
