@@ -10,10 +10,13 @@
 // from z = 0 on the FP16 operator (Jacobi preconditioning is the identity on
 // the symmetrically scaled matrices of §5.2). Every layer builds its Krylov
 // basis with classical Gram-Schmidt: the dot products of a step are one
-// deterministic reduction in double precision (block partials summed in
-// block order), the update of the new vector is done in double and rounded
-// to the layer's precision, and the Hessenberg matrix, its Givens rotations
-// and the small least-squares solve stay on the device in double precision.
+// deterministic reduction (block partials summed in block order, in double
+// precision), the update of the new vector is done in the layer's arithmetic
+// (double for the FP64 layers; FP32 for the FP32 layers of FP16-F3R, whose
+// per-thread partial sums are FP32 as well, since on GB300 the FP64 pipe
+// and not memory would bound those kernels), and the Hessenberg matrix, its
+// Givens rotations and the small least-squares solve stay on the device in
+// double precision.
 // Layers 2-4 run a fixed number of steps (no convergence test); layer 1
 // reads its residual estimate |g_{j+1}| after every step and confirms
 // convergence on the true residual b - A x in FP64.
@@ -29,6 +32,7 @@
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -60,33 +64,6 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;
 }
 
-// partial sums of v.v per block
-template <typename T>
-__global__ void __launch_bounds__(FT) k_norm2_part(int64_t n, const T *__restrict__ v,
-                                                   double *__restrict__ part) {
-    __shared__ double sh[FT / 32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
-        const double a = (double)v[i];
-        s = fma(a, a, s);
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// partial sums of w.v_i for the cnt basis vectors v_i (blockIdx.y = i)
-template <typename T>
-__global__ void __launch_bounds__(FT) k_mdot_part(int64_t n, const T *__restrict__ V,
-                                                  const T *__restrict__ w, double *__restrict__ part) {
-    __shared__ double sh[FT / 32];
-    const T *__restrict__ v = V + (int64_t)blockIdx.y * n;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
-        s = fma((double)w[i], (double)v[i], s);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
-}
-
 // Arnoldi state of one layer (double, device): H column-major (m+1) x m,
 // Givens cosines and sines, right-hand side g (m+1), solution y (m), and
 // scal = {beta = ||rhs||, 1 / (last norm), |g_{j+1}|}
@@ -95,24 +72,34 @@ struct Hess {
     int m;
 };
 
-// h[i][j] = sum of the partials of w.v_i, in block order (one block)
-__global__ void __launch_bounds__(FT) k_mdot_finish(int G, int cnt, const double *__restrict__ part,
-                                                    Hess h, int j) {
-    __shared__ double sh[FT / 32];
-    for (int i = 0; i < cnt; ++i) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < G; b += FT) s += part[(int64_t)i * G + b];
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) h.H[i + (int64_t)j * (h.m + 1)] = s;
+// The reducing kernels below end with the step that needs the whole
+// reduction: each block writes its partial, and the block that arrives last
+// (an atomic counter, back at 0 when it is done) adds the partials in block
+// order and finishes, so no one-block kernel follows. Called by every thread
+// after thread 0 has written the block's partial; true in the last block
+// once every partial is visible.
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1u;
+        if (last) *counter = 0u;
     }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// sum of the G partials at p, in block order (the whole block; thread 0 has it)
+__device__ __forceinline__ double partial_sum(const double *p, int G, double *sh) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < G; b += FT) s += ((const volatile double *)p)[b];
+    return block_sum(s, sh);
 }
 
 // beta = ||rhs|| from the partials; g = beta e_1; scal[1] = 1 / beta
-__global__ void __launch_bounds__(FT) k_begin(int G, const double *__restrict__ part, Hess h) {
-    __shared__ double sh[FT / 32];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < G; b += FT) s += part[b];
-    s = block_sum(s, sh);
+__device__ __forceinline__ void begin_finish(int G, const double *part, Hess h, double *sh) {
+    const double s = partial_sum(part, G, sh);
     if (threadIdx.x == 0) {
         const double beta = sqrt(s);
         h.scal[0] = beta;
@@ -123,43 +110,76 @@ __global__ void __launch_bounds__(FT) k_begin(int G, const double *__restrict__ 
     }
 }
 
+// partial sums of v.v per block; the last block sets up the layer (begin_finish)
+template <typename T>
+__global__ void __launch_bounds__(FT) k_norm2_begin(int64_t n, const T *__restrict__ v,
+                                                    double *__restrict__ part, unsigned *counter,
+                                                    Hess h) {
+    __shared__ double sh[FT / 32];
+    double s = 0.0;
+    if constexpr (std::is_same<T, float>::value) {  // an FP32 layer: FP32 thread partials
+        float sf = 0.f;
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+            sf = fmaf(v[i], v[i], sf);
+        s = (double)sf;
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+            const double a = (double)v[i];
+            s = fma(a, a, s);
+        }
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (last_block(counter)) begin_finish(gridDim.x, part, h, sh);
+}
+
+// partial sums of w.v_i for the cnt basis vectors v_i (blockIdx.y = i); the
+// last block sets h[i][j] = the sum of the partials of w.v_i, in block order
+template <typename T>
+__global__ void __launch_bounds__(FT) k_mdot(int64_t n, const T *__restrict__ V,
+                                             const T *__restrict__ w, double *__restrict__ part,
+                                             unsigned *counter, Hess h, int j) {
+    __shared__ double sh[FT / 32];
+    const T *__restrict__ v = V + (int64_t)blockIdx.y * n;
+    double s = 0.0;
+    if constexpr (std::is_same<T, float>::value) {
+        float sf = 0.f;
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+            sf = fmaf(w[i], v[i], sf);
+        s = (double)sf;
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+            s = fma((double)w[i], (double)v[i], s);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (!last_block(counter)) return;
+    const int G = gridDim.x;
+    for (int i = 0; i < (int)gridDim.y; ++i) {
+        const double t = partial_sum(part + (int64_t)i * G, G, sh);
+        if (threadIdx.x == 0) h.H[i + (int64_t)j * (h.m + 1)] = t;
+    }
+}
+
 // out = (TO)(in * scal[k])
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(FT) k_scale(int64_t n, const TI *__restrict__ in, TO *__restrict__ out,
                                               const double *__restrict__ scal) {
     const double s = *scal;
-    for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
-        out[i] = (TO)((double)in[i] * s);
-}
-
-// w = w - sum_i h[i][j] v_i (in double, rounded once to T); partials of w.w
-template <typename T>
-__global__ void __launch_bounds__(FT) k_orth(int64_t n, const T *__restrict__ V, int cnt, Hess h, int j,
-                                             T *__restrict__ w, double *__restrict__ part) {
-    __shared__ double sh[FT / 32];
-    __shared__ double hc[64];
-    for (int i = threadIdx.x; i < cnt; i += FT) hc[i] = h.H[i + (int64_t)j * (h.m + 1)];
-    __syncthreads();
-    double s = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
-        double a = (double)w[e];
-        for (int i = 0; i < cnt; ++i) a -= hc[i] * (double)V[(int64_t)i * n + e];
-        const T r = (T)a;
-        w[e] = r;
-        s = fma((double)r, (double)r, s);
+    if constexpr (std::is_same<TI, float>::value && std::is_same<TO, float>::value) {
+        const float sf = (float)s;
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+            out[i] = in[i] * sf;
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+            out[i] = (TO)((double)in[i] * s);
     }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // h[j+1][j] = ||w||; the earlier Givens rotations on column j, a new one
 // that zeroes h[j+1][j]; g updated; scal[1] = 1 / h[j+1][j], scal[2] = |g[j+1]|
-__global__ void __launch_bounds__(FT) k_arnoldi_finish(int G, const double *__restrict__ part, Hess h,
-                                                       int j) {
-    __shared__ double sh[FT / 32];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < G; b += FT) s += part[b];
-    s = block_sum(s, sh);
+__device__ __forceinline__ void arnoldi_finish(int G, const double *part, Hess h, int j, double *sh) {
+    const double s = partial_sum(part, G, sh);
     if (threadIdx.x != 0) return;
     const int ld = h.m + 1;
     double *col = h.H + (int64_t)j * ld;
@@ -183,6 +203,44 @@ __global__ void __launch_bounds__(FT) k_arnoldi_finish(int G, const double *__re
     h.scal[2] = fabs(h.g[j + 1]);
 }
 
+// w = w - sum_i h[i][j] v_i (in double, rounded once to T); partials of w.w;
+// the last block closes the Arnoldi step (arnoldi_finish)
+template <typename T>
+__global__ void __launch_bounds__(FT) k_orth(int64_t n, const T *__restrict__ V, int cnt, Hess h, int j,
+                                             T *__restrict__ w, double *__restrict__ part,
+                                             unsigned *counter) {
+    __shared__ double sh[FT / 32];
+    __shared__ double hc[64];
+    __shared__ float hf[64];
+    for (int i = threadIdx.x; i < cnt; i += FT) {
+        hc[i] = h.H[i + (int64_t)j * (h.m + 1)];
+        hf[i] = (float)hc[i];
+    }
+    __syncthreads();
+    double s = 0.0;
+    if constexpr (std::is_same<T, float>::value) {
+        float sf = 0.f;
+        for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
+            float a = w[e];
+            for (int i = 0; i < cnt; ++i) a = fmaf(-hf[i], V[(int64_t)i * n + e], a);
+            w[e] = a;
+            sf = fmaf(a, a, sf);
+        }
+        s = (double)sf;
+    } else {
+        for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
+            double a = (double)w[e];
+            for (int i = 0; i < cnt; ++i) a -= hc[i] * (double)V[(int64_t)i * n + e];
+            const T r = (T)a;
+            w[e] = r;
+            s = fma((double)r, (double)r, s);
+        }
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (last_block(counter)) arnoldi_finish(gridDim.x, part, h, j, sh);
+}
+
 // y = R^-1 g over the first k columns (R the rotated Hessenberg matrix)
 __global__ void k_backsolve(Hess h, int k) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -200,12 +258,24 @@ template <typename TZ, typename TO, bool ACC>
 __global__ void __launch_bounds__(FT) k_combine(int64_t n, const TZ *__restrict__ Z, int k,
                                                 const double *__restrict__ y, TO *__restrict__ out) {
     __shared__ double ys[64];
-    for (int i = threadIdx.x; i < k; i += FT) ys[i] = y[i];
+    __shared__ float yf[64];
+    for (int i = threadIdx.x; i < k; i += FT) {
+        ys[i] = y[i];
+        yf[i] = (float)y[i];
+    }
     __syncthreads();
-    for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
-        double a = ACC ? (double)out[e] : 0.0;
-        for (int j = 0; j < k; ++j) a += ys[j] * (double)Z[(int64_t)j * n + e];
-        out[e] = (TO)a;
+    if constexpr (std::is_same<TZ, float>::value && std::is_same<TO, float>::value) {
+        for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
+            float a = ACC ? out[e] : 0.f;
+            for (int j = 0; j < k; ++j) a = fmaf(yf[j], Z[(int64_t)j * n + e], a);
+            out[e] = a;
+        }
+    } else {
+        for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
+            double a = ACC ? (double)out[e] : 0.0;
+            for (int j = 0; j < k; ++j) a += ys[j] * (double)Z[(int64_t)j * n + e];
+            out[e] = (TO)a;
+        }
     }
 }
 
@@ -217,10 +287,11 @@ __global__ void __launch_bounds__(FT) k_rich(int64_t n, T *__restrict__ z, const
         z[e] = first ? (T)(omega * r[e]) : (T)(z[e] + omega * (r[e] - t[e]));
 }
 
-// r = b - A x (x, r, b double) and the partials of r.r
+// r = b - A x (x, r, b double) and the partials of r.r; the last block sets
+// up layer 1 from r (begin_finish: beta = ||r||, v_0 scale)
 __global__ void __launch_bounds__(FT) k_resid(int64_t n, const double *__restrict__ b,
                                               const double *__restrict__ ax, double *__restrict__ r,
-                                              double *__restrict__ part) {
+                                              double *__restrict__ part, unsigned *counter, Hess h) {
     __shared__ double sh[FT / 32];
     double s = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)FT + threadIdx.x; e < n; e += (int64_t)gridDim.x * FT) {
@@ -230,6 +301,7 @@ __global__ void __launch_bounds__(FT) k_resid(int64_t n, const double *__restric
     }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (last_block(counter)) begin_finish(gridDim.x, part, h, sh);
 }
 
 // one product of a layer: double vectors on the FP64 formats (SELL_F64,
@@ -285,6 +357,7 @@ struct F3R {
     int64_t n;
     int G;
     double *part;  // G * 64 partials
+    unsigned *counter;  // blocks of the running reduction that have finished (0 between launches)
     Layer<double> L1;
     Layer<TI> L2, L3;
     TI *rt = nullptr;  // the product of a Richardson step (the iterate is layer 3's z_j)
@@ -312,10 +385,8 @@ struct F3R {
         packsell_status st = layer_spmv(A, L.Z + (int64_t)j * n, w, s);
         if (st != PACKSELL_OK) return st;
         const int cnt = j + 1;
-        k_mdot_part<T><<<dim3(G, cnt), FT, 0, s>>>(n, L.V, w, part);
-        k_mdot_finish<<<1, FT, 0, s>>>(G, cnt, part, L.h, j);
-        k_orth<T><<<G, FT, 0, s>>>(n, L.V, cnt, L.h, j, w, part);
-        k_arnoldi_finish<<<1, FT, 0, s>>>(G, part, L.h, j);
+        k_mdot<T><<<dim3(G, cnt), FT, 0, s>>>(n, L.V, w, part, counter, L.h, j);
+        k_orth<T><<<G, FT, 0, s>>>(n, L.V, cnt, L.h, j, w, part, counter);
         k_scale<T, T><<<G, FT, 0, s>>>(n, w, w, L.h.scal + 1);
         PS_LAUNCH_CHECK("f3r: Arnoldi step");
         return PACKSELL_OK;
@@ -324,8 +395,7 @@ struct F3R {
     // v_0 = rhs / ||rhs|| (converted to T), g = ||rhs|| e_1
     template <typename T, typename TR>
     void begin(Layer<T> &L, const TR *rhs) {
-        k_norm2_part<TR><<<G, FT, 0, s>>>(n, rhs, part);
-        k_begin<<<1, FT, 0, s>>>(G, part, L.h);
+        k_norm2_begin<TR><<<G, FT, 0, s>>>(n, rhs, part, counter, L.h);
         k_scale<TR, T><<<G, FT, 0, s>>>(n, rhs, L.V, L.h.scal + 1);
     }
 
@@ -390,7 +460,7 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
                           (size_t)(o.m1 + 1) * o.m1 + 8 * (size_t)o.m1 + 16) +
         sizeof(TI) * ((size_t)(2 * o.m2 + 1) * n + (size_t)(2 * o.m3 + 1) * n + 2 * (size_t)n) +
         sizeof(double) * ((size_t)(o.m2 + 1) * o.m2 + (size_t)(o.m3 + 1) * o.m3 + 8 * (size_t)(o.m2 + o.m3) + 32) +
-        256 * 32;
+        256 * 40;
     double *r = nullptr, *ax = nullptr, *zt = nullptr, *prhs = nullptr, *pout = nullptr;
     double nb = 0.0;
     if (cudaMallocAsync(&mem, need, s) != cudaSuccess) {
@@ -408,13 +478,14 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
     F.omega = (float)o.omega;
     F.s = s;
     F.part = P.take<double>(64 * (size_t)G);
+    F.counter = P.take<unsigned>(1);
     r = P.take<double>(n);
     ax = P.take<double>(n);
     zt = P.take<double>(n);
     prhs = P.take<double>(n);
     pout = P.take<double>(n);
     F.rt = P.take<TI>(n);
-    if (!F.part || !r || !ax || !zt || !prhs || !pout || !F.rt || !make_layer(P, F.L1, o.m1, n) ||
+    if (!F.part || !F.counter || !r || !ax || !zt || !prhs || !pout || !F.rt || !make_layer(P, F.L1, o.m1, n) ||
         !make_layer(P, F.L2, o.m2, n) || !make_layer(P, F.L3, o.m3, n)) {
         st = fail(PACKSELL_ERR_NO_MEMORY, "packsell_f3r: workspace carving");
         goto out;
@@ -427,8 +498,7 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
         auto true_residual = [&](double *rr) -> packsell_status {
             packsell_status e = spmv_f64_impl(A1, x, ax, s);
             if (e != PACKSELL_OK) return e;
-            k_resid<<<G, FT, 0, s>>>(n, b, ax, r, F.part);
-            k_begin<<<1, FT, 0, s>>>(G, F.part, F.L1.h);  // beta = ||r||, v_0 scale
+            k_resid<<<G, FT, 0, s>>>(n, b, ax, r, F.part, F.counter, F.L1.h);  // beta = ||r||, v_0 scale
             PS_LAUNCH_CHECK("f3r: residual");
             double sc[3];
             if (!ck(cudaMemcpyAsync(sc, F.L1.h.scal, sizeof(sc), cudaMemcpyDeviceToHost, s)) ||
@@ -438,8 +508,8 @@ packsell_status run_f3r(const Matrix &A1, const Matrix &A2, const Matrix &A3, co
             return PACKSELL_OK;
         };
         // ||b||
-        k_norm2_part<double><<<G, FT, 0, s>>>(n, b, F.part);
-        k_begin<<<1, FT, 0, s>>>(G, F.part, F.L1.h);
+        if (!ck(cudaMemsetAsync(F.counter, 0, sizeof(unsigned), s))) goto out;
+        k_norm2_begin<double><<<G, FT, 0, s>>>(n, b, F.part, F.counter, F.L1.h);
         double sc[3];
         if (!ck(cudaMemcpyAsync(sc, F.L1.h.scal, sizeof(sc), cudaMemcpyDeviceToHost, s)) ||
             !ck(cudaStreamSynchronize(s)))
