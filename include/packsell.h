@@ -747,10 +747,11 @@ void packsell_f3r_opts_default(packsell_f3r_opts *o);
  *    FP16 SpMV of the paper);
  *  - FP64-F3R: A_mid and A_low SELL_F64 or W64_E11MY (every layer in FP64).
  * A_outer is SELL_F64 or W64_E11MY; all three square, of the same size, rows in original
- * order (any C and sigma). Krylov bases by classical Gram-Schmidt with
- * deterministic FP64 dot products, updates rounded once to the layer's
- * precision; Hessenberg matrices, Givens rotations and least-squares solves
- * in FP64 on the device. The outer residual estimate is read after every
+ * order (any C and sigma). Krylov bases by classical Gram-Schmidt in each
+ * layer's arithmetic: FP64 layers in double; FP32 layers in FP32, with the
+ * dot products' per-thread partials in FP32 and their block and grid sums in
+ * FP64 (deterministic: block order); Hessenberg matrices, Givens rotations
+ * and least-squares solves in FP64 on the device. The outer residual estimate is read after every
  * outer step; convergence is confirmed on the true FP64 residual (a cycle
  * restarts from it otherwise). FP16-F3R with a PackSELL FP16 A_low and with
  * the FP16 SELL copy of the same matrix runs the same arithmetic: the same
